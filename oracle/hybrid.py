@@ -1,0 +1,147 @@
+"""Oracle of the multi-frame layer -- TEST INFRASTRUCTURE ONLY.
+
+* ``Fsm``: LCP-FSM, the per-frame choice between LCP-S and LCP-T (Sec.
+  "Hybrid Compression with LCP-S & T").  The state diagram (Fig. 3) is not in
+  the text; the reading implemented here is: states T and S{k} (k = 2, 4, 8,
+  16).  The LCP-S estimate is the size of the most recent LCP-S frame.  With
+  no reference frame the choice is spatial; with a reference but no estimate
+  yet both are run and the smaller wins (ties to spatial), entering T or S2.
+  In T every frame tests LCP-T; it stays when T <= estimate, else the frame
+  is coded spatially and the state becomes S2.  In S{k} frames are coded
+  spatially without a test until the k-th, which tests LCP-T: a win enters T,
+  a loss doubles k (capped at 16).  PARITY UNPINNED against the paper (the
+  figure is missing); pinned only by its own definition in tests.
+* ``encode_trajectory`` / ``decode_trajectory``: Algorithm 1 (spatial anchor
+  frames): the first frame of each batch is predicted from the last anchor,
+  other frames from the previous frame, and a first frame coded spatially
+  becomes the new anchor.  Decoding follows the recursive rule of Sec.
+  "Spatial-Anchor-Frame-Based Batch Compression" in stream order.
+* ``choose_block_size``: Sec. "Best block size": exact sizes for each
+  candidate p, smallest wins, ties to the smaller p.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+FLAG_FIRST_IN_BATCH = 1
+FLAG_REF_ANCHOR = 2
+BLOCK_CANDIDATES = (2, 4, 8, 16, 32)
+
+
+class Fsm:
+    def __init__(self):
+        self.state = 2  # "T" or k of S{k}
+        self.counter = 0
+        self.s_est = None
+
+    def plan(self, has_ref: bool) -> str:
+        """'spatial', 'compare' or 'test' (test LCP-T against the estimate)."""
+        if not has_ref:
+            return "spatial"
+        if self.s_est is None:
+            return "compare"
+        if self.state == "T":
+            return "test"
+        self.counter += 1
+        if self.counter >= self.state:
+            self.counter = 0
+            return "test"
+        return "spatial"
+
+    def after_compare(self, t_wins: bool, s_size: int):
+        self.s_est = s_size
+        self.state = "T" if t_wins else 2
+        self.counter = 0
+
+    def after_test(self, t_wins: bool, s_size: int | None):
+        if s_size is not None:
+            self.s_est = s_size
+        if t_wins:
+            self.state = "T"
+        elif self.state == "T":
+            self.state = 2
+        else:
+            self.state = min(2 * self.state, 16)
+        self.counter = 0
+
+    def after_spatial(self, s_size: int):
+        self.s_est = s_size
+
+
+def encode_trajectory(frames, eb: float, mode="abs", p: int = 8, batch: int = 10,
+                      log2_chunk: int = 10):
+    """Algorithm 1 over an iterable of frames [D, N].  Returns a list of
+    (container bytes, method 'S'/'T') in frame order."""
+    fsm = Fsm()
+    prev = None    # (q, pi) of the previous frame, slot order
+    anchor = None  # (q, pi) of the last spatial anchor frame
+    out = []
+    for t, X in enumerate(frames):
+        first = (t % batch) == 0
+        ref = anchor if first else prev
+        flags = FLAG_FIRST_IN_BATCH if first else 0
+        tflags = flags | (FLAG_REF_ANCHOR if first else 0)
+        action = fsm.plan(ref is not None)
+        s_res = t_res = None
+        if action == "spatial":
+            s_res = oracle.compress_s(X, eb, mode, p, log2_chunk, flags)
+            fsm.after_spatial(len(s_res["bytes"]))
+            use_t = False
+        elif action == "compare":
+            s_res = oracle.compress_s(X, eb, mode, p, log2_chunk, flags)
+            t_res = oracle.compress_t(X, eb, mode, ref[0], ref[1], log2_chunk, tflags)
+            use_t = len(t_res["bytes"]) < len(s_res["bytes"])
+            fsm.after_compare(use_t, len(s_res["bytes"]))
+        else:  # test LCP-T against the estimate
+            t_res = oracle.compress_t(X, eb, mode, ref[0], ref[1], log2_chunk, tflags)
+            use_t = len(t_res["bytes"]) <= fsm.s_est
+            if not use_t:
+                s_res = oracle.compress_s(X, eb, mode, p, log2_chunk, flags)
+            fsm.after_test(use_t, None if use_t else len(s_res["bytes"]))
+        if use_t:
+            prev = (t_res["q"], ref[1])
+            out.append((t_res["bytes"], "T"))
+        else:
+            prev = (s_res["q"], s_res["pi"])
+            if first:
+                anchor = prev
+            out.append((s_res["bytes"], "S"))
+    return out
+
+
+def decode_trajectory(containers):
+    """Decodes containers in stream order; returns the list of decoded frames
+    [D, N] in slot order (the slot order of each frame's chain)."""
+    prev_q = None
+    anchor_q = None
+    frames = []
+    for buf in containers:
+        h = oracle.peek(buf)
+        if h["method"] == 0:
+            X, q = oracle.decompress(buf)
+            if h["flags"] & FLAG_FIRST_IN_BATCH:
+                anchor_q = q
+        else:
+            ref = anchor_q if h["flags"] & FLAG_REF_ANCHOR else prev_q
+            X, q = oracle.decompress(buf, ref)
+        prev_q = q
+        frames.append(X)
+    return frames
+
+
+def choose_block_size(X, eb: float, mode="abs", candidates=BLOCK_CANDIDATES,
+                      log2_chunk: int = 10) -> tuple[int, dict]:
+    """Exact compressed size per candidate p; returns (best p, sizes)."""
+    sizes = {}
+    for p in candidates:
+        try:
+            sizes[p] = oracle.compressed_size_s(X, eb, mode, p, log2_chunk)
+        except oracle.OracleError as err:
+            if err.status not in (oracle.ERR_ARG, oracle.ERR_RANGE):
+                raise
+    if not sizes:
+        raise oracle.OracleError(oracle.ERR_RANGE, "choose_block_size")
+    best = min(sizes, key=lambda k: (sizes[k], k))
+    return best, sizes
