@@ -1,0 +1,178 @@
+/*
+ * lcp.h -- C ABI of the B300 LCP library (liblcp.so).
+ *
+ * LCP (arXiv 2411.00761) is an error-bounded lossy compressor for particle
+ * frames.  This library runs its hot path on one GPU:
+ *
+ *   LCP-S  (Sec. "LCP-S: the Error-Bound Aware Block-wise Spatial
+ *          Compressor"): quantize every field into bins of width 2*eb (Eq.
+ *          quantization), group particles into blocks of p bins per axis (Eq.
+ *          block size and id), keep per non-empty block its id, particle count
+ *          and the particles' locations relative to the block corner, delta
+ *          code the three arrays and code each with Huffman or fixed-length
+ *          bits, whichever is shorter (Sec. "Block coding", Table 3).
+ *   LCP-T  (Sec. "LCP-T: The Temporal Compressor"): quantize as LCP-S, predict
+ *          every code from the previous (or anchor) frame, code the
+ *          differences.
+ *   LCP    (Sec. "Hybrid Compression with LCP-S & T", Algorithm 1): per frame
+ *          choice between the two with the LCP-FSM, spatial anchor frames
+ *          opening each batch.
+ *
+ * Conventions shared by every entry point:
+ *   - Frames are field-major ("SoA") float32 arrays [d][n] in DEVICE memory:
+ *     field f of particle i is fields[f * n + i].  d is 1..8 (3 for x, y, z;
+ *     further fields are extra dimensions of the block space, Sec. "Problem
+ *     formulation").  Pointers must be 16-byte aligned.
+ *   - The caller owns every input and output buffer.  The library owns only
+ *     the context's workspace and the trajectory state.
+ *   - Work is queued on the CUDA stream passed as `stream` (a cudaStream_t,
+ *     NULL for the legacy default stream).  Calls that return a size or a
+ *     status computed on the device synchronize that stream before returning.
+ *   - No call aborts or exits.  Every failure is an lcp_status; a failed call
+ *     leaves the output buffer contents unspecified and the trajectory state
+ *     unchanged.
+ *   - A context is not thread-safe: use one per host thread.
+ *
+ * The compressed container ("LCP1") is a byte string in device memory; its
+ * layout is fixed and documented with the library.  Output bytes are a pure
+ * function of the input values, eb, eb mode, p, method and reference state.
+ */
+#ifndef LCP_H
+#define LCP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LCP_API __attribute__((visibility("default")))
+#else
+#define LCP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LCP_OK = 0,
+  LCP_ERR_ARG = -1,       /* invalid argument (d, eb, mode, p, pointer, alignment) */
+  LCP_ERR_NONFINITE = -2, /* a NaN or infinity in the input frame */
+  LCP_ERR_RANGE = -3,     /* frame outside the codec's domain: a field needs
+                             2^30 or more bins, |value| >= 2^32 * 2 eb, or the
+                             block key needs more than 63 bits */
+  LCP_ERR_CAPACITY = -4,  /* output buffer too small; *out_size holds the need */
+  LCP_ERR_FORMAT = -5,    /* malformed container */
+  LCP_ERR_STATE = -6,     /* temporal frame without a matching reference */
+  LCP_ERR_NOMEM = -7,     /* device allocation failed */
+  LCP_ERR_TIMEOUT = -8,   /* a bounded device wait expired */
+  LCP_ERR_CUDA = -9       /* a CUDA runtime call failed */
+} lcp_status;
+
+typedef enum {
+  LCP_EB_ABS = 0, /* eb is the absolute bound of every field (Eq. abs) */
+  LCP_EB_REL = 1  /* eb_f = eb * (max_f - min_f), or eb when the range is 0 */
+} lcp_eb_mode;
+
+typedef enum {
+  LCP_SPATIAL = 0,  /* LCP-S */
+  LCP_TEMPORAL = 1, /* LCP-T against the trajectory's reference */
+  LCP_AUTO = 2      /* LCP-FSM choice (Sec. "Hybrid Compression"), Algorithm 1 */
+} lcp_method;
+
+typedef struct lcp_ctx lcp_ctx;   /* device workspace of one GPU */
+typedef struct lcp_traj lcp_traj; /* per-trajectory reference state (device) */
+
+/* Human-readable name of a status. */
+LCP_API const char *lcp_status_str(lcp_status s);
+
+/* Creates a context on CUDA device `device`.  The workspace grows on demand
+ * (cudaMalloc, which synchronizes the device).  ERR_CUDA if the device is
+ * unusable. */
+LCP_API lcp_status lcp_ctx_create(int device, lcp_ctx **out);
+LCP_API lcp_status lcp_ctx_destroy(lcp_ctx *ctx);
+/* Pre-sizes the workspace for frames of up to n particles of d fields. */
+LCP_API lcp_status lcp_ctx_reserve(lcp_ctx *ctx, uint64_t n, uint32_t d);
+
+/* Upper bound on the container size of a frame of n particles and d fields
+ * (any method). */
+LCP_API size_t lcp_max_compressed_size(uint64_t n, uint32_t d);
+
+/*
+ * Compresses one frame.
+ *   traj == NULL: stateless LCP-S; method must be LCP_SPATIAL or LCP_AUTO
+ *                 (which then means spatial).
+ *   traj != NULL: the frame is the next frame of that trajectory (Algorithm
+ *                 1); LCP_AUTO applies the LCP-FSM, the other methods force
+ *                 one (LCP_TEMPORAL needs a reference: ERR_STATE otherwise).
+ *   eb, mode:     error bound (Eq. abs); the bound used per field is the
+ *                 largest float32 not above eb_f, stored in the container.
+ *   p:            block edge in bins, block_size = 2 eb p (Eq. block size
+ *                 and id); a power of two, p^d <= 2^32.  p == 0 picks the
+ *                 smallest container over p = 2, 4, 8, 16, 32 (Sec. "Best
+ *                 block size"), ties to the smaller p.
+ *   d_out:        device buffer of out_cap bytes; *out_size receives the
+ *                 container size (also on ERR_CAPACITY, then the need).
+ *   chosen:       optional; receives the method used.
+ *   d_perm:       optional device uint32 [n]: for each decoded slot j, the
+ *                 input index of the particle decoded there (the container
+ *                 stores no permutation; decoded order is block order).
+ * Synchronizes `stream`.
+ */
+LCP_API lcp_status lcp_compress(lcp_ctx *ctx, lcp_traj *traj, const float *d_fields, uint64_t n,
+                        uint32_t d, double eb, lcp_eb_mode mode, uint32_t p, lcp_method method,
+                        void *d_out, size_t out_cap, size_t *out_size, lcp_method *chosen,
+                        uint32_t *d_perm, void *stream);
+
+/*
+ * Decompresses one container into d_out [d][n_cap] (field-major, stride n of
+ * the container).  traj (decoder-side trajectory) is needed for LCP-T frames,
+ * whose reference is the previous decoded frame or the last anchor as the
+ * container's flags say; it is updated for the frames that follow.  Decoded
+ * values are in slot order (blocks in id order, then raw outliers).
+ * *n_out / *d_fields receive the frame's shape.  Synchronizes `stream`.
+ */
+LCP_API lcp_status lcp_decompress(lcp_ctx *ctx, lcp_traj *traj, const void *d_in, size_t in_size,
+                          float *d_out, uint64_t n_cap, uint64_t *n_out, uint32_t *d_fields,
+                          void *stream);
+
+/* Reads n, d, method and flags from a container's header (device memory). */
+LCP_API lcp_status lcp_peek(const void *d_in, size_t in_size, uint64_t *n, uint32_t *d,
+                    lcp_method *method, uint32_t *flags, void *stream);
+
+/*
+ * LCP-FSM query (Sec. "Hybrid Compression"): the method the trajectory's next
+ * frame would get, without coding it or changing any state.  *est_s is the
+ * LCP-S size estimate (the size of the most recent LCP-S frame, 0 if none),
+ * *est_t the exact LCP-T size when the FSM tests LCP-T for this frame (0
+ * otherwise).
+ */
+LCP_API lcp_status lcp_select(lcp_ctx *ctx, lcp_traj *traj, const float *d_fields, uint64_t n,
+                      uint32_t d, double eb, lcp_eb_mode mode, lcp_method *chosen,
+                      uint64_t *est_s, uint64_t *est_t, void *stream);
+
+/*
+ * Trajectory state for Algorithm 1: batch_size frames per batch (the first
+ * frame of a batch is predicted from the last spatial anchor frame).  p is
+ * the block multiplier its LCP-S frames use (nonzero).  A trajectory object
+ * is used either for compressing or for decompressing one frame sequence.
+ */
+LCP_API lcp_status lcp_traj_create(lcp_ctx *ctx, uint32_t batch_size, uint32_t p, lcp_traj **out);
+LCP_API lcp_status lcp_traj_destroy(lcp_traj *traj);
+
+/*
+ * Element rules, exposed for verification.  For x[i] (device, n values) of a
+ * field with minimum m and bound e (float32, e > 0 normal):
+ *   q[i]    = floor((x[i] - m) / (2 e))            (Eq. quantization)
+ *   xr[i]   = RN32(m + (2 q[i] + 1) e)             (reverse quantization)
+ *   viol[i] = |x[i] - xr[i]| > e                   (Eq. abs violated)
+ * all over the reals, bit-exact.  Requires x[i] >= m, q < 2^30 and
+ * |x|, |m| < 2^32 * 2e (ERR_RANGE otherwise; checked per call on the host
+ * from m, e and the caller-supplied max_abs bound).
+ */
+LCP_API lcp_status lcp_quantize(const float *d_x, uint64_t n, float m, float e, float max_abs,
+                        int32_t *d_q, float *d_xr, uint8_t *d_viol, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LCP_H */

@@ -243,10 +243,14 @@ int orc_plan(const float *fields, uint64_t n, uint32_t d, double eb, int eb_mode
     plan[f].max_f = mx;
     plan[f].eb_f = ebf;
     plan[f].e = e;
+    /* a quotient estimate at or above 2^31 is certainly out of range (the
+     * exact count below is then skipped); otherwise the exact floor decides */
+    double qest = ((double)mx - (double)mn) / (2.0 * (double)e);
+    if (!(qest < 2147483648.0)) return ORC_ERR_RANGE;
     int64_t qmax = orc_q1(mx, mn, e);
     if (qmax >= (1ll << 30)) return ORC_ERR_RANGE;
     double amax = fmax(fabs((double)mn), fabs((double)mx));
-    if (!(amax < ldexp(2.0 * (double)e, 36))) return ORC_ERR_RANGE;
+    if (!(amax < ldexp(2.0 * (double)e, 32))) return ORC_ERR_RANGE;
     plan[f].qmax = (uint32_t)qmax;
   }
   return ORC_OK;

@@ -1,0 +1,526 @@
+// k_decode.cu -- decompression kernels.
+//
+// Decoding follows the coding chain backwards (Sec. "Block coding"): decode
+// each stream (chunks in parallel), undo the delta coding with scans, place
+// particles block by block and reconstruct every field with Eq. quantization
+// (reverse): x' = (2q + 1) eb + min, rounded once to f32.
+#include <algorithm>
+
+#include "lcp_kernels.h"
+
+namespace lcp {
+
+// ---------------------------------------------------------------------------
+// field plans for decoding (reconstruction and, for raw outliers, Q1)
+// ---------------------------------------------------------------------------
+__global__ void k_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan) {
+  int f = threadIdx.x;
+  if (f < (int)d) {
+    FieldPlan F;
+    int st = plan_field(df->m[f], df->m[f], (double)df->e[f], 0, df->lp, F);
+    F.qmax = df->qmax[f];
+    F.bn = ((unsigned long long)df->qmax[f] >> df->lp) + 1ull;
+    plan->f[f] = F;
+    if (st != OK) atomicCAS(&plan->status, OK, ERR_FORMAT);
+  }
+  if (f == 0) {
+    plan->d = d;
+    plan->lp = df->lp;
+    plan->rel_bits = df->lp * d;
+  }
+  __syncthreads();
+  if (f == 0) {
+    unsigned long long stride = 1ull;
+    for (uint32_t k = 0; k < d; ++k) {
+      plan->f[k].stride = stride;
+      stride *= plan->f[k].bn;
+    }
+  }
+}
+
+void launch_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan, cudaStream_t s) {
+  k_decode_plan<<<1, 32, 0, s>>>(df, d, plan);
+}
+
+// ---------------------------------------------------------------------------
+// Huffman decode tables from the section's (count per length, symbols)
+// ---------------------------------------------------------------------------
+__global__ void k_huff_table(const uint8_t *__restrict__ sec, HuffTable *__restrict__ T) {
+  __shared__ uint32_t cnt[kLmax + 1], first[kLmax + 2], index[kLmax + 2];
+  const uint32_t U = (uint32_t)sec[2] | ((uint32_t)sec[3] << 8);
+  if (threadIdx.x == 0) {
+    uint32_t code = 0, idx = 0, total = 0;
+    for (int L = 1; L <= kLmax; ++L) {
+      cnt[L] = (uint32_t)sec[32 + 2 * (L - 1)] | ((uint32_t)sec[33 + 2 * (L - 1)] << 8);
+      total += cnt[L];
+    }
+    for (int L = 1; L <= kLmax; ++L) {
+      code = (L == 1) ? 0u : (code + cnt[L - 1]) << 1;
+      first[L] = code;
+      index[L] = idx;
+      idx += cnt[L];
+      T->first[L] = code;
+      T->index[L] = index[L];
+      T->count[L] = cnt[L];
+    }
+    T->used = U;
+    T->ok = (total == U && U > 0 && U <= (uint32_t)kAlpha) ? 1u : 0u;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < U && i < (uint32_t)kAlpha; i += blockDim.x)
+    T->syms[i] = (uint16_t)((uint32_t)sec[80 + 2 * i] | ((uint32_t)sec[81 + 2 * i] << 8));
+  // first-level table: codes of up to kFastBits bits, entry = sym << 5 | len
+  for (uint32_t e = threadIdx.x; e < (1u << kFastBits); e += blockDim.x) T->fast[e] = 0u;
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < U && i < (uint32_t)kAlpha; i += blockDim.x) {
+    // length of the i-th symbol in canonical order
+    int L = 1;
+    while (L < kLmax && i >= index[L] + cnt[L]) ++L;
+    if (L > kFastBits) continue;
+    uint32_t code = first[L] + (i - index[L]);
+    uint32_t sym = (uint32_t)sec[80 + 2 * i] | ((uint32_t)sec[81 + 2 * i] << 8);
+    uint32_t lo = code << (kFastBits - L), hi = (code + 1) << (kFastBits - L);
+    for (uint32_t e = lo; e < hi && e < (1u << kFastBits); ++e) T->fast[e] = (sym << 5) | (uint32_t)L;
+  }
+}
+
+void launch_huff_table(const uint8_t *sec, HuffTable *T, cudaStream_t s) {
+  k_huff_table<<<1, 256, 0, s>>>(sec, T);
+}
+
+// ---------------------------------------------------------------------------
+// bit reader over a u32 payload (MSB first); loads past the end read zero
+// ---------------------------------------------------------------------------
+struct BitReader {
+  const uint32_t *pl;
+  unsigned long long nwords, next;
+  unsigned long long win;
+  int nb;  // valid bits in win (left aligned), kept > 32
+  __device__ __forceinline__ uint32_t word(unsigned long long i) const {
+    return i < nwords ? __ldg(pl + i) : 0u;
+  }
+  __device__ __forceinline__ void init(const uint32_t *p, unsigned long long nw,
+                                       unsigned long long pos) {
+    pl = p;
+    nwords = nw;
+    unsigned long long wi = pos >> 5;
+    int off = (int)(pos & 31);
+    win = ((unsigned long long)word(wi) << 32) | word(wi + 1);
+    win <<= off;
+    nb = 64 - off;
+    next = wi + 2;
+    if (nb <= 32) {
+      win |= (unsigned long long)word(next++) << (32 - nb);
+      nb += 32;
+    }
+  }
+  __device__ __forceinline__ uint32_t peek(int n) const {  // 1 <= n <= 32
+    return (uint32_t)(win >> (64 - n));
+  }
+  __device__ __forceinline__ void skip(int n) {  // n <= 32
+    win <<= n;
+    nb -= n;
+    if (nb <= 32) {
+      win |= (unsigned long long)word(next++) << (32 - nb);
+      nb += 32;
+    }
+  }
+  __device__ __forceinline__ unsigned long long read(int n) {  // n <= 64
+    unsigned long long v = 0;
+    if (n > 32) {
+      v = (unsigned long long)peek(n - 32) << 32;
+      skip(n - 32);
+      n = 32;
+    }
+    if (n > 0) {
+      v |= peek(n);
+      skip(n);
+    }
+    return v;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_huff_decode(const uint8_t *__restrict__ sec,
+                                                      StreamInfo info,
+                                                      const HuffTable *__restrict__ HT,
+                                                      T *__restrict__ out, int *__restrict__ err) {
+  __shared__ uint32_t fast[1 << kFastBits];
+  __shared__ uint32_t first[kLmax + 1], index[kLmax + 1], count[kLmax + 1];
+  __shared__ uint16_t syms[kAlpha];
+  for (int i = threadIdx.x; i < (1 << kFastBits); i += blockDim.x) fast[i] = HT->fast[i];
+  for (int i = threadIdx.x; i < (int)HT->used && i < kAlpha; i += blockDim.x) syms[i] = HT->syms[i];
+  if (threadIdx.x <= kLmax) {
+    first[threadIdx.x] = HT->first[threadIdx.x];
+    index[threadIdx.x] = HT->index[threadIdx.x];
+    count[threadIdx.x] = HT->count[threadIdx.x];
+  }
+  __syncthreads();
+  if (!HT->ok) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    return;
+  }
+  const unsigned long long cs = 1ull << info.log2_chunk;
+  const uint8_t *ct = sec + pad16(80ull + 2ull * info.used);
+  const uint32_t *pl = reinterpret_cast<const uint32_t *>(ct + pad16(8ull * info.n_chunks));
+  const unsigned long long nwords = words_of(info.payload_bits);
+  for (unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+       c < info.n_chunks; c += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long lo = c * cs, hi = min(info.n, lo + cs);
+    const unsigned long long pos = (unsigned long long)reinterpret_cast<const uint32_t *>(ct)[2 * c] |
+                                   ((unsigned long long)reinterpret_cast<const uint32_t *>(ct)[2 * c + 1] << 32);
+    if (pos > info.payload_bits) {
+      atomicExch(err, 1);
+      continue;
+    }
+    BitReader br;
+    br.init(pl, nwords, pos);
+    for (unsigned long long i = lo; i < hi; ++i) {
+      uint32_t e = fast[br.peek(kFastBits)];
+      uint32_t sym;
+      if (e) {
+        sym = e >> 5;
+        br.skip((int)(e & 31u));
+      } else {
+        int L = kFastBits + 1;
+        uint32_t code = 0;
+        for (; L <= kLmax; ++L) {
+          code = br.peek(L);
+          if (code - first[L] < count[L]) break;
+        }
+        if (L > kLmax) {
+          atomicExch(err, 1);
+          break;
+        }
+        sym = syms[index[L] + (code - first[L])];
+        br.skip(L);
+      }
+      unsigned long long v = sym;
+      if (sym == (uint32_t)kEsc) v = br.read((int)info.width);
+      out[i] = (T)v;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_fixed_decode(const uint8_t *__restrict__ sec, StreamInfo info,
+                               T *__restrict__ out) {
+  const uint32_t *pl = reinterpret_cast<const uint32_t *>(sec + 32);
+  const uint32_t w = info.width;
+  const unsigned long long nwords = words_of(info.payload_bits);
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < info.n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    if (w == 0) {
+      out[i] = (T)0;
+      continue;
+    }
+    const unsigned long long pos = i * w;
+    const unsigned long long wi = pos >> 5;
+    const int off = (int)(pos & 31);
+    // up to 64 + 31 bits: three words
+    unsigned long long a = __ldg(pl + wi);
+    unsigned long long b = wi + 1 < nwords ? __ldg(pl + wi + 1) : 0u;
+    unsigned long long c = wi + 2 < nwords ? __ldg(pl + wi + 2) : 0u;
+    unsigned long long hi64 = (a << 32) | b;  // bits [wi*32, wi*32+64)
+    unsigned long long v;
+    if (off + (int)w <= 64) {
+      v = (hi64 << off) >> (64 - w);
+    } else {
+      // value spills into the third word
+      unsigned long long top = (hi64 << off);  // 64 - off valid bits at the top
+      int rest = off + (int)w - 64;
+      v = (top >> (64 - w)) | (c >> (32 - rest));
+    }
+    out[i] = (T)v;
+  }
+}
+
+template <typename T>
+static void decode_stream_t(const uint8_t *sec, const StreamInfo &info, HuffTable *ht, T *out,
+                            int *err, int sms, cudaStream_t s) {
+  if (info.n == 0) return;
+  if (info.coder == 0) {
+    unsigned g = (unsigned)std::min<unsigned long long>((info.n + 255) / 256, 8ull * sms);
+    k_fixed_decode<T><<<g, 256, 0, s>>>(sec, info, out);
+  } else {
+    launch_huff_table(sec, ht, s);
+    unsigned g = (unsigned)std::min<unsigned long long>((info.n_chunks + 127) / 128, 64ull * sms);
+    k_huff_decode<T><<<g, 128, 0, s>>>(sec, info, ht, out, err);
+  }
+}
+
+void launch_decode_u64(const uint8_t *sec, const StreamInfo &info, HuffTable *ht,
+                       unsigned long long *out, int *err, int sms, cudaStream_t s) {
+  decode_stream_t<unsigned long long>(sec, info, ht, out, err, sms, s);
+}
+void launch_decode_u32(const uint8_t *sec, const StreamInfo &info, HuffTable *ht, uint32_t *out,
+                       int *err, int sms, cudaStream_t s) {
+  decode_stream_t<uint32_t>(sec, info, ht, out, err, sms, s);
+}
+
+// ---------------------------------------------------------------------------
+// scans over blocks (reduce, scan of tile sums, rescan)
+// ---------------------------------------------------------------------------
+constexpr int kScanTile = 4096;
+
+// mode 0: plain values; mode 1: unzigzag of the values
+template <int MODE>
+__global__ void __launch_bounds__(1024) k_tile_sum(const unsigned long long *__restrict__ in,
+                                                   uint64_t n,
+                                                   unsigned long long *__restrict__ sums) {
+  __shared__ unsigned long long s[32];
+  const uint64_t lo = (uint64_t)blockIdx.x * kScanTile;
+  unsigned long long acc = 0;
+  for (uint64_t i = lo + threadIdx.x; i < min(n, lo + kScanTile); i += blockDim.x) {
+    unsigned long long v = in[i];
+    acc += MODE ? (unsigned long long)unzigzag(v) : v;
+  }
+  for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    acc = s[threadIdx.x];
+    for (int o = 16; o; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) sums[blockIdx.x] = acc;
+  }
+}
+
+// out[i] = base + (inclusive or exclusive) prefix of f(in)
+template <int MODE, bool INCL>
+__global__ void __launch_bounds__(1024) k_tile_scan(const unsigned long long *__restrict__ in,
+                                                    uint64_t n,
+                                                    const unsigned long long *__restrict__ bases,
+                                                    unsigned long long *__restrict__ out) {
+  __shared__ unsigned long long s_warp[32];
+  const uint64_t lo = (uint64_t)blockIdx.x * kScanTile;
+  constexpr int per = kScanTile / 1024;
+  unsigned long long v[per];
+  unsigned long long sum = 0;
+  const uint64_t my = lo + (uint64_t)threadIdx.x * per;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    uint64_t i = my + k;
+    unsigned long long x = i < n ? in[i] : 0ull;
+    v[k] = MODE ? (unsigned long long)unzigzag(x) : x;
+    if (i >= n) v[k] = 0ull;
+    sum += v[k];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long x = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long t = s_warp[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    s_warp[lane] = t;
+  }
+  __syncthreads();
+  unsigned long long run = bases[blockIdx.x] + (w ? s_warp[w - 1] : 0ull) + x - sum;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    uint64_t i = my + k;
+    if (INCL) run += v[k];
+    if (i < n) out[i] = run;
+    if (!INCL) run += v[k];
+  }
+}
+
+void launch_scan_u64(const unsigned long long *in, uint64_t n, int mode, bool inclusive,
+                     unsigned long long *out, unsigned long long *tile_tmp,
+                     unsigned long long *tile_base, cudaStream_t s) {
+  if (n == 0) return;
+  const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (mode) k_tile_sum<1><<<(unsigned)tiles, 1024, 0, s>>>(in, n, tile_tmp);
+  else k_tile_sum<0><<<(unsigned)tiles, 1024, 0, s>>>(in, n, tile_tmp);
+  launch_scan_small(tile_tmp, (uint32_t)tiles, tile_base, s);
+  if (mode) {
+    if (inclusive) k_tile_scan<1, true><<<(unsigned)tiles, 1024, 0, s>>>(in, n, tile_base, out);
+    else k_tile_scan<1, false><<<(unsigned)tiles, 1024, 0, s>>>(in, n, tile_base, out);
+  } else {
+    if (inclusive) k_tile_scan<0, true><<<(unsigned)tiles, 1024, 0, s>>>(in, n, tile_base, out);
+    else k_tile_scan<0, false><<<(unsigned)tiles, 1024, 0, s>>>(in, n, tile_base, out);
+  }
+}
+
+// counts (inclusive scan of count deltas) must be >= 1 and sum to nb
+__global__ void k_check_counts(const unsigned long long *__restrict__ counts, uint64_t m,
+                               const unsigned long long *__restrict__ starts_total, uint64_t nb,
+                               int *__restrict__ err) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    long long c = (long long)counts[i];
+    if (c < 1 || (unsigned long long)c > nb) atomicExch(err, 1);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && *starts_total != nb) atomicExch(err, 1);
+}
+
+void launch_check_counts(const unsigned long long *counts, uint64_t m,
+                         const unsigned long long *starts_total, uint64_t nb, int *err, int sms,
+                         cudaStream_t s) {
+  k_check_counts<<<2 * sms, 256, 0, s>>>(counts, m, starts_total, nb, err);
+}
+
+// ---------------------------------------------------------------------------
+// LCP-S expand + reconstruct: one CTA per chunk of particles
+// ---------------------------------------------------------------------------
+constexpr int kExpThreads = 1024;
+
+template <int D>
+__global__ void __launch_bounds__(kExpThreads) k_expand_s(
+    const Plan *__restrict__ plan, const unsigned long long *__restrict__ bid,
+    const unsigned long long *__restrict__ bstart, uint64_t M, const uint32_t *__restrict__ s_rel,
+    uint64_t nb, uint64_t n, uint32_t log2_chunk, float *__restrict__ out,
+    int32_t *__restrict__ qout, int *__restrict__ err) {
+  __shared__ Plan sP;
+  __shared__ unsigned long long s_first;
+  __shared__ unsigned long long sb_start[kExpThreads + 1];
+  __shared__ uint32_t sb_f[kExpThreads + 1][D];
+  __shared__ uint32_t s_wv[32], s_wf[32];
+  if (threadIdx.x == 0) sP = *plan;
+  // tiles of kExpThreads particles; the chunk size divides the tile, so every
+  // tile starts a chunk (relative locations restart there)
+  const uint64_t cmask = (1ull << log2_chunk) - 1ull;
+  const uint64_t lo = (uint64_t)blockIdx.x * kExpThreads;
+  const uint64_t hi = min(nb, lo + kExpThreads);
+  if (threadIdx.x == 0) {
+    // last block whose start <= lo
+    uint64_t a = 0, b = M;  // answer in [a, b)
+    while (b - a > 1) {
+      uint64_t mid = (a + b) >> 1;
+      if (bstart[mid] <= lo) a = mid;
+      else b = mid;
+    }
+    s_first = a;
+  }
+  __syncthreads();
+  const uint32_t lp = sP.lp;
+  // load the blocks overlapping [lo, hi)
+  const uint64_t bi = s_first + threadIdx.x;
+  bool have = bi < M && bstart[bi] < hi;
+  if (have) {
+    sb_start[threadIdx.x] = bstart[bi];
+    const unsigned long long id = bid[bi];
+#pragma unroll
+    for (int f = 0; f < D; ++f) {
+      const FieldPlan &F = sP.f[f];
+      unsigned long long bf = (id / F.stride) % F.bn;
+      sb_f[threadIdx.x][f] = (uint32_t)(bf << lp);
+    }
+  }
+  const int nblk = __syncthreads_count(have);
+  // particle of this thread
+  const uint64_t k = lo + threadIdx.x;
+  const bool valid = k < hi;
+  int blk = 0;
+  unsigned long long v = 0;
+  bool seg = true;
+  if (valid) {
+    int a = 0, b = nblk;
+    while (b - a > 1) {
+      int mid = (a + b) >> 1;
+      if (sb_start[mid] <= k) a = mid;
+      else b = mid;
+    }
+    blk = a;
+    seg = (k == lo) || (sb_start[blk] == k) || ((k & cmask) == 0);
+    v = s_rel[k];
+  }
+  // segmented inclusive scan of v (segments start at block starts / chunk start)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = (uint32_t)v;
+  uint32_t fl = seg ? 1u : 0u;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    uint32_t g = __shfl_up_sync(0xffffffffu, fl, o);
+    if (lane >= o && !fl) x += y;
+    if (lane >= o) fl |= g;
+  }
+  if (lane == 31) {
+    s_wv[w] = x;
+    s_wf[w] = fl;
+  }
+  __syncthreads();
+  if (w == 0) {
+    uint32_t xv = s_wv[lane], xf = s_wf[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, xv, o);
+      uint32_t g = __shfl_up_sync(0xffffffffu, xf, o);
+      if (lane >= o && !xf) xv += y;
+      if (lane >= o) xf |= g;
+    }
+    s_wv[lane] = xv;  // inclusive carry-out of warps 0..lane
+  }
+  __syncthreads();
+  if (w > 0 && !fl) x += s_wv[w - 1];
+  if (!valid) return;
+  const uint32_t rel = x;
+#pragma unroll
+  for (int f = 0; f < D; ++f) {
+    const FieldPlan &F = sP.f[f];
+    const uint32_t q = sb_f[blk][f] + ((rel >> (f * lp)) & ((1u << lp) - 1u));
+    if (q > F.qmax) atomicExch(err, 1);
+    out[(uint64_t)f * n + k] = reconstruct((long long)q, F);
+    if (qout) qout[(uint64_t)f * n + k] = (int32_t)q;
+  }
+}
+
+template <int D>
+static void expand_t(const Plan *plan, const unsigned long long *bid, const unsigned long long *bstart,
+                     uint64_t M, const uint32_t *s_rel, uint64_t nb, uint64_t n,
+                     uint32_t log2_chunk, float *out, int32_t *qout, int *err, cudaStream_t s) {
+  const uint64_t chunks = (nb + kExpThreads - 1) / kExpThreads;
+  if (chunks == 0) return;
+  k_expand_s<D><<<(unsigned)chunks, kExpThreads, 0, s>>>(plan, bid, bstart, M, s_rel, nb, n,
+                                                        log2_chunk, out, qout, err);
+}
+
+void launch_expand_s(uint32_t d, const Plan *plan, const unsigned long long *bid,
+                     const unsigned long long *bstart, uint64_t M, const uint32_t *s_rel,
+                     uint64_t nb, uint64_t n, uint32_t log2_chunk, float *out, int32_t *qout,
+                     int *err, cudaStream_t s) {
+  switch (d) {
+    case 1: expand_t<1>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 2: expand_t<2>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 3: expand_t<3>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 4: expand_t<4>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 5: expand_t<5>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 6: expand_t<6>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 7: expand_t<7>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    default: expand_t<8>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+  }
+}
+
+// raw outliers of an LCP-S frame go to the last K slots; their codes (for a
+// trajectory reference) are Q1 of the raw values
+__global__ void k_outliers_decode(const Plan *__restrict__ plan, const float *__restrict__ raw,
+                                  uint64_t K, uint64_t n, uint32_t d, float *__restrict__ out,
+                                  int32_t *__restrict__ qout) {
+  const uint64_t nb = n - K;
+  for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < K * d;
+       t += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t f = t / K, j = t % K;
+    float x = raw[f * K + j];
+    out[f * n + nb + j] = x;
+    if (qout) {
+      bool chk;
+      qout[f * n + nb + j] = quantize(x, plan->f[f], chk);
+    }
+  }
+}
+
+void launch_outliers_decode(const Plan *plan, const float *raw, uint64_t K, uint64_t n, uint32_t d,
+                            float *out, int32_t *qout, int sms, cudaStream_t s) {
+  if (K == 0) return;
+  k_outliers_decode<<<2 * sms, 256, 0, s>>>(plan, raw, K, n, d, out, qout);
+}
+
+}  // namespace lcp

@@ -1,0 +1,994 @@
+// lcp_api.cu -- C ABI of the B300 LCP library: contexts, workspace,
+// LCP-S / LCP-T compression and decompression, trajectories (Algorithm 1)
+// with the LCP-FSM selection.
+#include <string.h>
+
+#include <algorithm>
+
+#include "../../include/lcp.h"
+#include "lcp_kernels.h"
+
+using namespace lcp;
+
+namespace {
+
+constexpr uint32_t kLog2Chunk = 10;  // chunk of 1024 symbols
+constexpr uint32_t kFlagFirst = 1u, kFlagRefAnchor = 2u;
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+};
+
+int grow(DevBuf &b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.cap >= bytes) return OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return ERR_NOMEM;
+  }
+  b.cap = bytes;
+  return OK;
+}
+
+template <typename T>
+T *P(DevBuf &b) {
+  return reinterpret_cast<T *>(b.p);
+}
+
+struct Workspace {
+  DevBuf mm, plan, keys, keys2, idx2, idx_alt, tile_hist, btot, bstart, s_rel, tmp_bid, tmp_pos,
+      bblocks, boff, prevne, s_id, s_cnt, hist, maxv, nvals, mcount, kcount, desc, codes, lens,
+      tables, chunk_bits, chunk_off, outl_idx, summary, q_in, q_slot, perm, sym, patch_s,
+      patch_i, patch_x, patch_s2, patch_i2, patch_so, patch_io, dec_fields, hufft, err,
+      scan_tmp, scan_base, bid, counts, starts, cand, tq, fplan, fstatus;
+};
+
+__global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
+__global__ void k_iota(uint32_t *p, const unsigned long long *cnt) {
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < *cnt;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    p[i] = (uint32_t)i;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+#define CK(expr)                        \
+  do {                                  \
+    if ((expr) != cudaSuccess) {        \
+      cudaGetLastError();               \
+      return ERR_CUDA;                  \
+    }                                   \
+  } while (0)
+#define TRY(expr)            \
+  do {                       \
+    int _s = (expr);         \
+    if (_s != OK) return _s; \
+  } while (0)
+
+uint32_t bits_target(uint64_t n) {
+  uint32_t b = 0;
+  while (b < 15 && ((2048ull << b) < n)) ++b;
+  return b;
+}
+
+bool aligned16(const void *p) { return (((uintptr_t)p) & 15u) == 0; }
+
+}  // namespace
+
+struct lcp_ctx {
+  int device = 0;
+  int sms = 148;
+  Workspace ws;
+  Plan *h_plan = nullptr;
+  Summary *h_sum = nullptr;
+  uint8_t *h_stage = nullptr;  // header staging (pinned)
+  int *h_err = nullptr;
+};
+
+struct lcp_traj {
+  lcp_ctx *ctx = nullptr;
+  uint32_t batch = 1, p = 8;
+  uint64_t t = 0;
+  uint64_t n = 0;
+  uint32_t d = 0;
+  bool has_prev = false, has_anchor = false;
+  // LCP-FSM: state 0 = T, else k of S{k}
+  int state = 2, counter = 0;
+  bool s_known = false;
+  uint64_t s_est = 0;
+  DevBuf prev_q, prev_pi, anc_q, anc_pi, new_q, new_pi;
+};
+
+// ===========================================================================
+// internal: LCP-S compression of one frame
+// ===========================================================================
+namespace {
+
+int read_plan(lcp_ctx *c, cudaStream_t s) {
+  CK(cudaMemcpyAsync(c->h_plan, c->ws.plan.p, sizeof(Plan), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return c->h_plan->status;
+}
+
+int read_summary(lcp_ctx *c, cudaStream_t s) {
+  CK(cudaMemcpyAsync(c->h_sum, c->ws.summary.p, sizeof(Summary), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return OK;
+}
+
+int ws_common(lcp_ctx *c, uint64_t n, uint32_t d) {
+  Workspace &w = c->ws;
+  TRY(grow(w.mm, sizeof(MinMax)));
+  TRY(grow(w.plan, sizeof(Plan)));
+  TRY(grow(w.hist, 3ull * kAlpha * 4));
+  TRY(grow(w.maxv, 4 * 8));
+  TRY(grow(w.nvals, 4 * 8));
+  TRY(grow(w.mcount, 8));
+  TRY(grow(w.kcount, 8));
+  TRY(grow(w.desc, 4 * sizeof(StreamDesc)));
+  TRY(grow(w.codes, 3ull * kAlpha * 4));
+  TRY(grow(w.lens, 3ull * kAlpha));
+  TRY(grow(w.tables, 3ull * (kAlpha + 32) * 2));
+  TRY(grow(w.summary, sizeof(Summary)));
+  const uint64_t nd = n * d;
+  const uint64_t chunks = std::max<uint64_t>(nd, n) / 1024 + 2;
+  TRY(grow(w.chunk_bits, chunks * 8));
+  TRY(grow(w.chunk_off, (chunks + 1) * 8));
+  return OK;
+}
+
+int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double eb, int mode,
+                    uint32_t p, uint32_t flags, uint8_t *out, size_t cap, bool size_only,
+                    uint32_t *perm_out, int32_t *q_slot_out, uint64_t *total_out,
+                    cudaStream_t s) {
+  Workspace &w = c->ws;
+  const int sms = c->sms;
+  TRY(ws_common(c, n, d));
+  const bool want_perm = perm_out != nullptr;
+  const bool want_q = q_slot_out != nullptr;
+  // 1-2. min/max and plan
+  launch_minmax(X, n, d, P<MinMax>(w.mm), sms, s);
+  launch_plan(P<MinMax>(w.mm), n, d, eb, mode, p, bits_target(n), 0, P<Plan>(w.plan), s);
+  CK(cudaGetLastError());
+  int st = read_plan(c, s);
+  if (st != OK) return st;
+  const uint32_t nb = 1u << c->h_plan->nbits;
+  const uint32_t nb1 = nb + 1;
+  int tiles = (int)std::min<uint64_t>((uint64_t)(2 * sms), std::max<uint64_t>(1, n / 2048));
+  if ((size_t)nb1 * 4 > 100 * 1024) tiles = std::min(tiles, sms);
+  const uint64_t nn = std::max<uint64_t>(n, 1);
+  TRY(grow(w.keys, nn * 8));
+  TRY(grow(w.keys2, nn * 8));
+  TRY(grow(w.tile_hist, (size_t)tiles * nb1 * 4));
+  TRY(grow(w.btot, (size_t)nb1 * 8));
+  TRY(grow(w.bstart, (size_t)(nb1 + 1) * 8));
+  TRY(grow(w.s_rel, nn * 4));
+  TRY(grow(w.tmp_bid, nn * 8));
+  TRY(grow(w.tmp_pos, nn * 4));
+  TRY(grow(w.bblocks, (size_t)nb1 * 4));
+  TRY(grow(w.boff, (size_t)nb1 * 8));
+  TRY(grow(w.prevne, (size_t)nb1 * 4));
+  TRY(grow(w.s_id, nn * 8));
+  TRY(grow(w.s_cnt, nn * 8));
+  TRY(grow(w.outl_idx, nn * 4));
+  if (want_perm) {
+    TRY(grow(w.idx2, nn * 4));
+    TRY(grow(w.idx_alt, nn * 4));
+  }
+  if (want_q) TRY(grow(w.q_in, nn * 4 * d));
+  // 3. quantize + keys + bucket histograms
+  launch_quantize_s(X, n, d, P<Plan>(w.plan), nb1, tiles, P<unsigned long long>(w.keys),
+                    P<uint32_t>(w.tile_hist), want_q ? P<int32_t>(w.q_in) : nullptr, s);
+  // 4. bucket offsets, 5. scatter
+  launch_bucket_offsets(P<uint32_t>(w.tile_hist), tiles, nb1, P<unsigned long long>(w.bstart),
+                        P<unsigned long long>(w.btot), s);
+  launch_scatter(P<unsigned long long>(w.keys), n, P<Plan>(w.plan), nb1, tiles,
+                 P<uint32_t>(w.tile_hist), P<unsigned long long>(w.keys2),
+                 want_perm ? P<uint32_t>(w.idx2) : nullptr, s);
+  CK(cudaGetLastError());
+  // 6. per-bucket sort + segmentation
+  CK(cudaMemsetAsync(w.hist.p, 0, 3ull * kAlpha * 4, s));
+  CK(cudaMemsetAsync(w.maxv.p, 0, 4 * 8, s));
+  LocalArgs la;
+  la.plan = P<Plan>(w.plan);
+  la.nb1 = nb1;
+  la.bucket_start = P<unsigned long long>(w.bstart);
+  la.keys = P<unsigned long long>(w.keys2);
+  la.idx = want_perm ? P<uint32_t>(w.idx2) : nullptr;
+  la.keys_alt = P<unsigned long long>(w.keys);  // free after the scatter
+  la.idx_alt = want_perm ? P<uint32_t>(w.idx_alt) : nullptr;
+  la.s_rel = P<uint32_t>(w.s_rel);
+  la.tmp_bid = P<unsigned long long>(w.tmp_bid);
+  la.tmp_pos = P<uint32_t>(w.tmp_pos);
+  la.bucket_blocks = P<uint32_t>(w.bblocks);
+  la.hist = P<uint32_t>(w.hist);
+  la.maxv = P<unsigned long long>(w.maxv);
+  la.perm = want_perm ? perm_out : nullptr;
+  la.q_in = want_q ? P<int32_t>(w.q_in) : nullptr;
+  la.q_slot = want_q ? q_slot_out : nullptr;
+  la.outl_idx = P<uint32_t>(w.outl_idx);
+  la.log2_chunk = kLog2Chunk;
+  la.n = n;
+  launch_local(la, sms, s);
+  CK(cudaGetLastError());
+  // 7. blocks: ids and counts
+  launch_blocks(P<Plan>(w.plan), nb1, P<unsigned long long>(w.bstart), P<uint32_t>(w.bblocks),
+                P<unsigned long long>(w.tmp_bid), P<uint32_t>(w.tmp_pos),
+                P<unsigned long long>(w.boff), P<int>(w.prevne), P<unsigned long long>(w.s_id),
+                P<unsigned long long>(w.s_cnt), P<uint32_t>(w.hist),
+                P<unsigned long long>(w.maxv), P<unsigned long long>(w.mcount), 2 * sms, s);
+  launch_counts_s(P<unsigned long long>(w.bstart), nb, n, P<unsigned long long>(w.mcount),
+                  P<unsigned long long>(w.nvals), P<unsigned long long>(w.kcount), s);
+  // 8. codebooks and the container layout
+  launch_codebook(3, P<uint32_t>(w.hist), P<unsigned long long>(w.maxv),
+                  P<unsigned long long>(w.nvals), kLog2Chunk, P<StreamDesc>(w.desc),
+                  P<uint32_t>(w.codes), P<uint8_t>(w.lens), P<uint16_t>(w.tables), s);
+  LayoutArgs L;
+  L.method = 0;
+  L.d = d;
+  L.log2_chunk = kLog2Chunk;
+  L.flags = flags;
+  L.p = p;
+  L.n = n;
+  L.plan = P<Plan>(w.plan);
+  L.desc = P<StreamDesc>(w.desc);
+  L.tables = P<uint16_t>(w.tables);
+  L.mcount = P<unsigned long long>(w.mcount);
+  L.kcount = P<unsigned long long>(w.kcount);
+  L.out = out;
+  L.cap = size_only ? ~0ull : cap;
+  L.summary = P<Summary>(w.summary);
+  launch_layout(L, sms, size_only, s);
+  CK(cudaGetLastError());
+  if (!size_only) {
+    // 9. payloads
+    StreamDesc *D = P<StreamDesc>(w.desc);
+    launch_encode_u64(P<unsigned long long>(w.s_id), n, D + 0, P<uint32_t>(w.codes),
+                      P<uint8_t>(w.lens), kLog2Chunk, out, P<Summary>(w.summary),
+                      P<unsigned long long>(w.chunk_bits), P<unsigned long long>(w.chunk_off), sms,
+                      s);
+    launch_encode_u64(P<unsigned long long>(w.s_cnt), n, D + 1, P<uint32_t>(w.codes) + kAlpha,
+                      P<uint8_t>(w.lens) + kAlpha, kLog2Chunk, out, P<Summary>(w.summary),
+                      P<unsigned long long>(w.chunk_bits), P<unsigned long long>(w.chunk_off), sms,
+                      s);
+    launch_encode_u32(P<uint32_t>(w.s_rel), n, D + 2, P<uint32_t>(w.codes) + 2 * kAlpha,
+                      P<uint8_t>(w.lens) + 2 * kAlpha, kLog2Chunk, out, P<Summary>(w.summary),
+                      P<unsigned long long>(w.chunk_bits), P<unsigned long long>(w.chunk_off), sms,
+                      s);
+    launch_outliers_s(X, n, d, P<uint32_t>(w.outl_idx), D + 3, out, P<Summary>(w.summary), sms, s);
+    CK(cudaGetLastError());
+  }
+  TRY(read_summary(c, s));
+  *total_out = c->h_sum->total;
+  return c->h_sum->status;
+}
+
+// ===========================================================================
+// internal: LCP-T compression of one frame against (qref, pi)
+// ===========================================================================
+int compress_t_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double eb, int mode,
+                    const uint32_t *pi, const int32_t *qref, uint32_t flags, uint8_t *out,
+                    size_t cap, bool size_only, int32_t *qnew, uint64_t *total_out,
+                    cudaStream_t s) {
+  Workspace &w = c->ws;
+  const int sms = c->sms;
+  TRY(ws_common(c, n, d));
+  const uint64_t nd = std::max<uint64_t>(n * d, 1);
+  TRY(grow(w.sym, nd * 4));
+  TRY(grow(w.patch_s, nd * 8));
+  TRY(grow(w.patch_x, nd * 4));
+  launch_minmax(X, n, d, P<MinMax>(w.mm), sms, s);
+  launch_plan(P<MinMax>(w.mm), n, d, eb, mode, 0, 0, 1, P<Plan>(w.plan), s);
+  CK(cudaGetLastError());
+  int st = read_plan(c, s);
+  if (st != OK) return st;
+  CK(cudaMemsetAsync(w.hist.p, 0, 3ull * kAlpha * 4, s));
+  CK(cudaMemsetAsync(w.maxv.p, 0, 4 * 8, s));
+  CK(cudaMemsetAsync(w.kcount.p, 0, 8, s));
+  CK(cudaMemsetAsync(w.mcount.p, 0, 8, s));
+  launch_quantize_t(X, n, d, P<Plan>(w.plan), pi, qref, P<uint32_t>(w.sym), qnew,
+                    P<uint32_t>(w.hist), P<unsigned long long>(w.maxv),
+                    P<unsigned long long>(w.kcount), P<unsigned long long>(w.patch_s),
+                    P<float>(w.patch_x), sms, s);
+  k_set_u64<<<1, 1, 0, s>>>(P<unsigned long long>(w.nvals), (unsigned long long)(n * d));
+  launch_codebook(1, P<uint32_t>(w.hist), P<unsigned long long>(w.maxv),
+                  P<unsigned long long>(w.nvals), kLog2Chunk, P<StreamDesc>(w.desc),
+                  P<uint32_t>(w.codes), P<uint8_t>(w.lens), P<uint16_t>(w.tables), s);
+  LayoutArgs L;
+  L.method = 1;
+  L.d = d;
+  L.log2_chunk = kLog2Chunk;
+  L.flags = flags;
+  L.p = 0;
+  L.n = n;
+  L.plan = P<Plan>(w.plan);
+  L.desc = P<StreamDesc>(w.desc);
+  L.tables = P<uint16_t>(w.tables);
+  L.mcount = P<unsigned long long>(w.mcount);
+  L.kcount = P<unsigned long long>(w.kcount);
+  L.out = out;
+  L.cap = size_only ? ~0ull : cap;
+  L.summary = P<Summary>(w.summary);
+  launch_layout(L, sms, size_only, s);
+  CK(cudaGetLastError());
+  if (!size_only) {
+    StreamDesc *D = P<StreamDesc>(w.desc);
+    launch_encode_u32(P<uint32_t>(w.sym), n * d, D + 0, P<uint32_t>(w.codes), P<uint8_t>(w.lens),
+                      kLog2Chunk, out, P<Summary>(w.summary),
+                      P<unsigned long long>(w.chunk_bits), P<unsigned long long>(w.chunk_off), sms,
+                      s);
+    // patches in increasing symbol index
+    TRY(grow(w.patch_i, nd * 4));
+    TRY(grow(w.patch_s2, nd * 8));
+    TRY(grow(w.patch_i2, nd * 4));
+    TRY(grow(w.patch_so, nd * 8));
+    TRY(grow(w.patch_io, nd * 4));
+    k_iota<<<sms, 256, 0, s>>>(P<uint32_t>(w.patch_i), P<unsigned long long>(w.kcount));
+    int kbits = (int)bitlen64(n * d > 0 ? n * d - 1 : 0);
+    launch_sort_pairs(P<unsigned long long>(w.patch_s), P<uint32_t>(w.patch_i),
+                      P<unsigned long long>(w.patch_s2), P<uint32_t>(w.patch_i2),
+                      P<unsigned long long>(w.kcount), kbits, P<unsigned long long>(w.patch_so),
+                      P<uint32_t>(w.patch_io), s);
+    launch_patches_write(P<unsigned long long>(w.patch_so), P<uint32_t>(w.patch_io),
+                         P<float>(w.patch_x), D + 1, out, P<Summary>(w.summary), sms, s);
+    CK(cudaGetLastError());
+  }
+  TRY(read_summary(c, s));
+  *total_out = c->h_sum->total;
+  return c->h_sum->status;
+}
+
+int check_frame_args(const void *X, uint64_t n, uint32_t d, double eb, int mode) {
+  if (d < 1 || d > 8) return ERR_ARG;
+  if (n >= (1ull << 32)) return ERR_ARG;
+  if (n > 0 && (!X || !aligned16(X))) return ERR_ARG;
+  if (!(eb > 0.0) || eb != eb || eb > 1e308) return ERR_ARG;
+  if (mode != LCP_EB_ABS && mode != LCP_EB_REL) return ERR_ARG;
+  return OK;
+}
+
+int check_p(uint32_t p, uint32_t d) {
+  if (p == 0 || p > 65536 || (p & (p - 1))) return ERR_ARG;
+  uint32_t lp = 0;
+  while ((1u << lp) < p) ++lp;
+  if (lp * d > 32) return ERR_ARG;
+  return OK;
+}
+
+// p == 0: exact size for each candidate, smallest wins, ties to the smaller p
+int choose_p(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double eb, int mode,
+             uint32_t *best, cudaStream_t s) {
+  const uint32_t cands[5] = {2, 4, 8, 16, 32};
+  uint64_t best_size = ~0ull;
+  int last = ERR_RANGE;
+  *best = 0;
+  for (uint32_t p : cands) {
+    if (check_p(p, d) != OK) continue;
+    uint64_t total = 0;
+    int st = compress_s_impl(c, X, n, d, eb, mode, p, 0, nullptr, 0, true, nullptr, nullptr,
+                             &total, s);
+    if (st == ERR_RANGE || st == ERR_ARG) {
+      last = st;
+      continue;
+    }
+    if (st != OK) return st;
+    if (total < best_size) {
+      best_size = total;
+      *best = p;
+    }
+  }
+  return *best ? OK : last;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *lcp_status_str(lcp_status s) {
+  switch (s) {
+    case LCP_OK: return "ok";
+    case LCP_ERR_ARG: return "invalid argument";
+    case LCP_ERR_NONFINITE: return "non-finite input value";
+    case LCP_ERR_RANGE: return "frame outside the codec's domain";
+    case LCP_ERR_CAPACITY: return "output buffer too small";
+    case LCP_ERR_FORMAT: return "malformed container";
+    case LCP_ERR_STATE: return "temporal frame without a matching reference";
+    case LCP_ERR_NOMEM: return "device allocation failed";
+    case LCP_ERR_TIMEOUT: return "bounded device wait expired";
+    case LCP_ERR_CUDA: return "CUDA runtime error";
+  }
+  return "unknown status";
+}
+
+lcp_status lcp_ctx_create(int device, lcp_ctx **out) {
+  if (!out) return LCP_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return LCP_ERR_CUDA;
+  }
+  DeviceGuard g(device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  lcp_ctx *c = new lcp_ctx();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMallocHost(&c->h_plan, sizeof(Plan)) != cudaSuccess ||
+      cudaMallocHost(&c->h_sum, sizeof(Summary)) != cudaSuccess ||
+      cudaMallocHost(&c->h_stage, 8192) != cudaSuccess ||
+      cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    lcp_ctx_destroy(c);
+    return LCP_ERR_NOMEM;
+  }
+  *out = c;
+  return LCP_OK;
+}
+
+lcp_status lcp_ctx_destroy(lcp_ctx *c) {
+  if (!c) return LCP_ERR_ARG;
+  DeviceGuard g(c->device);
+  DevBuf *bufs = reinterpret_cast<DevBuf *>(&c->ws);
+  for (size_t i = 0; i < sizeof(Workspace) / sizeof(DevBuf); ++i)
+    if (bufs[i].p) cudaFree(bufs[i].p);
+  if (c->h_plan) cudaFreeHost(c->h_plan);
+  if (c->h_sum) cudaFreeHost(c->h_sum);
+  if (c->h_stage) cudaFreeHost(c->h_stage);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  delete c;
+  return LCP_OK;
+}
+
+size_t lcp_max_compressed_size(uint64_t n, uint32_t d) {
+  return (size_t)(48ull + 16ull * d + 64ull + 256ull + (24ull + 16ull * d) * n);
+}
+
+lcp_status lcp_ctx_reserve(lcp_ctx *c, uint64_t n, uint32_t d) {
+  if (!c || d < 1 || d > 8) return LCP_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  int st = ws_common(c, n, d);
+  Workspace &w = c->ws;
+  const uint64_t nn = std::max<uint64_t>(n, 1);
+  if (st == OK) st = grow(w.keys, nn * 8);
+  if (st == OK) st = grow(w.keys2, nn * 8);
+  if (st == OK) st = grow(w.s_rel, nn * 4);
+  if (st == OK) st = grow(w.tmp_bid, nn * 8);
+  if (st == OK) st = grow(w.tmp_pos, nn * 4);
+  if (st == OK) st = grow(w.s_id, nn * 8);
+  if (st == OK) st = grow(w.s_cnt, nn * 8);
+  if (st == OK) st = grow(w.outl_idx, nn * 4);
+  return (lcp_status)st;
+}
+
+// ---------------------------------------------------------------------------
+// trajectories
+// ---------------------------------------------------------------------------
+lcp_status lcp_traj_create(lcp_ctx *c, uint32_t batch_size, uint32_t p, lcp_traj **out) {
+  if (!c || !out || batch_size == 0 || p == 0 || (p & (p - 1)) || p > 65536) return LCP_ERR_ARG;
+  lcp_traj *t = new lcp_traj();
+  t->ctx = c;
+  t->batch = batch_size;
+  t->p = p;
+  *out = t;
+  return LCP_OK;
+}
+
+lcp_status lcp_traj_destroy(lcp_traj *t) {
+  if (!t) return LCP_ERR_ARG;
+  DeviceGuard g(t->ctx->device);
+  DevBuf *bufs[] = {&t->prev_q, &t->prev_pi, &t->anc_q, &t->anc_pi, &t->new_q, &t->new_pi};
+  for (DevBuf *b : bufs)
+    if (b->p) cudaFree(b->p);
+  delete t;
+  return LCP_OK;
+}
+
+namespace {
+
+enum Action { A_SPATIAL, A_COMPARE, A_TEST, A_TEMPORAL };
+
+struct FsmCopy {
+  int state, counter;
+  bool s_known;
+  uint64_t s_est;
+};
+
+// the LCP-FSM decision for the next frame (mutates only the copy)
+Action fsm_plan(FsmCopy &f, bool has_ref) {
+  if (!has_ref) return A_SPATIAL;
+  if (!f.s_known) return A_COMPARE;
+  if (f.state == 0) return A_TEST;
+  f.counter += 1;
+  if (f.counter >= f.state) {
+    f.counter = 0;
+    return A_TEST;
+  }
+  return A_SPATIAL;
+}
+
+int traj_buffers(lcp_traj *t, uint64_t n, uint32_t d) {
+  const size_t qb = std::max<uint64_t>(n * d, 1) * 4, pb = std::max<uint64_t>(n, 1) * 4;
+  TRY(grow(t->prev_q, qb));
+  TRY(grow(t->prev_pi, pb));
+  TRY(grow(t->anc_q, qb));
+  TRY(grow(t->anc_pi, pb));
+  TRY(grow(t->new_q, qb));
+  TRY(grow(t->new_pi, pb));
+  return OK;
+}
+
+// compress the next frame of a trajectory (Algorithm 1)
+int traj_compress(lcp_ctx *c, lcp_traj *t, const float *X, uint64_t n, uint32_t d, double eb,
+                  int mode, int method, uint8_t *out, size_t cap, size_t *out_size,
+                  int *chosen, bool commit, uint64_t *est_s, uint64_t *est_t, cudaStream_t s) {
+  if (t->has_prev && (n != t->n || d != t->d)) return ERR_STATE;
+  TRY(check_p(t->p, d));
+  TRY(traj_buffers(t, n, d));
+  Workspace &w = c->ws;
+  const bool first = (t->t % t->batch) == 0;
+  const bool ref_anchor = first;
+  const bool has_ref = first ? t->has_anchor : t->has_prev;
+  const int32_t *rq = ref_anchor ? P<int32_t>(t->anc_q) : P<int32_t>(t->prev_q);
+  const uint32_t *rpi = ref_anchor ? P<uint32_t>(t->anc_pi) : P<uint32_t>(t->prev_pi);
+  const uint32_t sflags = first ? kFlagFirst : 0u;
+  const uint32_t tflags = sflags | (ref_anchor ? kFlagRefAnchor : 0u);
+  FsmCopy f{t->state, t->counter, t->s_known, t->s_est};
+  Action a;
+  if (method == LCP_SPATIAL) a = A_SPATIAL;
+  else if (method == LCP_TEMPORAL) {
+    if (!has_ref) return ERR_STATE;
+    a = A_TEMPORAL;
+  } else a = fsm_plan(f, has_ref);
+  const size_t qb = std::max<uint64_t>(n * d, 1) * 4;
+  TRY(grow(w.tq, qb));
+  TRY(grow(w.cand, lcp_max_compressed_size(n, d)));
+  bool use_t = false;
+  uint64_t s_size = 0, t_size = 0;
+  const bool size_only = !commit;
+  if (a == A_SPATIAL) {
+    TRY(compress_s_impl(c, X, n, d, eb, mode, t->p, sflags, out, cap, size_only,
+                        P<uint32_t>(t->new_pi), P<int32_t>(t->new_q), &s_size, s));
+    if (a == A_SPATIAL && method == LCP_AUTO) f.s_known = true, f.s_est = s_size;
+    if (method != LCP_AUTO) f.s_known = true, f.s_est = s_size;
+  } else if (a == A_TEMPORAL) {
+    TRY(compress_t_impl(c, X, n, d, eb, mode, rpi, rq, tflags, out, cap, size_only,
+                        P<int32_t>(w.tq), &t_size, s));
+    use_t = true;
+  } else if (a == A_COMPARE) {
+    TRY(compress_s_impl(c, X, n, d, eb, mode, t->p, sflags, out, cap, size_only,
+                        P<uint32_t>(t->new_pi), P<int32_t>(t->new_q), &s_size, s));
+    int st = compress_t_impl(c, X, n, d, eb, mode, rpi, rq, tflags, P<uint8_t>(w.cand),
+                             w.cand.cap, size_only, P<int32_t>(w.tq), &t_size, s);
+    if (st != OK) return st;
+    use_t = t_size < s_size;
+    f.s_known = true;
+    f.s_est = s_size;
+    f.state = use_t ? 0 : 2;
+    f.counter = 0;
+    if (use_t && commit) {
+      if (t_size > cap) {
+        *out_size = t_size;
+        return ERR_CAPACITY;
+      }
+      CK(cudaMemcpyAsync(out, w.cand.p, t_size, cudaMemcpyDeviceToDevice, s));
+    }
+  } else {  // A_TEST: LCP-T against the LCP-S estimate
+    int st = compress_t_impl(c, X, n, d, eb, mode, rpi, rq, tflags, out, cap, size_only,
+                             P<int32_t>(w.tq), &t_size, s);
+    if (st != OK && st != ERR_CAPACITY) return st;
+    use_t = t_size <= f.s_est;
+    if (use_t && st == ERR_CAPACITY) {
+      *out_size = t_size;
+      return ERR_CAPACITY;
+    }
+    if (!use_t) {
+      TRY(compress_s_impl(c, X, n, d, eb, mode, t->p, sflags, out, cap, size_only,
+                          P<uint32_t>(t->new_pi), P<int32_t>(t->new_q), &s_size, s));
+      f.s_est = s_size;
+    }
+    if (use_t) f.state = 0;
+    else f.state = (f.state == 0) ? 2 : std::min(2 * f.state, 16);
+    f.counter = 0;
+  }
+  *out_size = use_t ? t_size : s_size;
+  if (chosen) *chosen = use_t ? LCP_TEMPORAL : LCP_SPATIAL;
+  if (est_s) *est_s = (a == A_COMPARE) ? s_size : (f.s_known ? t->s_est : 0);
+  if (est_t) *est_t = t_size;
+  if (!commit) return OK;
+  // commit the reference state
+  if (use_t) {
+    std::swap(t->prev_q, w.tq);
+    if (ref_anchor)
+      CK(cudaMemcpyAsync(t->prev_pi.p, t->anc_pi.p, std::max<uint64_t>(n, 1) * 4,
+                         cudaMemcpyDeviceToDevice, s));
+  } else {
+    std::swap(t->prev_q, t->new_q);
+    std::swap(t->prev_pi, t->new_pi);
+    if (first) {
+      CK(cudaMemcpyAsync(t->anc_q.p, t->prev_q.p, qb, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(t->anc_pi.p, t->prev_pi.p, std::max<uint64_t>(n, 1) * 4,
+                         cudaMemcpyDeviceToDevice, s));
+      t->has_anchor = true;
+    }
+  }
+  CK(cudaStreamSynchronize(s));
+  t->has_prev = true;
+  t->n = n;
+  t->d = d;
+  t->t += 1;
+  t->state = f.state;
+  t->counter = f.counter;
+  t->s_known = f.s_known;
+  t->s_est = f.s_est;
+  return OK;
+}
+
+}  // namespace
+
+lcp_status lcp_compress(lcp_ctx *c, lcp_traj *traj, const float *d_fields, uint64_t n, uint32_t d,
+                        double eb, lcp_eb_mode mode, uint32_t p, lcp_method method, void *d_out,
+                        size_t out_cap, size_t *out_size, lcp_method *chosen, uint32_t *d_perm,
+                        void *stream) {
+  if (!c || !out_size) return LCP_ERR_ARG;
+  *out_size = 0;
+  int st = check_frame_args(d_fields, n, d, eb, mode);
+  if (st != OK) return (lcp_status)st;
+  if (!d_out || !aligned16(d_out)) return LCP_ERR_ARG;
+  if (method != LCP_SPATIAL && method != LCP_TEMPORAL && method != LCP_AUTO) return LCP_ERR_ARG;
+  if (!traj && method == LCP_TEMPORAL) return LCP_ERR_STATE;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (traj) {
+    int ch = LCP_SPATIAL;
+    st = traj_compress(c, traj, d_fields, n, d, eb, mode, method, (uint8_t *)d_out, out_cap,
+                       out_size, &ch, true, nullptr, nullptr, s);
+    if (chosen) *chosen = (lcp_method)ch;
+    if (st == OK && d_perm) {
+      const void *src = (ch == LCP_SPATIAL) ? traj->prev_pi.p : traj->prev_pi.p;
+      if (cudaMemcpyAsync(d_perm, src, n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return LCP_ERR_CUDA;
+    }
+    return (lcp_status)st;
+  }
+  if (p == 0) {
+    st = choose_p(c, d_fields, n, d, eb, mode, &p, s);
+    if (st != OK) return (lcp_status)st;
+  } else {
+    st = check_p(p, d);
+    if (st != OK) return (lcp_status)st;
+  }
+  uint64_t total = 0;
+  st = compress_s_impl(c, d_fields, n, d, eb, mode, p, 0, (uint8_t *)d_out, out_cap, false, d_perm,
+                       nullptr, &total, s);
+  *out_size = total;
+  if (chosen) *chosen = LCP_SPATIAL;
+  return (lcp_status)st;
+}
+
+lcp_status lcp_select(lcp_ctx *c, lcp_traj *traj, const float *d_fields, uint64_t n, uint32_t d,
+                      double eb, lcp_eb_mode mode, lcp_method *chosen, uint64_t *est_s,
+                      uint64_t *est_t, void *stream) {
+  if (!c || !traj || !chosen) return LCP_ERR_ARG;
+  int st = check_frame_args(d_fields, n, d, eb, mode);
+  if (st != OK) return (lcp_status)st;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  size_t sz = 0;
+  int ch = LCP_SPATIAL;
+  uint64_t es = 0, et = 0;
+  st = traj_compress(c, traj, d_fields, n, d, eb, mode, LCP_AUTO, nullptr, 0, &sz, &ch, false,
+                     &es, &et, (cudaStream_t)stream);
+  if (st != OK) return (lcp_status)st;
+  *chosen = (lcp_method)ch;
+  if (est_s) *est_s = es;
+  if (est_t) *est_t = et;
+  return LCP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// decompression
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_counts_total(const unsigned long long *starts, const unsigned long long *counts,
+                               uint64_t M, unsigned long long *total) {
+  *total = M ? starts[M - 1] + counts[M - 1] : 0ull;
+}
+
+inline uint64_t rd64(const uint8_t *p) {
+  uint64_t v;
+  memcpy(&v, p, 8);
+  return v;
+}
+inline uint32_t rd32(const uint8_t *p) {
+  uint32_t v;
+  memcpy(&v, p, 4);
+  return v;
+}
+
+struct Header {
+  int method;
+  uint32_t d, log2_chunk, flags, p, lp;
+  uint64_t n, K, M, total;
+  float m[kMaxD], e[kMaxD];
+  uint32_t qmax[kMaxD];
+  uint64_t off[4], bytes[4];
+  StreamInfo si[3];
+  int ns;
+};
+
+int read_header(lcp_ctx *c, const uint8_t *in, size_t in_size, Header &h, cudaStream_t s) {
+  if (!in || !aligned16(in) || in_size < 48) return ERR_FORMAT;
+  uint8_t *st = c->h_stage;
+  CK(cudaMemcpyAsync(st, in, 48, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (st[0] != 'L' || st[1] != 'C' || st[2] != 'P' || st[3] != '1' || st[4] != 1) return ERR_FORMAT;
+  h.method = st[5];
+  h.d = st[6];
+  h.log2_chunk = st[7];
+  if (h.method > 1 || h.d < 1 || h.d > 8) return ERR_FORMAT;
+  if (h.log2_chunk < 5 || h.log2_chunk > 10) return ERR_FORMAT;
+  h.flags = rd32(st + 8);
+  h.p = rd32(st + 12);
+  h.n = rd64(st + 16);
+  h.K = rd64(st + 24);
+  h.M = rd64(st + 32);
+  h.total = rd64(st + 40);
+  h.ns = h.method == 0 ? 3 : 1;
+  const uint64_t H = 48ull + 16ull * h.d + 16ull * h.ns + 16ull;
+  if (h.total > in_size || h.total < H || h.n >= (1ull << 32)) return ERR_FORMAT;
+  CK(cudaMemcpyAsync(st, in, H, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (uint32_t f = 0; f < h.d; ++f) {
+    memcpy(&h.m[f], st + 48 + 16 * f, 4);
+    memcpy(&h.e[f], st + 52 + 16 * f, 4);
+    h.qmax[f] = rd32(st + 56 + 16 * f);
+    if (h.qmax[f] >= (1u << 30)) return ERR_FORMAT;
+  }
+  for (int k = 0; k <= h.ns; ++k) {
+    h.off[k] = rd64(st + 48 + 16 * h.d + 16 * k);
+    h.bytes[k] = rd64(st + 48 + 16 * h.d + 16 * k + 8);
+    if (h.off[k] < H || h.off[k] > h.total || h.bytes[k] > h.total - h.off[k] || (h.off[k] & 15))
+      return ERR_FORMAT;
+  }
+  h.lp = 0;
+  if (h.method == 0) {
+    if (h.p == 0 || (h.p & (h.p - 1)) || h.p > 65536) return ERR_FORMAT;
+    while ((1u << h.lp) < h.p) ++h.lp;
+    if (h.lp * h.d > 32 || h.K > h.n || h.M > h.n - h.K) return ERR_FORMAT;
+    if (h.bytes[3] != pad16(4ull * h.d * h.K)) return ERR_FORMAT;
+    if ((h.M == 0) != (h.n == h.K)) return ERR_FORMAT;
+  } else {
+    if (h.bytes[1] != pad16(8ull * h.K) + pad16(4ull * h.K) || h.K > h.n * h.d) return ERR_FORMAT;
+  }
+  for (int k = 0; k < h.ns; ++k) {
+    if (h.bytes[k] < 32) return ERR_FORMAT;
+    CK(cudaMemcpyAsync(st + 4096 + 32 * k, in + h.off[k], 32, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < h.ns; ++k) {
+    const uint8_t *sh = st + 4096 + 32 * k;
+    StreamInfo &I = h.si[k];
+    I.coder = sh[0];
+    I.width = sh[1];
+    I.used = (uint32_t)sh[2] | ((uint32_t)sh[3] << 8);
+    I.n = rd64(sh + 8);
+    I.payload_bits = rd64(sh + 16);
+    I.maxv = rd64(sh + 24);
+    I.log2_chunk = h.log2_chunk;
+    const uint64_t want = h.method == 0 ? (k < 2 ? h.M : h.n - h.K) : h.n * h.d;
+    if (I.n != want || I.width > 64 || I.coder > 1) return ERR_FORMAT;
+    if (h.method == 0 && k == 2 && I.width > 32) return ERR_FORMAT;  // relative codes < 2^32
+    if (h.method == 1 && I.width > 32) return ERR_FORMAT;
+    if (I.coder == 0) {
+      I.n_chunks = 0;
+      if (I.payload_bits != I.n * I.width) return ERR_FORMAT;
+      if (h.bytes[k] != 32 + pad16(4 * words_of(I.payload_bits))) return ERR_FORMAT;
+    } else {
+      if (I.used == 0 || I.used > (uint32_t)kAlpha) return ERR_FORMAT;
+      I.n_chunks = (I.n + (1ull << h.log2_chunk) - 1) >> h.log2_chunk;
+      if (h.bytes[k] != pad16(80ull + 2ull * I.used) + pad16(8 * I.n_chunks) +
+                            pad16(4 * words_of(I.payload_bits)))
+        return ERR_FORMAT;
+    }
+  }
+  return OK;
+}
+
+int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, float *out,
+                    uint64_t n_cap, uint64_t *n_out, uint32_t *d_out, cudaStream_t s) {
+  Header h;
+  TRY(read_header(c, in, in_size, h, s));
+  if (n_out) *n_out = h.n;
+  if (d_out) *d_out = h.d;
+  if (h.n > n_cap) return ERR_CAPACITY;
+  if (h.n > 0 && (!out || !aligned16(out))) return ERR_ARG;
+  const bool first = (h.flags & kFlagFirst) != 0;
+  const bool ra = (h.flags & kFlagRefAnchor) != 0;
+  if (h.method == 1) {
+    if (!t) return ERR_STATE;
+    if (!(ra ? t->has_anchor : t->has_prev) || t->n != h.n || t->d != h.d) return ERR_STATE;
+  }
+  Workspace &w = c->ws;
+  const int sms = c->sms;
+  const uint64_t n = h.n, nn = std::max<uint64_t>(n, 1);
+  TRY(grow(w.plan, sizeof(Plan)));
+  TRY(grow(w.dec_fields, sizeof(DecodeFields)));
+  TRY(grow(w.hufft, 3 * sizeof(HuffTable)));
+  TRY(grow(w.err, 8));
+  if (t) TRY(traj_buffers(t, n, h.d));
+  DecodeFields *hf = reinterpret_cast<DecodeFields *>(c->h_stage + 6144);
+  memset(hf, 0, sizeof(DecodeFields));
+  for (uint32_t f = 0; f < h.d; ++f) {
+    hf->m[f] = h.m[f];
+    hf->e[f] = h.e[f];
+    hf->qmax[f] = h.qmax[f];
+  }
+  hf->lp = h.lp;
+  CK(cudaMemsetAsync(w.plan.p, 0, sizeof(Plan), s));
+  CK(cudaMemsetAsync(w.err.p, 0, 8, s));
+  CK(cudaMemcpyAsync(w.dec_fields.p, hf, sizeof(DecodeFields), cudaMemcpyHostToDevice, s));
+  launch_decode_plan(P<DecodeFields>(w.dec_fields), h.d, P<Plan>(w.plan), s);
+  int *err = P<int>(w.err);
+  HuffTable *ht = P<HuffTable>(w.hufft);
+  int32_t *qout = t ? P<int32_t>(t->new_q) : nullptr;
+  if (h.method == 0) {
+    const uint64_t nb = n - h.K, M = h.M, mm = std::max<uint64_t>(M, 1);
+    TRY(grow(w.s_id, mm * 8));
+    TRY(grow(w.s_cnt, mm * 8));
+    TRY(grow(w.s_rel, nn * 4));
+    TRY(grow(w.bid, mm * 8));
+    TRY(grow(w.counts, mm * 8));
+    TRY(grow(w.starts, mm * 8));
+    TRY(grow(w.btot, 16));
+    const uint64_t tiles = mm / 4096 + 2;
+    TRY(grow(w.scan_tmp, tiles * 8));
+    TRY(grow(w.scan_base, (tiles + 1) * 8));
+    launch_decode_u64(in + h.off[0], h.si[0], ht + 0, P<unsigned long long>(w.s_id), err, sms, s);
+    launch_decode_u64(in + h.off[1], h.si[1], ht + 1, P<unsigned long long>(w.s_cnt), err, sms, s);
+    launch_decode_u32(in + h.off[2], h.si[2], ht + 2, P<uint32_t>(w.s_rel), err, sms, s);
+    if (M > 0) {
+      unsigned long long *tt = P<unsigned long long>(w.scan_tmp);
+      unsigned long long *tb = P<unsigned long long>(w.scan_base);
+      launch_scan_u64(P<unsigned long long>(w.s_id), M, 0, true, P<unsigned long long>(w.bid), tt,
+                      tb, s);
+      launch_scan_u64(P<unsigned long long>(w.s_cnt), M, 1, true,
+                      P<unsigned long long>(w.counts), tt, tb, s);
+      launch_scan_u64(P<unsigned long long>(w.counts), M, 0, false,
+                      P<unsigned long long>(w.starts), tt, tb, s);
+      k_counts_total<<<1, 1, 0, s>>>(P<unsigned long long>(w.starts),
+                                     P<unsigned long long>(w.counts), M,
+                                     P<unsigned long long>(w.btot));
+      launch_check_counts(P<unsigned long long>(w.counts), M, P<unsigned long long>(w.btot), nb,
+                          err, sms, s);
+      launch_expand_s(h.d, P<Plan>(w.plan), P<unsigned long long>(w.bid),
+                      P<unsigned long long>(w.starts), M, P<uint32_t>(w.s_rel), nb, n,
+                      h.log2_chunk, out, qout, err, s);
+    }
+    launch_outliers_decode(P<Plan>(w.plan), reinterpret_cast<const float *>(in + h.off[3]), h.K,
+                           n, h.d, out, qout, sms, s);
+  } else {
+    const uint64_t nd = std::max<uint64_t>(n * h.d, 1);
+    TRY(grow(w.sym, nd * 4));
+    launch_decode_u32(in + h.off[0], h.si[0], ht, P<uint32_t>(w.sym), err, sms, s);
+    const int32_t *qref = ra ? P<int32_t>(t->anc_q) : P<int32_t>(t->prev_q);
+    launch_recon_t(P<Plan>(w.plan), n, h.d, P<uint32_t>(w.sym), qref, out, qout, err, sms, s);
+    launch_patches_apply(in + h.off[1], h.K, n * h.d, out, err, sms, s);
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->h_err, w.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(c->h_plan, w.plan.p, sizeof(Plan), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (*c->h_err || c->h_plan->status != OK) return ERR_FORMAT;
+  if (t) {
+    std::swap(t->prev_q, t->new_q);
+    if (h.method == 0 && first) {
+      CK(cudaMemcpyAsync(t->anc_q.p, t->prev_q.p, std::max<uint64_t>(n * h.d, 1) * 4,
+                         cudaMemcpyDeviceToDevice, s));
+      CK(cudaStreamSynchronize(s));
+      t->has_anchor = true;
+    }
+    t->has_prev = true;
+    t->n = n;
+    t->d = h.d;
+    t->t += 1;
+  }
+  return OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lcp_status lcp_decompress(lcp_ctx *c, lcp_traj *traj, const void *d_in, size_t in_size,
+                          float *d_out, uint64_t n_cap, uint64_t *n_out, uint32_t *d_fields,
+                          void *stream) {
+  if (!c) return LCP_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  return (lcp_status)decompress_impl(c, traj, (const uint8_t *)d_in, in_size, d_out, n_cap, n_out,
+                                     d_fields, (cudaStream_t)stream);
+}
+
+lcp_status lcp_peek(const void *d_in, size_t in_size, uint64_t *n, uint32_t *d,
+                    lcp_method *method, uint32_t *flags, void *stream) {
+  if (!d_in || in_size < 48) return LCP_ERR_FORMAT;
+  uint8_t h[48];
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(h, d_in, 48, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return LCP_ERR_CUDA;
+  }
+  if (h[0] != 'L' || h[1] != 'C' || h[2] != 'P' || h[3] != '1' || h[4] != 1 || h[5] > 1 ||
+      h[6] < 1 || h[6] > 8)
+    return LCP_ERR_FORMAT;
+  if (n) *n = rd64(h + 16);
+  if (d) *d = h[6];
+  if (method) *method = h[5] ? LCP_TEMPORAL : LCP_SPATIAL;
+  if (flags) *flags = rd32(h + 8);
+  return LCP_OK;
+}
+
+lcp_status lcp_quantize(const float *d_x, uint64_t n, float m, float e, float max_abs,
+                        int32_t *d_q, float *d_xr, uint8_t *d_viol, void *stream) {
+  if (n > 0 && (!d_x || !d_q || !d_xr || !d_viol)) return LCP_ERR_ARG;
+  if (!(e > 0.0f)) return LCP_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the plan lives in a small per-call device buffer
+  FieldPlan *fp = nullptr;
+  int *stp = nullptr;
+  if (cudaMallocAsync((void **)&fp, sizeof(FieldPlan) + 16, s) != cudaSuccess) {
+    cudaGetLastError();
+    return LCP_ERR_NOMEM;
+  }
+  stp = reinterpret_cast<int *>(fp + 1);
+  launch_field_plan(m, e, max_abs, fp, stp, s);
+  int hst = 0;
+  lcp_status r = LCP_OK;
+  if (cudaMemcpyAsync(&hst, stp, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    r = LCP_ERR_CUDA;
+  } else if (hst != OK) {
+    r = (lcp_status)hst;
+  } else {
+    // every q must stay below 2^30
+    double qest = ((double)max_abs + fabs((double)m)) / (2.0 * (double)e);
+    if (!(qest < 1073741824.0)) r = LCP_ERR_RANGE;
+    else {
+      launch_element_rules(d_x, n, fp, d_q, d_xr, d_viol, s);
+      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+        r = LCP_ERR_CUDA;
+    }
+  }
+  cudaFreeAsync(fp, s);
+  cudaStreamSynchronize(s);
+  return r;
+}
+
+}  // extern "C"

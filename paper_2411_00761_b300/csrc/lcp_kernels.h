@@ -1,0 +1,157 @@
+// lcp_kernels.h -- host-side launchers of the LCP kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lcp_common.cuh"
+
+namespace lcp {
+
+// container header fields the decoder needs per field
+struct DecodeFields {
+  float m[kMaxD];
+  float e[kMaxD];
+  uint32_t qmax[kMaxD];
+  uint32_t lp;
+};
+
+// one stream section as read from its 32-byte header
+struct StreamInfo {
+  unsigned long long n, payload_bits, n_chunks, maxv;
+  uint32_t coder, width, used, log2_chunk;
+};
+
+// canonical Huffman decode tables
+struct HuffTable {
+  uint32_t fast[1u << kFastBits];  // sym << 5 | len, 0 when the code is longer
+  uint32_t first[kLmax + 2], index[kLmax + 2], count[kLmax + 2];
+  uint16_t syms[kAlpha];
+  uint32_t used, ok;
+};
+
+// --- frame stage (k_frame.cu) -------------------------------------------
+void launch_minmax(const float *fields, uint64_t n, uint32_t d, MinMax *mm, int sms,
+                   cudaStream_t s);
+void launch_plan(const MinMax *mm, uint64_t n, uint32_t d, double eb, int mode, uint32_t p,
+                 uint32_t nbits_target, uint32_t method, Plan *plan, cudaStream_t s);
+void launch_quantize_s(const float *fields, uint64_t n, uint32_t d, const Plan *plan,
+                       uint32_t nb1, int tiles, unsigned long long *keys, uint32_t *tile_hist,
+                       int32_t *q, cudaStream_t s);
+void launch_field_plan(float m, float e, float max_abs, FieldPlan *fp, int *status,
+                       cudaStream_t s);
+void launch_element_rules(const float *x, uint64_t n, FieldPlan *fp_dev, int32_t *q, float *xr,
+                          uint8_t *viol, cudaStream_t s);
+
+// --- partition and segmentation (k_sort.cu) -----------------------------
+void launch_scan_small(const unsigned long long *in, uint32_t n, unsigned long long *out,
+                       cudaStream_t s);
+void launch_bucket_offsets(uint32_t *tile_hist, int tiles, uint32_t nb1,
+                           unsigned long long *bucket_start, unsigned long long *totals,
+                           cudaStream_t s);
+void launch_scatter(const unsigned long long *keys, uint64_t n, const Plan *plan, uint32_t nb1,
+                    int tiles, const uint32_t *tile_off, unsigned long long *keys_out,
+                    uint32_t *idx_out, cudaStream_t s);
+struct LocalArgs {
+  const Plan *plan;
+  uint32_t nb1;                            // buckets + 1 (outliers last)
+  const unsigned long long *bucket_start;  // [nb1 + 1]
+  unsigned long long *keys;                // partitioned keys
+  uint32_t *idx;                           // partitioned input indices (perm mode)
+  unsigned long long *keys_alt;            // scratch for large buckets
+  uint32_t *idx_alt;
+  uint32_t *s_rel;                         // [n]
+  unsigned long long *tmp_bid;             // [n] block ids per bucket region
+  uint32_t *tmp_pos;                       // [n] block start (bucket-local)
+  uint32_t *bucket_blocks;                 // [nb1]
+  uint32_t *hist;                          // [3][4096]
+  unsigned long long *maxv;                // [3]
+  uint32_t *perm;                          // [n] slot -> input index (perm mode) or null
+  const int32_t *q_in;                     // [d][n] codes by input index, or null
+  int32_t *q_slot;                         // [d][n] codes by slot, or null
+  uint32_t *outl_idx;                      // [n] outlier input indices, ascending
+  uint32_t log2_chunk;
+  uint64_t n;
+};
+void launch_local(const LocalArgs &a, int ctas, cudaStream_t s);
+void launch_blocks(const Plan *plan, uint32_t nb1, const unsigned long long *bucket_start,
+                   const uint32_t *bucket_blocks, const unsigned long long *tmp_bid,
+                   const uint32_t *tmp_pos, unsigned long long *block_off, int *prev_nonempty,
+                   unsigned long long *s_id, unsigned long long *s_cnt, uint32_t *hist,
+                   unsigned long long *maxv, unsigned long long *mcount, int ctas,
+                   cudaStream_t s);
+// value counts of the three LCP-S streams and K
+void launch_counts_s(const unsigned long long *bucket_start, uint32_t nb, uint64_t n,
+                     const unsigned long long *mcount, unsigned long long *nvals,
+                     unsigned long long *kcount, cudaStream_t s);
+// sorts cnt (device count) (key, payload) pairs by key with one CTA
+void launch_sort_pairs(unsigned long long *keys, uint32_t *vals, unsigned long long *keys_alt,
+                       uint32_t *vals_alt, const unsigned long long *cnt, int kbits,
+                       unsigned long long *keys_out, uint32_t *vals_out, cudaStream_t s);
+
+// --- coding (k_code.cu) --------------------------------------------------
+void launch_codebook(int ns, const uint32_t *hist, const unsigned long long *maxv,
+                     const unsigned long long *n_vals, uint32_t log2_chunk, StreamDesc *desc,
+                     uint32_t *codes, uint8_t *lens, uint16_t *tables, cudaStream_t s);
+struct LayoutArgs {
+  int method;  // 0 S, 1 T
+  uint32_t d, log2_chunk, flags, p;
+  uint64_t n;
+  const Plan *plan;
+  StreamDesc *desc;  // [ns + 1], the last one is the outlier / patch section
+  const uint16_t *tables;
+  const unsigned long long *mcount;  // M (S)
+  const unsigned long long *kcount;  // K
+  uint8_t *out;
+  unsigned long long cap;
+  Summary *summary;
+};
+// size_only: offsets and total only (no writes to out)
+void launch_layout(const LayoutArgs &a, int sms, bool size_only, cudaStream_t s);
+void launch_encode_u64(const unsigned long long *vals, uint64_t n, const StreamDesc *desc,
+                       const uint32_t *codes, const uint8_t *lens, uint32_t log2_chunk,
+                       uint8_t *out, const Summary *summary, unsigned long long *chunk_bits,
+                       unsigned long long *chunk_off, int sms, cudaStream_t s);
+void launch_encode_u32(const uint32_t *vals, uint64_t n, const StreamDesc *desc,
+                       const uint32_t *codes, const uint8_t *lens, uint32_t log2_chunk,
+                       uint8_t *out, const Summary *summary, unsigned long long *chunk_bits,
+                       unsigned long long *chunk_off, int sms, cudaStream_t s);
+void launch_outliers_s(const float *fields, uint64_t n, uint32_t d, const uint32_t *outl_idx,
+                       const StreamDesc *desc_outl, uint8_t *out, const Summary *summary,
+                       int sms, cudaStream_t s);
+
+// --- temporal (k_temporal.cu) --------------------------------------------
+void launch_quantize_t(const float *fields, uint64_t n, uint32_t d, const Plan *plan,
+                       const uint32_t *pi, const int32_t *qref, uint32_t *sym, int32_t *qnew,
+                       uint32_t *hist, unsigned long long *maxv, unsigned long long *kcount,
+                       unsigned long long *patch_s, float *patch_x, int sms, cudaStream_t s);
+void launch_patches_write(const unsigned long long *ps, const uint32_t *order, const float *px,
+                          const StreamDesc *od, uint8_t *out, const Summary *summary, int sms,
+                          cudaStream_t s);
+void launch_recon_t(const Plan *plan, uint64_t n, uint32_t d, const uint32_t *sym,
+                    const int32_t *qref, float *out, int32_t *qnew, int *err, int sms,
+                    cudaStream_t s);
+void launch_patches_apply(const uint8_t *sec, uint64_t K, uint64_t nd, float *out, int *err,
+                          int sms, cudaStream_t s);
+
+// --- decode (k_decode.cu) --------------------------------------------------
+void launch_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan, cudaStream_t s);
+void launch_huff_table(const uint8_t *sec, HuffTable *T, cudaStream_t s);
+void launch_decode_u64(const uint8_t *sec, const StreamInfo &info, HuffTable *ht,
+                       unsigned long long *out, int *err, int sms, cudaStream_t s);
+void launch_decode_u32(const uint8_t *sec, const StreamInfo &info, HuffTable *ht, uint32_t *out,
+                       int *err, int sms, cudaStream_t s);
+// mode 1: values are zigzag codes, scanned after unzigzag
+void launch_scan_u64(const unsigned long long *in, uint64_t n, int mode, bool inclusive,
+                     unsigned long long *out, unsigned long long *tile_tmp,
+                     unsigned long long *tile_base, cudaStream_t s);
+void launch_check_counts(const unsigned long long *counts, uint64_t m,
+                         const unsigned long long *starts_total, uint64_t nb, int *err, int sms,
+                         cudaStream_t s);
+void launch_expand_s(uint32_t d, const Plan *plan, const unsigned long long *bid,
+                     const unsigned long long *bstart, uint64_t M, const uint32_t *s_rel,
+                     uint64_t nb, uint64_t n, uint32_t log2_chunk, float *out, int32_t *qout,
+                     int *err, cudaStream_t s);
+void launch_outliers_decode(const Plan *plan, const float *raw, uint64_t K, uint64_t n, uint32_t d,
+                            float *out, int32_t *qout, int sms, cudaStream_t s);
+
+}  // namespace lcp

@@ -1,0 +1,223 @@
+"""Python binding of liblcp.so (the B300 LCP library).
+
+Argument marshalling only: every step of compression and decompression runs
+in the library's CUDA kernels.  Tensors are torch CUDA tensors (device memory
+and streams come from PyTorch); frames are float32 [d, n], field-major.
+There is no CPU fallback: importing this module without the built library,
+or calling it without a GPU, raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblcp.so")
+
+OK, ERR_ARG, ERR_NONFINITE, ERR_RANGE, ERR_CAPACITY, ERR_FORMAT, ERR_STATE, ERR_NOMEM, \
+    ERR_TIMEOUT, ERR_CUDA = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+EB_ABS, EB_REL = 0, 1
+SPATIAL, TEMPORAL, AUTO = 0, 1, 2
+FLAG_FIRST_IN_BATCH, FLAG_REF_ANCHOR = 1, 2
+
+# every entry point include/lcp.h declares, with its ctypes signature
+_vp, _u64, _u32, _sz = C.c_void_p, C.c_uint64, C.c_uint32, C.c_size_t
+SIGNATURES = {
+    "lcp_status_str": (C.c_char_p, [C.c_int]),
+    "lcp_ctx_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
+    "lcp_ctx_destroy": (C.c_int, [_vp]),
+    "lcp_ctx_reserve": (C.c_int, [_vp, _u64, _u32]),
+    "lcp_max_compressed_size": (_sz, [_u64, _u32]),
+    "lcp_compress": (C.c_int, [_vp, _vp, _vp, _u64, _u32, C.c_double, C.c_int, _u32, C.c_int, _vp,
+                               _sz, C.POINTER(_sz), C.POINTER(C.c_int), _vp, _vp]),
+    "lcp_decompress": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _u64, C.POINTER(_u64), C.POINTER(_u32),
+                                 _vp]),
+    "lcp_peek": (C.c_int, [_vp, _sz, C.POINTER(_u64), C.POINTER(_u32), C.POINTER(C.c_int),
+                           C.POINTER(_u32), _vp]),
+    "lcp_select": (C.c_int, [_vp, _vp, _vp, _u64, _u32, C.c_double, C.c_int, C.POINTER(C.c_int),
+                             C.POINTER(_u64), C.POINTER(_u64), _vp]),
+    "lcp_traj_create": (C.c_int, [_vp, _u32, _u32, C.POINTER(C.c_void_p)]),
+    "lcp_traj_destroy": (C.c_int, [_vp]),
+    "lcp_quantize": (C.c_int, [_vp, _u64, C.c_float, C.c_float, C.c_float, _vp, _vp, _vp, _vp]),
+}
+
+
+class LcpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.lcp_status_str(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} ({status})")
+        self.status = status
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Loads the in-tree liblcp.so; raises when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"liblcp.so is not built ({LIB_PATH}); run "
+                               "python -m paper_2411_00761_b300.build")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != OK:
+        raise LcpError(st, where)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _mode(mode) -> int:
+    return {"abs": EB_ABS, "rel": EB_REL, EB_ABS: EB_ABS, EB_REL: EB_REL}[mode]
+
+
+def _method(m) -> int:
+    return {"spatial": SPATIAL, "temporal": TEMPORAL, "auto": AUTO,
+            SPATIAL: SPATIAL, TEMPORAL: TEMPORAL, AUTO: AUTO}[m]
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def max_compressed_size(n: int, d: int) -> int:
+    return int(load().lcp_max_compressed_size(n, d))
+
+
+class Context:
+    """Device workspace of one GPU (lcp_ctx)."""
+
+    def __init__(self, device: int = 0):
+        load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("the LCP library needs a CUDA GPU")
+        self.device = device
+        h = C.c_void_p()
+        _check(_lib.lcp_ctx_create(device, C.byref(h)), "lcp_ctx_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            _lib.lcp_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, n: int, d: int):
+        _check(_lib.lcp_ctx_reserve(self.h, n, d), "lcp_ctx_reserve")
+
+    def compress(self, X: torch.Tensor, eb: float, mode="abs", p: int = 8, method="spatial",
+                 traj: "Trajectory | None" = None, out: torch.Tensor | None = None,
+                 perm: bool = False, stream=None) -> dict:
+        """Compresses X [d, n] (float32, CUDA, contiguous).  Returns the
+        container (a uint8 view of `out`), its size, the method used and,
+        when asked, the slot permutation (int32 [n])."""
+        assert X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.is_contiguous()
+        d, n = X.shape
+        if out is None:
+            out = torch.empty(max_compressed_size(n, d), dtype=torch.uint8, device=X.device)
+        pm = torch.empty(max(n, 1), dtype=torch.int32, device=X.device) if perm else None
+        size = C.c_size_t(0)
+        chosen = C.c_int(0)
+        st = _lib.lcp_compress(self.h, traj.h if traj is not None else None, _ptr(X), n, d,
+                               float(eb), _mode(mode), p, _method(method), _ptr(out),
+                               out.numel(), C.byref(size), C.byref(chosen), _ptr(pm),
+                               _stream(stream))
+        if st == ERR_CAPACITY:
+            raise LcpError(st, f"lcp_compress (needs {size.value} bytes)")
+        _check(st, "lcp_compress")
+        return dict(bytes=out[: size.value], size=size.value,
+                    method="temporal" if chosen.value == TEMPORAL else "spatial",
+                    perm=pm[:n] if perm else None)
+
+    def decompress(self, buf: torch.Tensor, size: int | None = None,
+                   traj: "Trajectory | None" = None, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+        """Decodes a container (uint8 CUDA tensor) into float32 [d, n] in slot
+        order."""
+        assert buf.is_cuda and buf.dtype == torch.uint8
+        size = buf.numel() if size is None else size
+        n, d, _, _ = self.peek(buf, size, stream)
+        if out is None:
+            out = torch.empty((d, n), dtype=torch.float32, device=buf.device)
+        nn = C.c_uint64(0)
+        dd = C.c_uint32(0)
+        st = _lib.lcp_decompress(self.h, traj.h if traj is not None else None, _ptr(buf), size,
+                                 _ptr(out), out.numel() // max(d, 1), C.byref(nn), C.byref(dd),
+                                 _stream(stream))
+        _check(st, "lcp_decompress")
+        return out.view(-1)[: d * n].view(d, n)
+
+    def peek(self, buf: torch.Tensor, size: int | None = None, stream=None):
+        n = C.c_uint64(0)
+        d = C.c_uint32(0)
+        m = C.c_int(0)
+        fl = C.c_uint32(0)
+        size = buf.numel() if size is None else size
+        _check(_lib.lcp_peek(_ptr(buf), size, C.byref(n), C.byref(d), C.byref(m), C.byref(fl),
+                             _stream(stream)), "lcp_peek")
+        return n.value, d.value, ("temporal" if m.value == TEMPORAL else "spatial"), fl.value
+
+    def select(self, traj: "Trajectory", X: torch.Tensor, eb: float, mode="abs", stream=None):
+        d, n = X.shape
+        ch = C.c_int(0)
+        es = C.c_uint64(0)
+        et = C.c_uint64(0)
+        _check(_lib.lcp_select(self.h, traj.h, _ptr(X), n, d, float(eb), _mode(mode),
+                               C.byref(ch), C.byref(es), C.byref(et), _stream(stream)),
+               "lcp_select")
+        return ("temporal" if ch.value == TEMPORAL else "spatial"), es.value, et.value
+
+
+class Trajectory:
+    """Reference state of one frame sequence (lcp_traj), for compressing or for
+    decompressing it."""
+
+    def __init__(self, ctx: Context, batch: int = 10, p: int = 8):
+        self.ctx = ctx
+        h = C.c_void_p()
+        _check(_lib.lcp_traj_create(ctx.h, batch, p, C.byref(h)), "lcp_traj_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            _lib.lcp_traj_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def quantize(x: torch.Tensor, m: float, e: float, max_abs: float | None = None, stream=None):
+    """Element rules on the GPU: (q, x', violation) for values x >= m."""
+    assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+    load()
+    n = x.numel()
+    q = torch.empty(n, dtype=torch.int32, device=x.device)
+    xr = torch.empty(n, dtype=torch.float32, device=x.device)
+    v = torch.empty(n, dtype=torch.uint8, device=x.device)
+    if max_abs is None:
+        max_abs = float(x.abs().max()) if n else 0.0
+    _check(_lib.lcp_quantize(_ptr(x), n, m, e, max_abs, _ptr(q), _ptr(xr), _ptr(v),
+                             _stream(stream)), "lcp_quantize")
+    return q, xr, v.bool()

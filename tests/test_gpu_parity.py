@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact throughout: quantization codes, reconstructed values and guard
+decisions element by element; the container bytes of LCP-S and LCP-T frames;
+the decoded particles; the slot permutation.  Sizes span several tiles,
+partition buckets and a ragged tail; edge cases cover empty frames, a single
+particle, all particles in one block, bounds near the f32 spacing (raw
+outliers), one and eight fields, and buckets too large for shared memory.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2411_00761_b300 import synth
+from tests import exact_ref as X
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lcp():
+    from paper_2411_00761_b300 import lcp as L
+    return L
+
+
+@pytest.fixture(scope="module")
+def ctx(lcp):
+    return lcp.Context(0)
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_bytes(res):
+    return res["bytes"].cpu().numpy().tobytes()
+
+
+# ---------------------------------------------------------------------------
+# element rules
+# ---------------------------------------------------------------------------
+ELEM_CASES = [(0.0, 1e-3, 1.0), (-0.5, 3.7e-4, 1.0), (1000.0, 0.25, 50.0), (-2000.0, 3.6, 4000.0),
+              (1.0e-6, 1e-3, 1.0), (0.0, 1e-7, 1e-3), (123.456, 1e-5, 0.01), (-3.0, 0.7, 6.0)]
+
+
+@pytest.mark.parametrize("m,eb,scale", ELEM_CASES)
+def test_element_rules_bit_exact(lcp, orc, m, eb, scale):
+    rng = np.random.default_rng(int(abs(m) * 1000 + eb * 1e7) % 2 ** 31)
+    m = np.float32(m)
+    e = np.float32(orc.round_down_f32(eb))
+    vals = (m + rng.random(200000) * scale).astype(np.float32)
+    # values at and next to exact bin edges
+    ks = rng.integers(0, int(scale / (2 * float(e))) + 1, size=2000)
+    edges = []
+    for k in ks:
+        r = X.rn32(X.F(m) + int(k) * 2 * X.F(e))
+        edges += [r, np.nextafter(r, np.float32(np.inf), dtype=np.float32),
+                  np.nextafter(r, np.float32(-np.inf), dtype=np.float32)]
+    vals = np.concatenate([vals, np.array(edges, np.float32), np.array([m], np.float32)])
+    vals = vals[vals >= m]
+    q, xr, v = lcp.quantize(to_dev(vals), float(m), float(e))
+    q_ref = orc.q1(vals, float(m), float(e))
+    assert np.array_equal(q.cpu().numpy().astype(np.int64), q_ref)
+    xr_ref = orc.q2(q_ref, float(m), float(e))
+    assert np.array_equal(xr.cpu().numpy().view(np.uint32), xr_ref.view(np.uint32))
+    v_ref = orc.q3(vals, xr_ref, float(e))
+    assert np.array_equal(v.cpu().numpy(), v_ref)
+
+
+# ---------------------------------------------------------------------------
+# LCP-S frames
+# ---------------------------------------------------------------------------
+def frames_s():
+    yield "uniform_clusters_ragged", synth.uniform_clusters((1 << 17) + 77, 0), 1e-3, "abs", 8
+    yield "uniform_clusters_p2", synth.uniform_clusters(50001, 5), 1e-3, "abs", 2
+    yield "md_fcc", synth.md_fcc(200003, 1, cells=40), 1e-4, "rel", 16
+    yield "md_fcc_p32", synth.md_fcc(65536, 3, cells=30), 1e-4, "rel", 32
+    yield "cosmology6", synth.cosmology(100000, 2), 1e-3, "rel", 4
+    yield "cosmology6_p8", synth.cosmology(30011, 7), 1e-3, "rel", 8
+
+
+def check_s(ctx, orc, Xf, eb, mode, p):
+    r = ctx.compress(to_dev(Xf), eb, mode, p, perm=True)
+    o = orc.compress_s(Xf, eb, mode, p)
+    gb = gpu_bytes(r)
+    assert len(gb) == len(o["bytes"])
+    assert gb == o["bytes"]
+    assert np.array_equal(r["perm"].cpu().numpy().astype(np.uint32), o["pi"])
+    Y = ctx.decompress(r["bytes"]).cpu().numpy()
+    Yo, _ = orc.decompress(o["bytes"])
+    assert np.array_equal(Y.view(np.uint32), Yo.view(np.uint32))
+    return r, o
+
+
+@pytest.mark.parametrize("name,Xf,eb,mode,p", list(frames_s()))
+def test_lcp_s_bytes_and_decode(ctx, orc, name, Xf, eb, mode, p):
+    check_s(ctx, orc, Xf, eb, mode, p)
+
+
+def test_lcp_s_decodes_oracle_containers_other_chunks(ctx, orc):
+    Xf = synth.uniform_clusters(40000, 9)
+    for lc in (5, 8, 10):
+        o = orc.compress_s(Xf, 1e-3, "abs", 8, log2_chunk=lc)
+        Y = ctx.decompress(to_dev(np.frombuffer(o["bytes"], np.uint8))).cpu().numpy()
+        Yo, _ = orc.decompress(o["bytes"])
+        assert np.array_equal(Y.view(np.uint32), Yo.view(np.uint32))
+
+
+def test_degenerate_frames(ctx, orc):
+    rng = np.random.default_rng(4)
+    cases = [
+        (np.full((3, 5000), 0.37, np.float32), 1e-3, "abs", 8),            # one block
+        (np.zeros((3, 0), np.float32), 1e-3, "abs", 8),                    # empty
+        (np.array([[0.5], [0.25], [0.125]], np.float32), 1e-3, "abs", 8),  # one particle
+        ((1000.0 + rng.random((3, 20000))).astype(np.float32), 4e-5, "abs", 4),  # outliers
+        ((1000.0 + rng.random((3, 3000))).astype(np.float32), 1e-6, "abs", 4),   # sub-ulp bound
+        (rng.random((1, 70000)).astype(np.float32), 1e-4, "abs", 16),      # d = 1
+        (rng.random((8, 30000)).astype(np.float32), 0.05, "abs", 2),       # d = 8
+        (np.stack([np.linspace(0, 1, 9000, dtype=np.float32), np.full(9000, 5.0, np.float32)]),
+         1e-3, "rel", 4),                                                  # constant field
+    ]
+    for Xf, eb, mode, p in cases:
+        check_s(ctx, orc, Xf, eb, mode, p)
+
+
+def test_large_bucket_global_path(ctx, orc):
+    """Many distinct keys in one partition bucket: sorted in global memory."""
+    rng = np.random.default_rng(8)
+    n = 60000
+    # all particles inside one block along the top axis, spread in the others
+    Xf = np.stack([rng.random(n), rng.random(n), np.full(n, 0.5) + rng.random(n) * 1e-3])
+    Xf = Xf.astype(np.float32)
+    check_s(ctx, orc, Xf, 1e-3, "abs", 4)
+
+
+def test_status_codes(ctx, lcp):
+    Xn = np.zeros((3, 100), np.float32)
+    Xn[1, 7] = np.nan
+    with pytest.raises(lcp.LcpError) as ei:
+        ctx.compress(to_dev(Xn), 1e-3)
+    assert ei.value.status == lcp.ERR_NONFINITE
+    with pytest.raises(lcp.LcpError) as ei:
+        ctx.compress(to_dev(np.zeros((3, 10), np.float32)), 1e-3, p=3)
+    assert ei.value.status == lcp.ERR_ARG
+    big = np.array([[0.0, 1.0e9]] * 3, np.float32)
+    with pytest.raises(lcp.LcpError) as ei:
+        ctx.compress(to_dev(big), 1e-3)
+    assert ei.value.status == lcp.ERR_RANGE
+    wide = np.array([[0.0, 1.0e3]] * 8, np.float32)
+    with pytest.raises(lcp.LcpError) as ei:
+        ctx.compress(to_dev(wide), 1e-4, p=2)
+    assert ei.value.status == lcp.ERR_RANGE
+    # capacity
+    Xf = synth.uniform_clusters(10000, 1)
+    out = torch.empty(100, dtype=torch.uint8, device="cuda")
+    with pytest.raises(lcp.LcpError) as ei:
+        ctx.compress(to_dev(Xf), 1e-3, out=out)
+    assert ei.value.status == lcp.ERR_CAPACITY
+
+
+def test_block_size_autotune_matches_oracle(ctx, orc):
+    from oracle import hybrid
+    Xf = synth.md_fcc(40000, 1, cells=25)
+    best, sizes = hybrid.choose_block_size(Xf, 1e-4, "rel")
+    r = ctx.compress(to_dev(Xf), 1e-4, "rel", p=0)
+    assert r["size"] == sizes[best]
+    assert gpu_bytes(r) == orc.compress_s(Xf, 1e-4, "rel", best)["bytes"]
+
+
+# ---------------------------------------------------------------------------
+# LCP-T and the hybrid (Algorithm 1 with the LCP-FSM)
+# ---------------------------------------------------------------------------
+def test_lcp_t_bytes_forced(ctx, orc, lcp):
+    frames = list(synth.brownian_trajectory(30017, 3, 13))
+    tr = lcp.Trajectory(ctx, batch=10, p=8)
+    r0 = ctx.compress(to_dev(frames[0]), 1e-3, "abs", traj=tr, method="spatial", perm=True)
+    o0 = orc.compress_s(frames[0], 1e-3, "abs", 8, flags=1)
+    assert gpu_bytes(r0) == o0["bytes"]
+    r1 = ctx.compress(to_dev(frames[1]), 1e-3, "abs", traj=tr, method="temporal")
+    o1 = orc.compress_t(frames[1], 1e-3, "abs", o0["q"], o0["pi"])
+    assert r1["method"] == "temporal"
+    assert gpu_bytes(r1) == o1["bytes"]
+    # decode side: S then T through a decoder trajectory
+    dt = lcp.Trajectory(ctx, batch=10, p=8)
+    Y0 = ctx.decompress(r0["bytes"], traj=dt).cpu().numpy()
+    Y1 = ctx.decompress(r1["bytes"], traj=dt).cpu().numpy()
+    Yo1, _ = orc.decompress(o1["bytes"], o0["q"])
+    assert np.array_equal(Y1.view(np.uint32), Yo1.view(np.uint32))
+    assert Y0.shape == frames[0].shape
+
+
+def test_hybrid_trajectory_matches_oracle(ctx, orc, lcp):
+    from oracle import hybrid
+    n, nf, batch = 20011, 24, 5
+    frames = list(synth.brownian_trajectory(n, nf, 21, sigma=0.02))
+    enc = hybrid.encode_trajectory(frames, 1e-3, "abs", 8, batch=batch)
+    tr = lcp.Trajectory(ctx, batch=batch, p=8)
+    dt = lcp.Trajectory(ctx, batch=batch, p=8)
+    dec_o = hybrid.decode_trajectory([b for b, _ in enc])
+    for t, (Xf, (ob, om)) in enumerate(zip(frames, enc)):
+        r = ctx.compress(to_dev(Xf), 1e-3, "abs", traj=tr, method="auto")
+        assert r["method"] == {"S": "spatial", "T": "temporal"}[om], t
+        assert gpu_bytes(r) == ob, t
+        Y = ctx.decompress(r["bytes"], traj=dt).cpu().numpy()
+        assert np.array_equal(Y.view(np.uint32), dec_o[t].view(np.uint32)), t
+
+
+def test_select_is_a_query(ctx, lcp):
+    frames = list(synth.brownian_trajectory(5000, 4, 2))
+    tr = lcp.Trajectory(ctx, batch=10, p=8)
+    assert ctx.select(tr, to_dev(frames[0]), 1e-3)[0] == "spatial"
+    ctx.compress(to_dev(frames[0]), 1e-3, traj=tr, method="auto")
+    a = ctx.select(tr, to_dev(frames[1]), 1e-3)
+    b = ctx.select(tr, to_dev(frames[1]), 1e-3)
+    assert a == b
+    r = ctx.compress(to_dev(frames[1]), 1e-3, traj=tr, method="auto")
+    assert r["method"] == a[0]
+
+
+def test_temporal_needs_reference(ctx, lcp):
+    tr = lcp.Trajectory(ctx, batch=10, p=8)
+    Xf = synth.uniform_clusters(1000, 1)
+    with pytest.raises(lcp.LcpError) as ei:
+        ctx.compress(to_dev(Xf), 1e-3, traj=tr, method="temporal")
+    assert ei.value.status == lcp.ERR_STATE
+    with pytest.raises(lcp.LcpError) as ei:
+        ctx.compress(to_dev(Xf), 1e-3, method="temporal")
+    assert ei.value.status == lcp.ERR_STATE
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads in the bench's launch configuration
+# ---------------------------------------------------------------------------
+def test_full_size_plain_frame_bytes(ctx, orc):
+    """2^20 particles, the plain LCP-S frame: the whole container."""
+    Xf = synth.uniform_clusters(1 << 20, 0)
+    check_s(ctx, orc, Xf, 1e-3, "abs", 8)
+
+
+@pytest.mark.parametrize("which", ["md", "cosmology"])
+def test_full_size_sampled(ctx, orc, lcp, which):
+    """16M-particle MD and 64M-particle 6-field frames: every decoded value is
+    within the bound of its particle; on a sample of particles the decoded
+    value equals the oracle's reconstruction of the oracle's code bit for bit;
+    the decoded frame holds every particle once."""
+    if which == "md":
+        Xf, eb, mode, p = synth.md_fcc(1 << 24, 1), 1e-4, "rel", 16
+    else:
+        Xf, eb, mode, p = synth.cosmology(1 << 26, 2), 1e-3, "rel", 4
+    Xd = to_dev(Xf)
+    r = ctx.compress(Xd, eb, mode, p, perm=True)
+    Y = ctx.decompress(r["bytes"])
+    perm = r["perm"].long()
+    d, n = Xf.shape
+    assert torch.equal(torch.sort(perm).values, torch.arange(n, device="cuda"))
+    hdr = r["bytes"][:48 + 16 * d].cpu().numpy()
+    e = hdr[48:48 + 16 * d].view(np.float32).reshape(d, 4)[:, 1]
+    m = hdr[48:48 + 16 * d].view(np.float32).reshape(d, 4)[:, 0]
+    err = (Xd[:, perm].double() - Y.double()).abs().max(dim=1).values.cpu().numpy()
+    assert (err <= e.astype(np.float64)).all()
+    rng = np.random.default_rng(0)
+    slots = rng.choice(n, 20000, replace=False)
+    pi = perm.cpu().numpy()[slots]
+    Ys = Y[:, torch.from_numpy(slots).cuda()].cpu().numpy()
+    K = int(np.frombuffer(r["bytes"][24:32].cpu().numpy().tobytes(), np.uint64)[0])
+    for f in range(d):
+        x = Xf[f, pi]
+        q = orc.q1(x, float(m[f]), float(e[f]))
+        xr = orc.q2(q, float(m[f]), float(e[f]))
+        raw = slots >= n - K
+        exp = np.where(raw, x, xr)
+        assert np.array_equal(Ys[f].view(np.uint32), exp.view(np.uint32))
