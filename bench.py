@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the LCP hot path on B300 GPUs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cosmology|md|plain]
+                    [--impl ours|reference]
+
+A step is one LCP-S round trip of one synthetic frame: compression (min/max,
+quantization and block keys, partition, per-bucket sort and segmentation,
+codebooks, encoding) followed by decompression (stream decoding, block scans,
+expansion and reconstruction), inputs resident in HBM.  The default workload
+is the 64M-particle cosmology-like frame (x, y, z, vx, vy, vz; eb = 1e-3 of
+each field's range) with the block size chosen by the exact block-size search.
+
+Prints one JSON line.  `value` is the round-trip throughput in GB/s of raw
+input (size / (compress + decompress time)); compress and decompress rates,
+the compression ratio and their HBM roofline fractions are reported beside
+it.  `roofline` is for the kernel that dominates the step, timed live with
+CUDA events on the launching stream.  `e2e` repeats the step through the same
+C-ABI calls with the frame in pinned host memory, host<->device copies inside
+the timed region.  `cpu_baseline` times the CPU oracle on a bounded sample.
+
+N > 1 (torchrun): replicas, one frame per rank, no data exchange (frames are
+independent); barrier + max over ranks around the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "cosmology": dict(desc="cosmology-like frame: 64M particles, x y z vx vy vz f32, 4096 r^-2 "
+                           "halos (70%) + uniform background, eb = 1e-3 of each field's range",
+                      n=1 << 26, d=6, eb=1e-3, mode="rel", p=0, seed=2),
+    "md": dict(desc="MD-like frame: 16M particles of a 252^3-cell FCC lattice + N(0, 0.05^2), "
+                    "eb = 1e-4 of each field's range", n=1 << 24, d=3, eb=1e-4, mode="rel", p=0,
+               seed=1),
+    "plain": dict(desc="plain LCP-S frame: 2^20 particles, uniform + 64 Gaussian clusters, "
+                       "eb = 1e-3 absolute, p = 8", n=1 << 20, d=3, eb=1e-3, mode="abs", p=8,
+                  seed=0),
+}
+
+
+def make_frame(name: str, seed: int):
+    from paper_2411_00761_b300 import synth
+    w = WORKLOADS[name]
+    if name == "cosmology":
+        return synth.cosmology(w["n"], seed)
+    if name == "md":
+        return synth.md_fcc(w["n"], seed)
+    return synth.uniform_clusters(w["n"], seed)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# algorithmic bytes of each stage (what its function must read and write), in
+# terms of N particles, D fields, M blocks, K raw outliers and C container bytes
+def stage_bytes(stage: str, N, D, M, K, C):
+    raw = 4 * N * D
+    nb = N - K
+    table = {
+        "s.minmax": raw,
+        "s.quantize": raw + 8 * N,
+        "s.bucket_offsets": 0,
+        "s.scatter": 16 * N,
+        "s.local_sort": 8 * N + 4 * nb + 12 * M,
+        "s.blocks": 12 * M + 16 * M,
+        "s.codebook": 0,
+        "s.encode": 16 * M + 4 * nb + C,
+        "d.streams": C + 16 * M + 4 * nb,
+        "d.block_scans": 48 * M,
+        "d.expand": 16 * M + 4 * nb + raw,
+    }
+    return table.get(stage, 0)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_baseline(name: str, X: np.ndarray, p: int, n_sample: int):
+    """The oracle as it stands, single-threaded, on the first n_sample
+    particles of the frame (storage order is random, so this is a random
+    subset)."""
+    import oracle
+    w = WORKLOADS[name]
+    S = np.ascontiguousarray(X[:, :n_sample])
+    t0 = time.perf_counter()
+    r = oracle.compress_s(S, w["eb"], w["mode"], p)
+    t1 = time.perf_counter()
+    oracle.decompress(r["bytes"])
+    t2 = time.perf_counter()
+    return S.nbytes, t1 - t0, t2 - t1, len(r["bytes"])
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    name = args.workload
+    w = WORKLOADS[name]
+    X = make_frame(name, w["seed"])
+    p = w["p"] or 4
+    n_sample = args.sample or (1 << 18 if w["d"] == 6 else 1 << 19)
+    times = []
+    for k in range(args.warmup + args.steps):
+        nbytes, tc, td, csize = cpu_baseline(name, X, p, n_sample)
+        if k >= args.warmup:
+            times.append(tc + td)
+    t = sum(times) / len(times)
+    val = nbytes / t / 1e9
+    line = {
+        "impl": "reference", "metric": "compress/decompress GB/s vs HBM peak at fixed eb + ratio",
+        "value": val, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 in, integer codes",
+        "data": "synthetic", "config": {"workload": name, "desc": w["desc"], "p": p,
+                                        "sample_particles": n_sample},
+        "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n_sample} particles of the frame per step"},
+        "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="cosmology", choices=list(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sample", type=int, default=0, help="CPU-baseline sample particles")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=0, help="override the particle count (small cases)")
+    args = ap.parse_args()
+    if args.n:
+        WORKLOADS[args.workload]["n"] = args.n
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_00761_b300 import lcp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    name = args.workload
+    w = WORKLOADS[name]
+    X = make_frame(name, w["seed"] + rank)
+    D, N = X.shape
+    raw = X.nbytes
+    Xd = torch.from_numpy(X).to(dev)
+    ctx = lcp.Context(local)
+    ctx.reserve(N, D)
+    out = torch.empty(lcp.max_compressed_size(N, D), dtype=torch.uint8, device=dev)
+    Y = torch.empty((D, N), dtype=torch.float32, device=dev)
+    p = w["p"]
+    if p == 0:  # exact block-size search (Sec. "Best block size"), once per frame
+        r = ctx.compress(Xd, w["eb"], w["mode"], p=0, out=out)
+        p = int(np.frombuffer(out[12:16].cpu().numpy().tobytes(), np.uint32)[0])
+    stream = torch.cuda.current_stream(dev)
+
+    def step(profile=None):
+        r = ctx.compress(Xd, w["eb"], w["mode"], p=p, out=out)
+        if profile is not None:
+            profile.extend(ctx.profile_read())
+        ctx.decompress(r["bytes"], r["size"], out=Y)
+        if profile is not None:
+            profile.extend(ctx.profile_read())
+        return r
+
+    for _ in range(args.warmup):
+        r = step()
+    csize = r["size"]
+    hdr = out[:48].cpu().numpy().tobytes()
+    K = int(np.frombuffer(hdr[24:32], np.uint64)[0])
+    M = int(np.frombuffer(hdr[32:40], np.uint64)[0])
+
+    # timed region: compress and decompress timed separately with events
+    ctx.profile(True)
+    prof = []
+    tc, td = [], []
+    launches0 = lcp.kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            r = ctx.compress(Xd, w["eb"], w["mode"], p=p, out=out)
+            e1.record(stream)
+            prof.extend(ctx.profile_read())
+            ctx.decompress(r["bytes"], r["size"], out=Y)
+            e2.record(stream)
+            prof.extend(ctx.profile_read())
+            e2.synchronize()
+            tc.append(e0.elapsed_time(e1))
+            td.append(e1.elapsed_time(e2))
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+    launches = lcp.kernel_launches() - launches0
+    ctx.profile(False)
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_step = total_ms / args.steps
+    value = world * raw / (ms_step * 1e-3) / 1e9
+    tcm, tdm = statistics.mean(tc), statistics.mean(td)
+    peak, peak_kind = peaks()
+
+    # dominant kernel from the live stage timings
+    per = {}
+    for nm, ms in prof:
+        per.setdefault(nm, []).append(ms)
+    avg = {k: statistics.mean(v) for k, v in per.items()}
+    dom = max(avg, key=avg.get)
+    dbytes = stage_bytes(dom, N, D, M, K, csize)
+    achieved = dbytes / (avg[dom] * 1e-3) / 1e9
+
+    # e2e through the same calls with host buffers
+    e2e = None
+    if not args.no_e2e:
+        Xh = torch.from_numpy(X).pin_memory()
+        Ch = torch.empty(csize + 64, dtype=torch.uint8).pin_memory()
+        Yh = torch.empty((D, N), dtype=torch.float32).pin_memory()
+        Cd = torch.empty_like(out)
+        ts = []
+        for k in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Xd.copy_(Xh, non_blocking=True)
+            rr = ctx.compress(Xd, w["eb"], w["mode"], p=p, out=out)
+            Ch[: rr["size"]].copy_(rr["bytes"], non_blocking=True)
+            Cd[: rr["size"]].copy_(Ch[: rr["size"]], non_blocking=True)
+            ctx.decompress(Cd[: rr["size"]], rr["size"], out=Y)
+            Yh.copy_(Y, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            if k >= args.warmup:
+                ts.append(a.elapsed_time(b))
+        e2e_ms = statistics.mean(ts)
+        e2e = {"value": raw / (e2e_ms * 1e-3) / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": raw + csize, "d2h_bytes_per_step": csize + raw,
+               "ms_per_step": e2e_ms}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        ns = args.sample or (1 << 21 if D == 6 else min(N, 1 << 21))
+        nbytes, ctime, dtime, cs = cpu_baseline(name, X, p, ns)
+        cpu = {"value": nbytes / (ctime + dtime) / 1e9, "unit": "GB/s", "cores": 1,
+               "kind": "oracle", "sample": f"first {ns} particles of the frame (random subset), "
+                                            f"one compress + decompress round trip",
+               "compress_gbs": nbytes / ctime / 1e9, "decompress_gbs": nbytes / dtime / 1e9}
+
+    if rank == 0:
+        clocks = clk.summary()
+        line = {
+            "metric": "compress/decompress GB/s vs HBM peak at fixed eb + ratio",
+            "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 in, integer codes",
+            "data": "synthetic",
+            "config": {"workload": name, "desc": w["desc"], "particles": N, "fields": D,
+                       "eb": w["eb"], "eb_mode": w["mode"], "p": p,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": f"input {raw / 1e9:.2f} GB > 126 MB L2 every step (no flush)"},
+            "compress_gbs": raw / (tcm * 1e-3) / 1e9,
+            "decompress_gbs": raw / (tdm * 1e-3) / 1e9,
+            "compress_ms": tcm, "decompress_ms": tdm,
+            "ratio": raw / csize, "container_bytes": csize, "blocks": M, "raw_outliers": K,
+            "compress_roofline_frac": (raw + csize) / (tcm * 1e-3) / 1e9 / peak,
+            "decompress_roofline_frac": (raw + csize) / (tdm * 1e-3) / 1e9 / peak,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "algorithmic_bytes_per_launch": dbytes,
+                         "avg_ms": avg[dom]},
+            "stages_ms": {k: round(v, 4) for k, v in sorted(avg.items(), key=lambda x: -x[1])},
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -160,6 +160,19 @@ LCP_API lcp_status lcp_traj_create(lcp_ctx *ctx, uint32_t batch_size, uint32_t p
 LCP_API lcp_status lcp_traj_destroy(lcp_traj *traj);
 
 /*
+ * Per-kernel timing (tracing).  With profiling on, every entry point records
+ * a CUDA event pair on its stream around each major kernel (stage names such
+ * as "s.quantize", "s.local_sort", "d.expand").  lcp_ctx_profile_read returns
+ * the number of stages of the most recent call (at most cap), their names in
+ * names[32 * k] (NUL-terminated) and durations in ms[k]; it waits for those
+ * events.  The paper has no counterpart: this is measurement plumbing.
+ */
+LCP_API lcp_status lcp_ctx_profile(lcp_ctx *ctx, int enable);
+/* Number of CUDA kernels this library has launched in this process. */
+LCP_API uint64_t lcp_kernel_launches(void);
+LCP_API int lcp_ctx_profile_read(lcp_ctx *ctx, char *names, float *ms, int cap);
+
+/*
  * Element rules, exposed for verification.  For x[i] (device, n values) of a
  * field with minimum m and bound e (float32, e > 0 normal):
  *   q[i]    = floor((x[i] - m) / (2 e))            (Eq. quantization)

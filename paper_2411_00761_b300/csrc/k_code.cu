@@ -272,6 +272,7 @@ void launch_codebook(int ns, const uint32_t *hist, const unsigned long long *max
     cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
+  note_launch();
   k_codebook<<<ns, kCbThreads, smem, s>>>(hist, maxv, n_vals, log2_chunk, desc, codes, lens,
                                           tables);
 }
@@ -382,9 +383,12 @@ __global__ void k_layout_write(LayoutArgs a) {
 }
 
 void launch_layout(const LayoutArgs &a, int sms, bool size_only, cudaStream_t s) {
+  note_launch();
   k_layout_size<<<1, 32, 0, s>>>(a);
   if (size_only) return;
+  note_launch();
   k_zero<<<2 * sms, 512, 0, s>>>(a.out, a.summary);
+  note_launch();
   k_layout_write<<<1, 256, 0, s>>>(a);
 }
 
@@ -547,16 +551,20 @@ static void encode_stream(const T *vals, uint64_t n, const StreamDesc *desc, con
   unsigned long long words_max = (n * 64ull + 31ull) / 32ull;
   unsigned g = (unsigned)std::min<unsigned long long>((words_max + 255) / 256, 8ull * sms);
   if (g == 0) g = 1;
+  note_launch();
   k_encode_fixed<T><<<g, 256, 0, s>>>(vals, desc, out, summary);
   // Huffman (no-op unless chosen)
   unsigned long long chunks = (n + (1ull << log2_chunk) - 1ull) >> log2_chunk;
   if (chunks == 0) return;
   unsigned gc = (unsigned)std::min<unsigned long long>((chunks * 32 + 255) / 256, 16ull * sms);
+  note_launch();
   k_chunk_bits<T><<<gc, 256, 0, s>>>(vals, desc, lens, log2_chunk, chunk_bits, summary);
   launch_scan_small(chunk_bits, (uint32_t)chunks, chunk_off, s);
   unsigned gt = (unsigned)std::min<unsigned long long>((chunks + 255) / 256, 4ull * sms);
+  note_launch();
   k_chunk_table<<<gt, 256, 0, s>>>(chunk_off, desc, out, summary);
   unsigned ge = (unsigned)std::min<unsigned long long>((chunks + kEncWarps - 1) / kEncWarps, 16ull * sms);
+  note_launch();
   k_huff_encode<T><<<ge, 32 * kEncWarps, 0, s>>>(vals, desc, codes, lens, log2_chunk, chunk_off,
                                                   out, summary);
 }
@@ -596,6 +604,7 @@ __global__ void k_outliers_s(const float *__restrict__ fields, uint64_t n, uint3
 void launch_outliers_s(const float *fields, uint64_t n, uint32_t d, const uint32_t *outl_idx,
                        const StreamDesc *desc_outl, uint8_t *out, const Summary *summary,
                        int sms, cudaStream_t s) {
+  note_launch();
   k_outliers_s<<<2 * sms, 256, 0, s>>>(fields, n, d, outl_idx, desc_outl, out, summary);
 }
 

@@ -39,6 +39,7 @@ __global__ void k_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan) {
 }
 
 void launch_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan, cudaStream_t s) {
+  note_launch();
   k_decode_plan<<<1, 32, 0, s>>>(df, d, plan);
 }
 
@@ -85,6 +86,7 @@ __global__ void k_huff_table(const uint8_t *__restrict__ sec, HuffTable *__restr
 }
 
 void launch_huff_table(const uint8_t *sec, HuffTable *T, cudaStream_t s) {
+  note_launch();
   k_huff_table<<<1, 256, 0, s>>>(sec, T);
 }
 
@@ -241,10 +243,12 @@ static void decode_stream_t(const uint8_t *sec, const StreamInfo &info, HuffTabl
   if (info.n == 0) return;
   if (info.coder == 0) {
     unsigned g = (unsigned)std::min<unsigned long long>((info.n + 255) / 256, 8ull * sms);
+    note_launch();
     k_fixed_decode<T><<<g, 256, 0, s>>>(sec, info, out);
   } else {
     launch_huff_table(sec, ht, s);
     unsigned g = (unsigned)std::min<unsigned long long>((info.n_chunks + 127) / 128, 64ull * sms);
+    note_launch();
     k_huff_decode<T><<<g, 128, 0, s>>>(sec, info, ht, out, err);
   }
 }
@@ -337,9 +341,11 @@ void launch_scan_u64(const unsigned long long *in, uint64_t n, int mode, bool in
                      unsigned long long *tile_base, cudaStream_t s) {
   if (n == 0) return;
   const uint64_t tiles = (n + kScanTile - 1) / kScanTile;
+  note_launch();
   if (mode) k_tile_sum<1><<<(unsigned)tiles, 1024, 0, s>>>(in, n, tile_tmp);
   else k_tile_sum<0><<<(unsigned)tiles, 1024, 0, s>>>(in, n, tile_tmp);
   launch_scan_small(tile_tmp, (uint32_t)tiles, tile_base, s);
+  note_launch();
   if (mode) {
     if (inclusive) k_tile_scan<1, true><<<(unsigned)tiles, 1024, 0, s>>>(in, n, tile_base, out);
     else k_tile_scan<1, false><<<(unsigned)tiles, 1024, 0, s>>>(in, n, tile_base, out);
@@ -364,6 +370,7 @@ __global__ void k_check_counts(const unsigned long long *__restrict__ counts, ui
 void launch_check_counts(const unsigned long long *counts, uint64_t m,
                          const unsigned long long *starts_total, uint64_t nb, int *err, int sms,
                          cudaStream_t s) {
+  note_launch();
   k_check_counts<<<2 * sms, 256, 0, s>>>(counts, m, starts_total, nb, err);
 }
 
@@ -479,6 +486,7 @@ static void expand_t(const Plan *plan, const unsigned long long *bid, const unsi
                      uint32_t log2_chunk, float *out, int32_t *qout, int *err, cudaStream_t s) {
   const uint64_t chunks = (nb + kExpThreads - 1) / kExpThreads;
   if (chunks == 0) return;
+  note_launch();
   k_expand_s<D><<<(unsigned)chunks, kExpThreads, 0, s>>>(plan, bid, bstart, M, s_rel, nb, n,
                                                         log2_chunk, out, qout, err);
 }
@@ -520,6 +528,7 @@ __global__ void k_outliers_decode(const Plan *__restrict__ plan, const float *__
 void launch_outliers_decode(const Plan *plan, const float *raw, uint64_t K, uint64_t n, uint32_t d,
                             float *out, int32_t *qout, int sms, cudaStream_t s) {
   if (K == 0) return;
+  note_launch();
   k_outliers_decode<<<2 * sms, 256, 0, s>>>(plan, raw, K, n, d, out, qout);
 }
 

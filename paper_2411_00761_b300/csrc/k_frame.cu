@@ -80,12 +80,14 @@ __global__ void __launch_bounds__(256) k_minmax(const float *__restrict__ fields
 
 void launch_minmax(const float *fields, uint64_t n, uint32_t d, MinMax *mm, int sms,
                    cudaStream_t s) {
+  note_launch();
   k_minmax_init<<<1, 32, 0, s>>>(mm);
   if (n == 0) return;
   uint64_t want = (n + 4095) / 4096;
   int gx = (int)(want < (uint64_t)(4 * sms) ? want : (uint64_t)(4 * sms));
   gx = (gx + (int)d - 1) / (int)d;
   if (gx < 1) gx = 1;
+  note_launch();
   k_minmax<<<dim3(gx, d), 256, 0, s>>>(fields, n, mm);
 }
 
@@ -153,6 +155,7 @@ __global__ void k_plan(const MinMax *mm, uint64_t n, uint32_t d, double eb, int 
 
 void launch_plan(const MinMax *mm, uint64_t n, uint32_t d, double eb, int mode, uint32_t p,
                  uint32_t nbits_target, uint32_t method, Plan *plan, cudaStream_t s) {
+  note_launch();
   k_plan<<<1, 32, 0, s>>>(mm, n, d, eb, mode, p, nbits_target, method, plan);
 }
 
@@ -260,6 +263,7 @@ static void launch_q(const float *fields, uint64_t n, const Plan *plan, uint32_t
     cudaFuncSetAttribute(k_quantize_s<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
+  note_launch();
   k_quantize_s<D><<<tiles, 512, smem, s>>>(fields, n, plan, nb1, span, keys, tile_hist, q);
 }
 
@@ -313,11 +317,13 @@ void launch_element_rules(const float *x, uint64_t n, FieldPlan *fp_dev, int32_t
   if (n == 0) return;
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
+  note_launch();
   k_element_rules<<<(unsigned)blocks, 256, 0, s>>>(x, n, fp_dev, q, xr, viol);
 }
 
 void launch_field_plan(float m, float e, float max_abs, FieldPlan *fp, int *status,
                        cudaStream_t s) {
+  note_launch();
   k_field_plan<<<1, 1, 0, s>>>(m, e, max_abs, fp, status);
 }
 

@@ -95,13 +95,17 @@ void launch_bucket_offsets(uint32_t *tile_hist, int tiles, uint32_t nb1,
                            unsigned long long *bucket_start, unsigned long long *totals,
                            cudaStream_t s) {
   unsigned g = (nb1 + 255) / 256;
+  note_launch();
   k_bucket_colsum<<<g, 256, 0, s>>>(tile_hist, tiles, nb1, totals);
+  note_launch();
   k_scan_small<<<1, 1024, 0, s>>>(totals, nb1, bucket_start);
+  note_launch();
   k_bucket_tileoff<<<g, 256, 0, s>>>(tile_hist, tiles, nb1, bucket_start);
 }
 
 void launch_scan_small(const unsigned long long *in, uint32_t n, unsigned long long *out,
                        cudaStream_t s) {
+  note_launch();
   k_scan_small<<<1, 1024, 0, s>>>(in, n, out);
 }
 
@@ -141,6 +145,7 @@ void launch_scatter(const unsigned long long *keys, uint64_t n, const Plan *plan
     cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
+  note_launch();
   k_scatter<<<tiles, 512, sizeof(uint32_t) * nb1, s>>>(keys, n, plan, nb1, span, tile_off,
                                                       keys_out, idx_out);
 }
@@ -381,6 +386,7 @@ void launch_local(const LocalArgs &a, int ctas, cudaStream_t s) {
     cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
+  note_launch();
   k_local<<<ctas, kLocalThreads, smem, s>>>(a);
 }
 
@@ -506,7 +512,9 @@ void launch_blocks(const Plan *plan, uint32_t nb1, const unsigned long long *buc
                    unsigned long long *maxv, unsigned long long *mcount, int ctas,
                    cudaStream_t s) {
   const uint32_t nb = nb1 - 1;
+  note_launch();
   k_blocks_scan<<<1, 1024, 0, s>>>(bucket_blocks, nb, block_off, prev_nonempty, mcount);
+  note_launch();
   k_blocks<<<ctas, 512, 0, s>>>(plan, nb, bucket_start, bucket_blocks, tmp_bid, tmp_pos,
                                 block_off, prev_nonempty, s_id, s_cnt, hist, maxv);
 }
@@ -526,6 +534,7 @@ __global__ void k_counts_s(const unsigned long long *__restrict__ bucket_start, 
 void launch_counts_s(const unsigned long long *bucket_start, uint32_t nb, uint64_t n,
                      const unsigned long long *mcount, unsigned long long *nvals,
                      unsigned long long *kcount, cudaStream_t s) {
+  note_launch();
   k_counts_s<<<1, 1, 0, s>>>(bucket_start, nb, n, mcount, nvals, kcount);
 }
 
@@ -561,6 +570,7 @@ __global__ void __launch_bounds__(kLocalThreads, 1) k_sort_pairs(
 void launch_sort_pairs(unsigned long long *keys, uint32_t *vals, unsigned long long *keys_alt,
                        uint32_t *vals_alt, const unsigned long long *cnt, int kbits,
                        unsigned long long *keys_out, uint32_t *vals_out, cudaStream_t s) {
+  note_launch();
   k_sort_pairs<<<1, kLocalThreads, 0, s>>>(keys, vals, keys_alt, vals_alt, cnt, kbits, keys_out,
                                            vals_out);
 }

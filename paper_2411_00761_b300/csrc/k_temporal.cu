@@ -71,6 +71,7 @@ void launch_quantize_t(const float *fields, uint64_t n, uint32_t d, const Plan *
   unsigned gx = (unsigned)std::min<unsigned long long>((n + 511) / 512, (unsigned long long)(2 * sms));
   gx = (gx + d - 1) / d;
   if (gx == 0) gx = 1;
+  note_launch();
   k_quantize_t<0><<<dim3(gx, d), 512, 0, s>>>(fields, n, plan, pi, qref, sym, qnew, hist, maxv,
                                               kcount, patch_s, patch_x);
 }
@@ -97,6 +98,7 @@ __global__ void k_patches_write(const unsigned long long *__restrict__ ps,
 void launch_patches_write(const unsigned long long *ps, const uint32_t *order, const float *px,
                           const StreamDesc *od, uint8_t *out, const Summary *summary, int sms,
                           cudaStream_t s) {
+  note_launch();
   k_patches_write<<<sms, 256, 0, s>>>(ps, order, px, od, out, summary);
 }
 
@@ -129,6 +131,7 @@ void launch_recon_t(const Plan *plan, uint64_t n, uint32_t d, const uint32_t *sy
                     cudaStream_t s) {
   if (n == 0) return;
   unsigned gx = (unsigned)std::min<unsigned long long>((n + 511) / 512, (unsigned long long)(4 * sms));
+  note_launch();
   k_recon_t<<<dim3(gx, d), 512, 0, s>>>(plan, n, sym, qref, out, qnew, err);
 }
 
@@ -150,6 +153,7 @@ __global__ void k_patches_apply(const uint8_t *__restrict__ sec, uint64_t K, uin
 void launch_patches_apply(const uint8_t *sec, uint64_t K, uint64_t nd, float *out, int *err,
                           int sms, cudaStream_t s) {
   if (K == 0) return;
+  note_launch();
   k_patches_apply<<<sms, 256, 0, s>>>(sec, K, nd, out, err);
 }
 

@@ -10,6 +10,8 @@
 
 using namespace lcp;
 
+unsigned long long lcp::g_launches = 0;
+
 namespace {
 
 constexpr uint32_t kLog2Chunk = 10;  // chunk of 1024 symbols
@@ -91,10 +93,27 @@ bool aligned16(const void *p) { return (((uintptr_t)p) & 15u) == 0; }
 
 }  // namespace
 
+namespace {
+// Stage marks: prof_begin(c, name, s) ... prof_end(c, s) around one kernel
+void prof_reset(lcp_ctx *c);
+void prof_begin(lcp_ctx *c, const char *name, cudaStream_t s);
+void prof_end(lcp_ctx *c, cudaStream_t s);
+}  // namespace
+
+// per-kernel timing of the last call (events recorded on the call's stream)
+struct Profile {
+  bool on = false;
+  int n = 0;
+  char names[32][32];
+  cudaEvent_t ev[64];
+  bool made = false;
+};
+
 struct lcp_ctx {
   int device = 0;
   int sms = 148;
   Workspace ws;
+  Profile prof;
   Plan *h_plan = nullptr;
   Summary *h_sum = nullptr;
   uint8_t *h_stage = nullptr;  // header staging (pinned)
@@ -114,6 +133,27 @@ struct lcp_traj {
   uint64_t s_est = 0;
   DevBuf prev_q, prev_pi, anc_q, anc_pi, new_q, new_pi;
 };
+
+namespace {
+void prof_reset(lcp_ctx *c) { c->prof.n = 0; }
+void prof_begin(lcp_ctx *c, const char *name, cudaStream_t s) {
+  Profile &P = c->prof;
+  if (!P.on || P.n >= 32) return;
+  if (!P.made) {
+    for (int i = 0; i < 64; ++i) cudaEventCreate(&P.ev[i]);
+    P.made = true;
+  }
+  strncpy(P.names[P.n], name, 31);
+  P.names[P.n][31] = 0;
+  cudaEventRecord(P.ev[2 * P.n], s);
+}
+void prof_end(lcp_ctx *c, cudaStream_t s) {
+  Profile &P = c->prof;
+  if (!P.on || P.n >= 32) return;
+  cudaEventRecord(P.ev[2 * P.n + 1], s);
+  ++P.n;
+}
+}  // namespace
 
 // ===========================================================================
 // internal: LCP-S compression of one frame
@@ -163,7 +203,9 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   const bool want_perm = perm_out != nullptr;
   const bool want_q = q_slot_out != nullptr;
   // 1-2. min/max and plan
+  prof_begin(c, "s.minmax", s);
   launch_minmax(X, n, d, P<MinMax>(w.mm), sms, s);
+  prof_end(c, s);
   launch_plan(P<MinMax>(w.mm), n, d, eb, mode, p, bits_target(n), 0, P<Plan>(w.plan), s);
   CK(cudaGetLastError());
   int st = read_plan(c, s);
@@ -193,14 +235,20 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   }
   if (want_q) TRY(grow(w.q_in, nn * 4 * d));
   // 3. quantize + keys + bucket histograms
+  prof_begin(c, "s.quantize", s);
   launch_quantize_s(X, n, d, P<Plan>(w.plan), nb1, tiles, P<unsigned long long>(w.keys),
                     P<uint32_t>(w.tile_hist), want_q ? P<int32_t>(w.q_in) : nullptr, s);
+  prof_end(c, s);
   // 4. bucket offsets, 5. scatter
+  prof_begin(c, "s.bucket_offsets", s);
   launch_bucket_offsets(P<uint32_t>(w.tile_hist), tiles, nb1, P<unsigned long long>(w.bstart),
                         P<unsigned long long>(w.btot), s);
+  prof_end(c, s);
+  prof_begin(c, "s.scatter", s);
   launch_scatter(P<unsigned long long>(w.keys), n, P<Plan>(w.plan), nb1, tiles,
                  P<uint32_t>(w.tile_hist), P<unsigned long long>(w.keys2),
                  want_perm ? P<uint32_t>(w.idx2) : nullptr, s);
+  prof_end(c, s);
   CK(cudaGetLastError());
   // 6. per-bucket sort + segmentation
   CK(cudaMemsetAsync(w.hist.p, 0, 3ull * kAlpha * 4, s));
@@ -225,9 +273,12 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   la.outl_idx = P<uint32_t>(w.outl_idx);
   la.log2_chunk = kLog2Chunk;
   la.n = n;
+  prof_begin(c, "s.local_sort", s);
   launch_local(la, sms, s);
+  prof_end(c, s);
   CK(cudaGetLastError());
   // 7. blocks: ids and counts
+  prof_begin(c, "s.blocks", s);
   launch_blocks(P<Plan>(w.plan), nb1, P<unsigned long long>(w.bstart), P<uint32_t>(w.bblocks),
                 P<unsigned long long>(w.tmp_bid), P<uint32_t>(w.tmp_pos),
                 P<unsigned long long>(w.boff), P<int>(w.prevne), P<unsigned long long>(w.s_id),
@@ -235,7 +286,9 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
                 P<unsigned long long>(w.maxv), P<unsigned long long>(w.mcount), 2 * sms, s);
   launch_counts_s(P<unsigned long long>(w.bstart), nb, n, P<unsigned long long>(w.mcount),
                   P<unsigned long long>(w.nvals), P<unsigned long long>(w.kcount), s);
+  prof_end(c, s);
   // 8. codebooks and the container layout
+  prof_begin(c, "s.codebook", s);
   launch_codebook(3, P<uint32_t>(w.hist), P<unsigned long long>(w.maxv),
                   P<unsigned long long>(w.nvals), kLog2Chunk, P<StreamDesc>(w.desc),
                   P<uint32_t>(w.codes), P<uint8_t>(w.lens), P<uint16_t>(w.tables), s);
@@ -255,9 +308,11 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   L.cap = size_only ? ~0ull : cap;
   L.summary = P<Summary>(w.summary);
   launch_layout(L, sms, size_only, s);
+  prof_end(c, s);
   CK(cudaGetLastError());
   if (!size_only) {
     // 9. payloads
+    prof_begin(c, "s.encode", s);
     StreamDesc *D = P<StreamDesc>(w.desc);
     launch_encode_u64(P<unsigned long long>(w.s_id), n, D + 0, P<uint32_t>(w.codes),
                       P<uint8_t>(w.lens), kLog2Chunk, out, P<Summary>(w.summary),
@@ -272,6 +327,7 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
                       P<unsigned long long>(w.chunk_bits), P<unsigned long long>(w.chunk_off), sms,
                       s);
     launch_outliers_s(X, n, d, P<uint32_t>(w.outl_idx), D + 3, out, P<Summary>(w.summary), sms, s);
+    prof_end(c, s);
     CK(cudaGetLastError());
   }
   TRY(read_summary(c, s));
@@ -302,10 +358,13 @@ int compress_t_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   CK(cudaMemsetAsync(w.maxv.p, 0, 4 * 8, s));
   CK(cudaMemsetAsync(w.kcount.p, 0, 8, s));
   CK(cudaMemsetAsync(w.mcount.p, 0, 8, s));
+  prof_begin(c, "t.quantize", s);
   launch_quantize_t(X, n, d, P<Plan>(w.plan), pi, qref, P<uint32_t>(w.sym), qnew,
                     P<uint32_t>(w.hist), P<unsigned long long>(w.maxv),
                     P<unsigned long long>(w.kcount), P<unsigned long long>(w.patch_s),
                     P<float>(w.patch_x), sms, s);
+  prof_end(c, s);
+  note_launch();
   k_set_u64<<<1, 1, 0, s>>>(P<unsigned long long>(w.nvals), (unsigned long long)(n * d));
   launch_codebook(1, P<uint32_t>(w.hist), P<unsigned long long>(w.maxv),
                   P<unsigned long long>(w.nvals), kLog2Chunk, P<StreamDesc>(w.desc),
@@ -339,6 +398,7 @@ int compress_t_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
     TRY(grow(w.patch_i2, nd * 4));
     TRY(grow(w.patch_so, nd * 8));
     TRY(grow(w.patch_io, nd * 4));
+    note_launch();
     k_iota<<<sms, 256, 0, s>>>(P<uint32_t>(w.patch_i), P<unsigned long long>(w.kcount));
     int kbits = (int)bitlen64(n * d > 0 ? n * d - 1 : 0);
     launch_sort_pairs(P<unsigned long long>(w.patch_s), P<uint32_t>(w.patch_i),
@@ -659,6 +719,7 @@ lcp_status lcp_compress(lcp_ctx *c, lcp_traj *traj, const float *d_fields, uint6
   DeviceGuard g(c->device);
   if (!g.ok) return LCP_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
+  prof_reset(c);
   if (traj) {
     int ch = LCP_SPATIAL;
     st = traj_compress(c, traj, d_fields, n, d, eb, mode, method, (uint8_t *)d_out, out_cap,
@@ -868,35 +929,46 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
     const uint64_t tiles = mm / 4096 + 2;
     TRY(grow(w.scan_tmp, tiles * 8));
     TRY(grow(w.scan_base, (tiles + 1) * 8));
+    prof_begin(c, "d.streams", s);
     launch_decode_u64(in + h.off[0], h.si[0], ht + 0, P<unsigned long long>(w.s_id), err, sms, s);
     launch_decode_u64(in + h.off[1], h.si[1], ht + 1, P<unsigned long long>(w.s_cnt), err, sms, s);
     launch_decode_u32(in + h.off[2], h.si[2], ht + 2, P<uint32_t>(w.s_rel), err, sms, s);
+    prof_end(c, s);
     if (M > 0) {
       unsigned long long *tt = P<unsigned long long>(w.scan_tmp);
       unsigned long long *tb = P<unsigned long long>(w.scan_base);
+      prof_begin(c, "d.block_scans", s);
       launch_scan_u64(P<unsigned long long>(w.s_id), M, 0, true, P<unsigned long long>(w.bid), tt,
                       tb, s);
       launch_scan_u64(P<unsigned long long>(w.s_cnt), M, 1, true,
                       P<unsigned long long>(w.counts), tt, tb, s);
       launch_scan_u64(P<unsigned long long>(w.counts), M, 0, false,
                       P<unsigned long long>(w.starts), tt, tb, s);
+      note_launch();
       k_counts_total<<<1, 1, 0, s>>>(P<unsigned long long>(w.starts),
                                      P<unsigned long long>(w.counts), M,
                                      P<unsigned long long>(w.btot));
       launch_check_counts(P<unsigned long long>(w.counts), M, P<unsigned long long>(w.btot), nb,
                           err, sms, s);
+      prof_end(c, s);
+      prof_begin(c, "d.expand", s);
       launch_expand_s(h.d, P<Plan>(w.plan), P<unsigned long long>(w.bid),
                       P<unsigned long long>(w.starts), M, P<uint32_t>(w.s_rel), nb, n,
                       h.log2_chunk, out, qout, err, s);
+      prof_end(c, s);
     }
     launch_outliers_decode(P<Plan>(w.plan), reinterpret_cast<const float *>(in + h.off[3]), h.K,
                            n, h.d, out, qout, sms, s);
   } else {
     const uint64_t nd = std::max<uint64_t>(n * h.d, 1);
     TRY(grow(w.sym, nd * 4));
+    prof_begin(c, "t.decode_stream", s);
     launch_decode_u32(in + h.off[0], h.si[0], ht, P<uint32_t>(w.sym), err, sms, s);
+    prof_end(c, s);
     const int32_t *qref = ra ? P<int32_t>(t->anc_q) : P<int32_t>(t->prev_q);
+    prof_begin(c, "t.recon", s);
     launch_recon_t(P<Plan>(w.plan), n, h.d, P<uint32_t>(w.sym), qref, out, qout, err, sms, s);
+    prof_end(c, s);
     launch_patches_apply(in + h.off[1], h.K, n * h.d, out, err, sms, s);
   }
   CK(cudaGetLastError());
@@ -930,6 +1002,7 @@ lcp_status lcp_decompress(lcp_ctx *c, lcp_traj *traj, const void *d_in, size_t i
   if (!c) return LCP_ERR_ARG;
   DeviceGuard g(c->device);
   if (!g.ok) return LCP_ERR_CUDA;
+  prof_reset(c);
   return (lcp_status)decompress_impl(c, traj, (const uint8_t *)d_in, in_size, d_out, n_cap, n_out,
                                      d_fields, (cudaStream_t)stream);
 }
@@ -989,6 +1062,32 @@ lcp_status lcp_quantize(const float *d_x, uint64_t n, float m, float e, float ma
   cudaFreeAsync(fp, s);
   cudaStreamSynchronize(s);
   return r;
+}
+
+uint64_t lcp_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+lcp_status lcp_ctx_profile(lcp_ctx *c, int enable) {
+  if (!c) return LCP_ERR_ARG;
+  c->prof.on = enable != 0;
+  c->prof.n = 0;
+  return LCP_OK;
+}
+
+int lcp_ctx_profile_read(lcp_ctx *c, char *names, float *ms, int cap) {
+  if (!c || !c->prof.on) return 0;
+  DeviceGuard g(c->device);
+  int k = 0;
+  for (; k < c->prof.n && k < cap; ++k) {
+    float t = 0.0f;
+    if (cudaEventSynchronize(c->prof.ev[2 * k + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, c->prof.ev[2 * k], c->prof.ev[2 * k + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      t = -1.0f;
+    }
+    if (ms) ms[k] = t;
+    if (names) memcpy(names + 32 * k, c->prof.names[k], 32);
+  }
+  return k;
 }
 
 }  // extern "C"

@@ -7,6 +7,10 @@
 
 namespace lcp {
 
+// kernels launched by this library in this process (all threads)
+extern unsigned long long g_launches;
+inline void note_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }
+
 // container header fields the decoder needs per field
 struct DecodeFields {
   float m[kMaxD];

@@ -41,6 +41,9 @@ SIGNATURES = {
     "lcp_traj_create": (C.c_int, [_vp, _u32, _u32, C.POINTER(C.c_void_p)]),
     "lcp_traj_destroy": (C.c_int, [_vp]),
     "lcp_quantize": (C.c_int, [_vp, _u64, C.c_float, C.c_float, C.c_float, _vp, _vp, _vp, _vp]),
+    "lcp_ctx_profile": (C.c_int, [_vp, C.c_int]),
+    "lcp_kernel_launches": (_u64, []),
+    "lcp_ctx_profile_read": (C.c_int, [_vp, C.c_char_p, C.POINTER(C.c_float), C.c_int]),
 }
 
 
@@ -93,6 +96,11 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def kernel_launches() -> int:
+    """CUDA kernels the library has launched in this process."""
+    return int(load().lcp_kernel_launches())
+
+
 def max_compressed_size(n: int, d: int) -> int:
     return int(load().lcp_max_compressed_size(n, d))
 
@@ -119,6 +127,18 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def profile(self, enable: bool = True):
+        """Per-kernel CUDA-event timing of subsequent calls."""
+        _check(_lib.lcp_ctx_profile(self.h, 1 if enable else 0), "lcp_ctx_profile")
+
+    def profile_read(self) -> list[tuple[str, float]]:
+        """(stage, ms) of the most recent call."""
+        names = C.create_string_buffer(32 * 32)
+        ms = (C.c_float * 32)()
+        k = _lib.lcp_ctx_profile_read(self.h, names, ms, 32)
+        raw = names.raw
+        return [(raw[32 * i:32 * i + 32].split(b"\0")[0].decode(), float(ms[i])) for i in range(k)]
 
     def reserve(self, n: int, d: int):
         _check(_lib.lcp_ctx_reserve(self.h, n, d), "lcp_ctx_reserve")
