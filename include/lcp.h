@@ -185,6 +185,33 @@ LCP_API int lcp_ctx_profile_read(lcp_ctx *ctx, char *names, float *ms, int cap);
 LCP_API lcp_status lcp_quantize(const float *d_x, uint64_t n, float m, float e, float max_abs,
                         int32_t *d_q, float *d_xr, uint8_t *d_viol, void *stream);
 
+/*
+ * The element rules of lcp_quantize for callers that cannot allocate device
+ * memory: code that runs inside an application which owns the GPU's memory
+ * through its own pool (a cudaMalloc would bypass the pool and synchronize
+ * the device), or loops that forbid allocation once running.  The paper has
+ * no counterpart; this is library plumbing.
+ *
+ * Same inputs and outputs as lcp_quantize, bit for bit, plus *n_violations
+ * (optional, host): how many values break the bound.  The call allocates
+ * nothing: its scratch (per-block counts, a completion counter, the status)
+ * is one fixed device array of about 16.5 KB inside the library, which every
+ * GPU that loads the library holds until the process exits.
+ *   - n may be at most LCP_NOALLOC_MAX_ELEMENTS; larger n returns LCP_ERR_ARG
+ *     before any work is queued.
+ *   - The first call on each device resolves the device address of that
+ *     array (cudaGetSymbolAddress); make that first call before any stream
+ *     capture.
+ *   - All calls share the array: the call clears the counter it needs, but
+ *     two calls whose work overlaps on the GPU (on different streams, or
+ *     from different threads) race on it.  Serialize them.
+ * Synchronizes `stream`.
+ */
+#define LCP_NOALLOC_MAX_ELEMENTS 16777216ull
+LCP_API lcp_status lcp_quantize_noalloc(const float *d_x, uint64_t n, float m, float e,
+                                        float max_abs, int32_t *d_q, float *d_xr,
+                                        uint8_t *d_viol, uint64_t *n_violations, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -43,6 +43,8 @@ SIGNATURES = {
     "lcp_quantize": (C.c_int, [_vp, _u64, C.c_float, C.c_float, C.c_float, _vp, _vp, _vp, _vp]),
     "lcp_ctx_profile": (C.c_int, [_vp, C.c_int]),
     "lcp_kernel_launches": (_u64, []),
+    "lcp_quantize_noalloc": (C.c_int, [_vp, _u64, C.c_float, C.c_float, C.c_float, _vp, _vp, _vp,
+                                       C.POINTER(_u64), _vp]),
     "lcp_ctx_profile_read": (C.c_int, [_vp, C.c_char_p, C.POINTER(C.c_float), C.c_int]),
 }
 
@@ -241,3 +243,21 @@ def quantize(x: torch.Tensor, m: float, e: float, max_abs: float | None = None, 
     _check(_lib.lcp_quantize(_ptr(x), n, m, e, max_abs, _ptr(q), _ptr(xr), _ptr(v),
                              _stream(stream)), "lcp_quantize")
     return q, xr, v.bool()
+
+
+NOALLOC_MAX_ELEMENTS = 16777216
+
+
+def quantize_noalloc(x: torch.Tensor, m: float, e: float, max_abs: float, q: torch.Tensor,
+                     xr: torch.Tensor, viol: torch.Tensor, stream=None) -> int:
+    """The element rules without any device allocation (lcp_quantize_noalloc),
+    for callers that cannot allocate: writes into the caller's q (int32), xr
+    (float32) and viol (uint8) and returns how many values break the bound.
+    At most NOALLOC_MAX_ELEMENTS values per call; calls must not overlap on
+    the GPU (they share one fixed scratch array)."""
+    load()
+    nv = C.c_uint64(0)
+    _check(_lib.lcp_quantize_noalloc(_ptr(x), x.numel(), m, e, max_abs, _ptr(q), _ptr(xr),
+                                     _ptr(viol), C.byref(nv), _stream(stream)),
+           "lcp_quantize_noalloc")
+    return nv.value
