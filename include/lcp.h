@@ -168,6 +168,9 @@ LCP_API lcp_status lcp_traj_destroy(lcp_traj *traj);
  * events.  The paper has no counterpart: this is measurement plumbing.
  */
 LCP_API lcp_status lcp_ctx_profile(lcp_ctx *ctx, int enable);
+/* Description of the last failed CUDA runtime call on this thread (empty if
+ * none): the call, its place in the library and CUDA's error string. */
+LCP_API const char *lcp_last_error(void);
 /* Number of CUDA kernels this library has launched in this process. */
 LCP_API uint64_t lcp_kernel_launches(void);
 LCP_API int lcp_ctx_profile_read(lcp_ctx *ctx, char *names, float *ms, int cap);

@@ -36,6 +36,31 @@ __global__ void k_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan) {
       stride *= plan->f[k].bn;
     }
   }
+  if (f < (int)d) {
+    // floor(r / bn) for r < 2^63: m = ceil(2^(63+l) / bn), l = ceil(log2 bn), then
+    // floor(r m / 2^(63+l)) = floor(r / bn) (Granlund-Montgomery, division by
+    // invariant integers using multiplication, Thm. 4.2)
+    const unsigned long long bn = plan->f[f].bn;
+    if (bn <= 1) {
+      plan->f[f].bmagic = 0;
+      plan->f[f].bshift = 255;
+    } else {
+      uint32_t l = 0;
+      while ((1ull << l) < bn) ++l;
+      // binary long division of 2^(63+l) by bn; the quotient fits 64 bits
+      unsigned long long q = 0, rem = 0;
+      for (int bit = 63 + (int)l; bit >= 0; --bit) {
+        rem = (rem << 1) | (bit == 63 + (int)l ? 1ull : 0ull);
+        q <<= 1;
+        if (rem >= bn) {
+          rem -= bn;
+          q |= 1ull;
+        }
+      }
+      plan->f[f].bmagic = q + (rem != 0 ? 1ull : 0ull);
+      plan->f[f].bshift = l - 1;
+    }
+  }
 }
 
 void launch_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan, cudaStream_t s) {
@@ -142,14 +167,21 @@ struct BitReader {
   }
 };
 
+// One warp decodes 32 consecutive chunks, lane l the chunk c0 + l, 32 symbols
+// per round into shared memory; the warp then writes each lane's 32 values
+// with coalesced stores.
+constexpr int kDecWarps = 2;
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_huff_decode(const uint8_t *__restrict__ sec,
-                                                      StreamInfo info,
-                                                      const HuffTable *__restrict__ HT,
-                                                      T *__restrict__ out, int *__restrict__ err) {
+__global__ void __launch_bounds__(32 * kDecWarps) k_huff_decode(const uint8_t *__restrict__ sec,
+                                                                StreamInfo info,
+                                                                const HuffTable *__restrict__ HT,
+                                                                T *__restrict__ out,
+                                                                int *__restrict__ err) {
   __shared__ uint32_t fast[1 << kFastBits];
   __shared__ uint32_t first[kLmax + 1], index[kLmax + 1], count[kLmax + 1];
   __shared__ uint16_t syms[kAlpha];
+  __shared__ T stage[kDecWarps][32][33];
   for (int i = threadIdx.x; i < (1 << kFastBits); i += blockDim.x) fast[i] = HT->fast[i];
   for (int i = threadIdx.x; i < (int)HT->used && i < kAlpha; i += blockDim.x) syms[i] = HT->syms[i];
   if (threadIdx.x <= kLmax) {
@@ -162,44 +194,70 @@ __global__ void __launch_bounds__(128) k_huff_decode(const uint8_t *__restrict__
     if (threadIdx.x == 0) atomicExch(err, 1);
     return;
   }
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const unsigned long long cs = 1ull << info.log2_chunk;
   const uint8_t *ct = sec + pad16(80ull + 2ull * info.used);
   const uint32_t *pl = reinterpret_cast<const uint32_t *>(ct + pad16(8ull * info.n_chunks));
   const unsigned long long nwords = words_of(info.payload_bits);
-  for (unsigned long long c = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-       c < info.n_chunks; c += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long lo = c * cs, hi = min(info.n, lo + cs);
-    const unsigned long long pos = (unsigned long long)reinterpret_cast<const uint32_t *>(ct)[2 * c] |
-                                   ((unsigned long long)reinterpret_cast<const uint32_t *>(ct)[2 * c + 1] << 32);
-    if (pos > info.payload_bits) {
-      atomicExch(err, 1);
-      continue;
-    }
+  const unsigned long long groups = (info.n_chunks + 31) / 32;
+  for (unsigned long long g = (unsigned long long)blockIdx.x * kDecWarps + wl; g < groups;
+       g += (unsigned long long)gridDim.x * kDecWarps) {
+    const unsigned long long c = g * 32 + lane;
+    const bool act = c < info.n_chunks;
+    const unsigned long long lo = c * cs;
+    const unsigned long long hi = act ? min(info.n, lo + cs) : lo;
     BitReader br;
-    br.init(pl, nwords, pos);
-    for (unsigned long long i = lo; i < hi; ++i) {
-      uint32_t e = fast[br.peek(kFastBits)];
-      uint32_t sym;
-      if (e) {
-        sym = e >> 5;
-        br.skip((int)(e & 31u));
-      } else {
-        int L = kFastBits + 1;
-        uint32_t code = 0;
-        for (; L <= kLmax; ++L) {
-          code = br.peek(L);
-          if (code - first[L] < count[L]) break;
-        }
-        if (L > kLmax) {
-          atomicExch(err, 1);
-          break;
-        }
-        sym = syms[index[L] + (code - first[L])];
-        br.skip(L);
+    bool ok = true;
+    if (act) {
+      const unsigned long long pos =
+          (unsigned long long)reinterpret_cast<const uint32_t *>(ct)[2 * c] |
+          ((unsigned long long)reinterpret_cast<const uint32_t *>(ct)[2 * c + 1] << 32);
+      if (pos > info.payload_bits) {
+        atomicExch(err, 1);
+        ok = false;
       }
-      unsigned long long v = sym;
-      if (sym == (uint32_t)kEsc) v = br.read((int)info.width);
-      out[i] = (T)v;
+      br.init(pl, nwords, ok ? pos : 0ull);
+    }
+    const unsigned long long mine = (act && ok) ? hi - lo : 0ull;
+    for (unsigned long long r0 = 0; r0 < cs; r0 += 32) {
+      // decode up to 32 symbols of this lane's chunk
+      for (int k = 0; k < 32; ++k) {
+        if (r0 + k >= mine) break;
+        uint32_t e = fast[br.peek(kFastBits)];
+        uint32_t sym;
+        if (e) {
+          sym = e >> 5;
+          br.skip((int)(e & 31u));
+        } else {
+          int L = kFastBits + 1;
+          uint32_t code = 0;
+          for (; L <= kLmax; ++L) {
+            code = br.peek(L);
+            if (code - first[L] < count[L]) break;
+          }
+          if (L > kLmax) {
+            atomicExch(err, 1);
+            sym = 0;
+            L = 1;
+          } else {
+            sym = syms[index[L] + (code - first[L])];
+          }
+          br.skip(L);
+        }
+        unsigned long long v = sym;
+        if (sym == (uint32_t)kEsc) v = br.read((int)info.width);
+        stage[wl][lane][k] = (T)v;
+      }
+      __syncwarp();
+      // coalesced write-out: row l holds chunk (g*32 + l) symbols r0..r0+31
+      for (int l = 0; l < 32; ++l) {
+        const unsigned long long cl = g * 32 + l;
+        if (cl >= info.n_chunks) break;
+        const unsigned long long base = cl * cs + r0;
+        const unsigned long long lim = min(info.n, cl * cs + cs);
+        if (base + lane < lim) out[base + lane] = stage[wl][l][lane];
+      }
+      __syncwarp();
     }
   }
 }
@@ -247,9 +305,11 @@ static void decode_stream_t(const uint8_t *sec, const StreamInfo &info, HuffTabl
     k_fixed_decode<T><<<g, 256, 0, s>>>(sec, info, out);
   } else {
     launch_huff_table(sec, ht, s);
-    unsigned g = (unsigned)std::min<unsigned long long>((info.n_chunks + 127) / 128, 64ull * sms);
+    const unsigned long long groups = (info.n_chunks + 31) / 32;
+    unsigned g = (unsigned)std::min<unsigned long long>((groups + kDecWarps - 1) / kDecWarps,
+                                                        64ull * sms);
     note_launch();
-    k_huff_decode<T><<<g, 128, 0, s>>>(sec, info, ht, out, err);
+    k_huff_decode<T><<<g, 32 * kDecWarps, 0, s>>>(sec, info, ht, out, err);
   }
 }
 
@@ -355,6 +415,190 @@ void launch_scan_u64(const unsigned long long *in, uint64_t n, int mode, bool in
   }
 }
 
+// ---------------------------------------------------------------------------
+// block scans of an LCP-S frame, fused: block ids (inclusive scan of the id
+// deltas), counts (inclusive scan of the count deltas) and block starts
+// (exclusive scan of the counts), plus, per tile of kExpTile particles, the
+// block holding the tile's first particle.  Tile aggregates: id sum A, count
+// delta sum B, and P = sum of the local inclusive count prefixes, so that the
+// counts of a tile with carry-in C sum to len * C + P.
+// ---------------------------------------------------------------------------
+constexpr int kBsTile = 4096;
+constexpr int kExpTile = 1024;
+
+struct BsAgg {
+  unsigned long long a, b, p, len;
+};
+
+template <int THREADS>
+__device__ __forceinline__ unsigned long long blk_exscan(unsigned long long v,
+                                                         unsigned long long *s_warp,
+                                                         unsigned long long &total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long t = lane < THREADS / 32 ? s_warp[lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    s_warp[lane] = t;
+  }
+  __syncthreads();
+  unsigned long long base = w > 0 ? s_warp[w - 1] : 0ull;
+  total = s_warp[THREADS / 32 - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+__global__ void __launch_bounds__(1024) k_bscan_sum(const unsigned long long *__restrict__ sid,
+                                                    const unsigned long long *__restrict__ scnt,
+                                                    uint64_t M, BsAgg *__restrict__ agg) {
+  __shared__ unsigned long long s_warp[32];
+  constexpr int per = kBsTile / 1024;
+  const uint64_t lo = (uint64_t)blockIdx.x * kBsTile + (uint64_t)threadIdx.x * per;
+  unsigned long long a = 0, b = 0, d[per];
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    const uint64_t i = lo + k;
+    d[k] = 0;
+    if (i < M) {
+      a += sid[i];
+      d[k] = (unsigned long long)unzigzag(scnt[i]);
+    }
+    b += d[k];
+  }
+  unsigned long long ta, tb;
+  blk_exscan<1024>(a, s_warp, ta);
+  unsigned long long run = blk_exscan<1024>(b, s_warp, tb);  // prefix of deltas before me
+  unsigned long long p = 0;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    run += d[k];
+    if (lo + k < M) p += run;
+  }
+  unsigned long long tp;
+  blk_exscan<1024>(p, s_warp, tp);
+  if (threadIdx.x == 0) {
+    const uint64_t t0 = (uint64_t)blockIdx.x * kBsTile;
+    agg[blockIdx.x] = BsAgg{ta, tb, tp, (M - t0) < (uint64_t)kBsTile ? M - t0 : (uint64_t)kBsTile};
+  }
+}
+
+// tile bases: id base, count carry-in, start base (one CTA)
+__global__ void __launch_bounds__(1024) k_bscan_top(BsAgg *__restrict__ agg, uint32_t tiles) {
+  __shared__ unsigned long long s_warp[32];
+  const uint32_t per = (tiles + 1023) / 1024;
+  const uint32_t lo = threadIdx.x * per, hi = min(tiles, lo + per);
+  unsigned long long sa = 0, sb = 0;
+  for (uint32_t t = lo; t < hi; ++t) {
+    sa += agg[t].a;
+    sb += agg[t].b;
+  }
+  unsigned long long tot;
+  unsigned long long ra = blk_exscan<1024>(sa, s_warp, tot);
+  unsigned long long rb = blk_exscan<1024>(sb, s_warp, tot);
+  // totals of counts per tile need the carry-in of each tile
+  unsigned long long st = 0;
+  {
+    unsigned long long cb = rb;
+    for (uint32_t t = lo; t < hi; ++t) {
+      st += agg[t].len * cb + agg[t].p;
+      cb += agg[t].b;
+    }
+  }
+  unsigned long long rs = blk_exscan<1024>(st, s_warp, tot);
+  for (uint32_t t = lo; t < hi; ++t) {
+    const BsAgg g = agg[t];
+    agg[t] = BsAgg{ra, rb, rs, g.len};
+    ra += g.a;
+    rs += g.len * rb + g.p;
+    rb += g.b;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_bscan_apply(const unsigned long long *__restrict__ sid,
+                                                      const unsigned long long *__restrict__ scnt,
+                                                      uint64_t M, const BsAgg *__restrict__ agg,
+                                                      unsigned long long *__restrict__ bid,
+                                                      unsigned long long *__restrict__ bstart,
+                                                      uint32_t *__restrict__ tile_first,
+                                                      uint64_t nb, int *__restrict__ err) {
+  __shared__ unsigned long long s_warp[32];
+  constexpr int per = kBsTile / 1024;
+  const BsAgg base = agg[blockIdx.x];
+  const uint64_t lo = (uint64_t)blockIdx.x * kBsTile + (uint64_t)threadIdx.x * per;
+  unsigned long long a[per], d[per];
+  unsigned long long sa = 0, sb = 0;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    const uint64_t i = lo + k;
+    a[k] = 0;
+    d[k] = 0;
+    if (i < M) {
+      a[k] = sid[i];
+      d[k] = (unsigned long long)unzigzag(scnt[i]);
+    }
+    sa += a[k];
+    sb += d[k];
+  }
+  unsigned long long tot;
+  unsigned long long ra = base.a + blk_exscan<1024>(sa, s_warp, tot);
+  unsigned long long rd = blk_exscan<1024>(sb, s_warp, tot);  // local count-delta prefix
+  // local counts c_i = carry + local inclusive delta prefix; starts need their
+  // exclusive prefix within the tile
+  unsigned long long cs = 0, lp = rd;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    lp += d[k];
+    if (lo + k < M) cs += base.b + lp;
+  }
+  unsigned long long rs = base.p + blk_exscan<1024>(cs, s_warp, tot);
+  lp = rd;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    const uint64_t i = lo + k;
+    lp += d[k];
+    ra += a[k];
+    if (i < M) {
+      const long long c = (long long)(base.b + lp);
+      bid[i] = ra;
+      bstart[i] = rs;
+      if (c < 1 || (unsigned long long)c > nb || rs + (unsigned long long)c > nb) atomicExch(err, 1);
+      // tiles whose first particle lies in this block
+      const unsigned long long e = rs + (unsigned long long)(c > 0 ? c : 0);
+      if (e <= nb) {
+        for (unsigned long long t = (rs + kExpTile - 1) / kExpTile; t * kExpTile < e; ++t)
+          tile_first[t] = (uint32_t)i;
+      }
+      if (i == M - 1 && e != nb) atomicExch(err, 1);
+      rs += (unsigned long long)(c > 0 ? c : 0);
+    }
+  }
+}
+
+void launch_block_scans(const unsigned long long *sid, const unsigned long long *scnt, uint64_t M,
+                        void *agg, unsigned long long *bid, unsigned long long *bstart,
+                        uint32_t *tile_first, uint64_t nb, int *err, cudaStream_t s) {
+  if (M == 0) return;
+  const uint64_t tiles = (M + kBsTile - 1) / kBsTile;
+  BsAgg *g = reinterpret_cast<BsAgg *>(agg);
+  note_launch();
+  k_bscan_sum<<<(unsigned)tiles, 1024, 0, s>>>(sid, scnt, M, g);
+  note_launch();
+  k_bscan_top<<<1, 1024, 0, s>>>(g, (uint32_t)tiles);
+  note_launch();
+  k_bscan_apply<<<(unsigned)tiles, 1024, 0, s>>>(sid, scnt, M, g, bid, bstart, tile_first, nb, err);
+}
+
 // counts (inclusive scan of count deltas) must be >= 1 and sum to nb
 __global__ void k_check_counts(const unsigned long long *__restrict__ counts, uint64_t m,
                                const unsigned long long *__restrict__ starts_total, uint64_t nb,
@@ -383,10 +627,9 @@ template <int D>
 __global__ void __launch_bounds__(kExpThreads) k_expand_s(
     const Plan *__restrict__ plan, const unsigned long long *__restrict__ bid,
     const unsigned long long *__restrict__ bstart, uint64_t M, const uint32_t *__restrict__ s_rel,
-    uint64_t nb, uint64_t n, uint32_t log2_chunk, float *__restrict__ out,
-    int32_t *__restrict__ qout, int *__restrict__ err) {
+    uint64_t nb, uint64_t n, uint32_t log2_chunk, const uint32_t *__restrict__ tile_first,
+    float *__restrict__ out, int32_t *__restrict__ qout, int *__restrict__ err) {
   __shared__ Plan sP;
-  __shared__ unsigned long long s_first;
   __shared__ unsigned long long sb_start[kExpThreads + 1];
   __shared__ uint32_t sb_f[kExpThreads + 1][D];
   __shared__ uint32_t s_wv[32], s_wf[32];
@@ -396,29 +639,23 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_s(
   const uint64_t cmask = (1ull << log2_chunk) - 1ull;
   const uint64_t lo = (uint64_t)blockIdx.x * kExpThreads;
   const uint64_t hi = min(nb, lo + kExpThreads);
-  if (threadIdx.x == 0) {
-    // last block whose start <= lo
-    uint64_t a = 0, b = M;  // answer in [a, b)
-    while (b - a > 1) {
-      uint64_t mid = (a + b) >> 1;
-      if (bstart[mid] <= lo) a = mid;
-      else b = mid;
-    }
-    s_first = a;
-  }
+  const uint64_t first = tile_first[blockIdx.x];
   __syncthreads();
   const uint32_t lp = sP.lp;
-  // load the blocks overlapping [lo, hi)
-  const uint64_t bi = s_first + threadIdx.x;
+  // load the blocks overlapping [lo, hi); block-id -> per-axis block indices
+  // by multiply-shift division (field 0 fastest)
+  const uint64_t bi = first + threadIdx.x;
   bool have = bi < M && bstart[bi] < hi;
   if (have) {
     sb_start[threadIdx.x] = bstart[bi];
-    const unsigned long long id = bid[bi];
+    unsigned long long r = bid[bi];
 #pragma unroll
     for (int f = 0; f < D; ++f) {
       const FieldPlan &F = sP.f[f];
-      unsigned long long bf = (id / F.stride) % F.bn;
+      unsigned long long qd = F.bshift == 255u ? r : (__umul64hi(r, F.bmagic) >> F.bshift);
+      unsigned long long bf = r - qd * F.bn;
       sb_f[threadIdx.x][f] = (uint32_t)(bf << lp);
+      r = qd;
     }
   }
   const int nblk = __syncthreads_count(have);
@@ -483,27 +720,28 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_s(
 template <int D>
 static void expand_t(const Plan *plan, const unsigned long long *bid, const unsigned long long *bstart,
                      uint64_t M, const uint32_t *s_rel, uint64_t nb, uint64_t n,
-                     uint32_t log2_chunk, float *out, int32_t *qout, int *err, cudaStream_t s) {
+                     uint32_t log2_chunk, const uint32_t *tile_first, float *out, int32_t *qout,
+                     int *err, cudaStream_t s) {
   const uint64_t chunks = (nb + kExpThreads - 1) / kExpThreads;
   if (chunks == 0) return;
   note_launch();
   k_expand_s<D><<<(unsigned)chunks, kExpThreads, 0, s>>>(plan, bid, bstart, M, s_rel, nb, n,
-                                                        log2_chunk, out, qout, err);
+                                                        log2_chunk, tile_first, out, qout, err);
 }
 
 void launch_expand_s(uint32_t d, const Plan *plan, const unsigned long long *bid,
                      const unsigned long long *bstart, uint64_t M, const uint32_t *s_rel,
-                     uint64_t nb, uint64_t n, uint32_t log2_chunk, float *out, int32_t *qout,
-                     int *err, cudaStream_t s) {
+                     uint64_t nb, uint64_t n, uint32_t log2_chunk, const uint32_t *tile_first,
+                     float *out, int32_t *qout, int *err, cudaStream_t s) {
   switch (d) {
-    case 1: expand_t<1>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
-    case 2: expand_t<2>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
-    case 3: expand_t<3>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
-    case 4: expand_t<4>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
-    case 5: expand_t<5>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
-    case 6: expand_t<6>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
-    case 7: expand_t<7>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
-    default: expand_t<8>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 1: expand_t<1>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
+    case 2: expand_t<2>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
+    case 3: expand_t<3>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
+    case 4: expand_t<4>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
+    case 5: expand_t<5>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
+    case 6: expand_t<6>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
+    case 7: expand_t<7>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
+    default: expand_t<8>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
   }
 }
 

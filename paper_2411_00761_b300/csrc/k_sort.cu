@@ -12,9 +12,10 @@
 
 namespace lcp {
 
-constexpr int kLocalThreads = 1024;
+constexpr int kLocalThreads = 512;
 constexpr int kLocalWarps = kLocalThreads / 32;
-constexpr int kCap = 6144;  // keys sorted in shared memory
+constexpr int kCap = 4096;  // keys of a unit sorted in shared memory
+constexpr int kSubBits = 10; // level-2 split of oversized buckets
 
 // ---------------------------------------------------------------------------
 // block-wide exclusive scan of u64 values held one per thread
@@ -154,7 +155,8 @@ void launch_scatter(const unsigned long long *keys, uint64_t n, const Plan *plan
 // stable CTA radix sort (8-bit digits).  Warp w owns the contiguous element
 // range [w*S, (w+1)*S); within a warp elements are ranked in order with
 // __match_any_sync, so each pass is stable.  Arrays may live in shared or
-// global memory (generic pointers).
+// global memory (generic pointers).  Counters are warp-major (w * 256 + digit)
+// so the lanes of a warp touch different banks.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -171,31 +173,35 @@ __device__ void radix_pass(const unsigned long long *kin, const uint32_t *iin,
   const int S = (cnt + kLocalWarps - 1) / kLocalWarps;
   const int wlo = min(cnt, w * S), whi = min(cnt, wlo + S);
   const uint32_t lt = lanemask_lt();
+  uint32_t *wc = s_cnt + w * 256;
   for (int base = wlo; base < whi; base += 32) {
     int j = base + lane;
     bool valid = j < whi;
     uint32_t dg = 256u + lane;
     if (valid) dg = by_idx ? ((iin[j] >> shift) & 255u) : (uint32_t)((kin[j] >> shift) & 255ull);
     uint32_t peers = __match_any_sync(0xffffffffu, dg);
-    if (valid && lane == __ffs(peers) - 1) s_cnt[dg * kLocalWarps + w] += __popc(peers);
+    if (valid && lane == __ffs(peers) - 1) wc[dg] += __popc(peers);
     __syncwarp();
   }
   __syncthreads();
-  // exclusive scan over (digit, warp) in digit-major order
+  // exclusive scan over (digit, warp) in digit-major order: logical index
+  // i = digit * warps + warp lives at warp * 256 + digit
   {
     constexpr int per = 256 * kLocalWarps / kLocalThreads;
     uint32_t v[per];
     unsigned long long sum = 0;
 #pragma unroll
     for (int k = 0; k < per; ++k) {
-      v[k] = s_cnt[threadIdx.x * per + k];
+      const int i = threadIdx.x * per + k;
+      v[k] = s_cnt[(i % kLocalWarps) * 256 + i / kLocalWarps];
       sum += v[k];
     }
     unsigned long long tot;
     unsigned long long run = block_exscan<kLocalThreads>(sum, s_warp, tot);
 #pragma unroll
     for (int k = 0; k < per; ++k) {
-      s_cnt[threadIdx.x * per + k] = (uint32_t)run;
+      const int i = threadIdx.x * per + k;
+      s_cnt[(i % kLocalWarps) * 256 + i / kLocalWarps] = (uint32_t)run;
       run += v[k];
     }
   }
@@ -212,13 +218,13 @@ __device__ void radix_pass(const unsigned long long *kin, const uint32_t *iin,
       dg = by_idx ? ((iv >> shift) & 255u) : (uint32_t)((kv >> shift) & 255ull);
     }
     uint32_t peers = __match_any_sync(0xffffffffu, dg);
-    uint32_t basepos = valid ? s_cnt[dg * kLocalWarps + w] : 0u;
+    uint32_t basepos = valid ? wc[dg] : 0u;
     __syncwarp();
     if (valid) {
       uint32_t pos = basepos + __popc(peers & lt);
       kout[pos] = kv;
       if (iout) iout[pos] = iv;
-      if (lane == __ffs(peers) - 1) s_cnt[dg * kLocalWarps + w] = basepos + __popc(peers);
+      if (lane == __ffs(peers) - 1) wc[dg] = basepos + __popc(peers);
     }
     __syncwarp();
   }
@@ -257,18 +263,301 @@ __device__ int cta_sort(unsigned long long *k, uint32_t *i, unsigned long long *
 }
 
 // ---------------------------------------------------------------------------
-// per-bucket sort + segmentation (persistent over buckets)
+// level-2 partition of buckets larger than the shared-memory sort: each such
+// bucket is split by the next kSubBits key bits (still block-id bits, so no
+// block crosses a sub-bucket), one CTA per bucket.  Sort units: the ordered
+// list of key ranges that k_local sorts -- consecutive small level-1 buckets
+// merged greedily up to kCap keys, split buckets as greedy merges of their
+// consecutive sub-buckets, and the outlier bucket.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kLocalThreads, 1) k_local(LocalArgs a) {
+__global__ void __launch_bounds__(1024) k_seg_plan(const Plan *__restrict__ plan, uint32_t nb1,
+                                                   const unsigned long long *__restrict__ bstart,
+                                                   uint32_t *__restrict__ big_list,
+                                                   int *__restrict__ big_of,
+                                                   uint32_t *__restrict__ nbig) {
+  __shared__ unsigned long long s_warp[32];
+  const Plan &P = *plan;
+  const uint32_t nb = nb1 - 1;
+  const int sub = min(kSubBits, (int)P.part_shift - (int)P.rel_bits);
+  const uint32_t per = (nb1 + 1023) / 1024;
+  const uint32_t lo = threadIdx.x * per, hi = min(nb1, lo + per);
+  unsigned long long c = 0;
+  for (uint32_t b = lo; b < hi; ++b) {
+    const bool big = sub > 0 && b < nb && (bstart[b + 1] - bstart[b]) > (unsigned long long)kCap;
+    c += big;
+  }
+  unsigned long long tot;
+  unsigned long long run = block_exscan<1024>(c, s_warp, tot);
+  for (uint32_t b = lo; b < hi; ++b) {
+    const bool big = sub > 0 && b < nb && (bstart[b + 1] - bstart[b]) > (unsigned long long)kCap;
+    big_of[b] = big ? (int)run : -1;
+    if (big) big_list[run++] = b;
+  }
+  if (threadIdx.x == 0) *nbig = (uint32_t)tot;
+}
+
+// greedy merge of consecutive sub-bucket counts into units of <= kCap keys;
+// emit(offset, count) per unit.  Returns the number of units.
+template <typename F>
+__device__ uint32_t greedy_units(const uint32_t *cnt, uint32_t nsub, F emit) {
+  uint32_t units = 0, uoff = 0, ucnt = 0, off = 0;
+  for (uint32_t d = 0; d < nsub; ++d) {
+    const uint32_t c = cnt[d];
+    if (c) {
+      if (ucnt && ucnt + c > (uint32_t)kCap) {
+        emit(uoff, ucnt);
+        ++units;
+        ucnt = 0;
+      }
+      if (!ucnt) uoff = off;
+      ucnt += c;
+    }
+    off += c;
+  }
+  if (ucnt) {
+    emit(uoff, ucnt);
+    ++units;
+  }
+  return units;
+}
+
+__global__ void __launch_bounds__(1024) k_split_big(const Plan *__restrict__ plan,
+                                                    const unsigned long long *__restrict__ bstart,
+                                                    const uint32_t *__restrict__ big_list,
+                                                    const uint32_t *__restrict__ nbig,
+                                                    const unsigned long long *__restrict__ keys,
+                                                    const uint32_t *__restrict__ idx,
+                                                    unsigned long long *__restrict__ keys_out,
+                                                    uint32_t *__restrict__ idx_out,
+                                                    uint32_t *__restrict__ sub_cnt,
+                                                    uint32_t *__restrict__ big_units) {
+  __shared__ uint32_t h[1 << kSubBits];
+  __shared__ uint32_t hc[1 << kSubBits];
+  __shared__ unsigned long long s_warp[32];
+  const Plan &P = *plan;
+  const int sub = min(kSubBits, (int)P.part_shift - (int)P.rel_bits);
+  const int shift2 = (int)P.part_shift - sub;
+  const uint32_t mask = (1u << sub) - 1u;
+  const uint32_t nsub = 1u << sub;
+  constexpr int per = (1 << kSubBits) / 1024;
+  for (uint32_t j = blockIdx.x; j < *nbig; j += gridDim.x) {
+    const uint32_t b = big_list[j];
+    const uint64_t lo = bstart[b];
+    const uint64_t cnt = bstart[b + 1] - lo;
+    for (uint32_t d = threadIdx.x; d < (1u << kSubBits); d += blockDim.x) h[d] = 0u;
+    __syncthreads();
+    for (uint64_t t = threadIdx.x; t < cnt; t += blockDim.x)
+      atomicAdd(&h[(uint32_t)(keys[lo + t] >> shift2) & mask], 1u);
+    __syncthreads();
+    uint32_t v[per];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+      const uint32_t d = threadIdx.x * per + k;
+      v[k] = d < nsub ? h[d] : 0u;
+      sum += v[k];
+      if (d < nsub) {
+        sub_cnt[(uint64_t)j * (1u << kSubBits) + d] = v[k];
+        hc[d] = v[k];
+      }
+    }
+    unsigned long long tot;
+    unsigned long long run = block_exscan<1024>(sum, s_warp, tot);
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+      const uint32_t d = threadIdx.x * per + k;
+      if (d < nsub) h[d] = (uint32_t)run;
+      run += v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) big_units[j] = greedy_units(hc, nsub, [](uint32_t, uint32_t) {});
+    for (uint64_t t = threadIdx.x; t < cnt; t += blockDim.x) {
+      const unsigned long long k = keys[lo + t];
+      const uint32_t pos = atomicAdd(&h[(uint32_t)(k >> shift2) & mask], 1u);
+      keys_out[lo + pos] = k;
+      if (idx_out) idx_out[lo + pos] = idx[lo + t];
+    }
+    __syncthreads();
+  }
+}
+
+// Unit list (one CTA).  Thread t owns buckets [t*per, (t+1)*per); within that
+// range consecutive small buckets merge greedily up to kCap keys (a single
+// bucket above kCap that cannot be split forms its own unit); a split bucket
+// contributes its sub-bucket units, written by k_units_big at big_base[j];
+// the outlier bucket is a unit of its own.
+__global__ void __launch_bounds__(1024) k_units_small(uint32_t nb1,
+                                                      const unsigned long long *__restrict__ bstart,
+                                                      const int *__restrict__ big_of,
+                                                      const uint32_t *__restrict__ big_units,
+                                                      uint32_t *__restrict__ big_base,
+                                                      uint32_t *__restrict__ u_lo,
+                                                      uint32_t *__restrict__ u_cnt,
+                                                      uint32_t *__restrict__ u_meta,
+                                                      uint32_t *__restrict__ nunit) {
+  __shared__ unsigned long long s_warp[32];
+  const uint32_t nb = nb1 - 1;
+  const uint32_t per = (nb1 + 1023) / 1024;
+  const uint32_t lo = threadIdx.x * per, hi = min(nb1, lo + per);
+  unsigned long long count = 0;
+  uint64_t ucnt = 0;
+  for (uint32_t b = lo; b < hi; ++b) {
+    const uint64_t c = bstart[b + 1] - bstart[b];
+    const int j = big_of[b];
+    if (j >= 0 || b == nb) {
+      if (ucnt) {
+        ++count;
+        ucnt = 0;
+      }
+      if (j >= 0) count += big_units[j];
+      else if (c) ++count;
+      continue;
+    }
+    if (!c) continue;
+    if (ucnt && ucnt + c > (uint64_t)kCap) {
+      ++count;
+      ucnt = 0;
+    }
+    ucnt += c;
+  }
+  if (ucnt) ++count;
+  unsigned long long tot;
+  unsigned long long out = block_exscan<1024>(count, s_warp, tot);
+  if (threadIdx.x == 0) *nunit = (uint32_t)tot;
+  uint64_t ulo = 0;
+  ucnt = 0;
+  for (uint32_t b = lo; b < hi; ++b) {
+    const uint64_t c = bstart[b + 1] - bstart[b];
+    const int j = big_of[b];
+    if (j >= 0 || b == nb) {
+      if (ucnt) {
+        u_lo[out] = (uint32_t)ulo;
+        u_cnt[out] = (uint32_t)ucnt;
+        u_meta[out] = 0u;
+        ++out;
+        ucnt = 0;
+      }
+      if (j >= 0) {
+        big_base[j] = (uint32_t)out;
+        out += big_units[j];
+      } else if (c) {
+        u_lo[out] = (uint32_t)bstart[b];
+        u_cnt[out] = (uint32_t)c;
+        u_meta[out] = 2u;  // the outlier bucket
+        ++out;
+      }
+      continue;
+    }
+    if (!c) continue;
+    if (ucnt && ucnt + c > (uint64_t)kCap) {
+      u_lo[out] = (uint32_t)ulo;
+      u_cnt[out] = (uint32_t)ucnt;
+      u_meta[out] = 0u;
+      ++out;
+      ucnt = 0;
+    }
+    if (!ucnt) ulo = bstart[b];
+    ucnt += c;
+  }
+  if (ucnt) {
+    u_lo[out] = (uint32_t)ulo;
+    u_cnt[out] = (uint32_t)ucnt;
+    u_meta[out] = 0u;
+  }
+}
+
+// units of each split bucket (one CTA per bucket, thread 0 walks the
+// sub-bucket counts)
+__global__ void k_units_big(const unsigned long long *__restrict__ bstart,
+                            const uint32_t *__restrict__ big_list,
+                            const uint32_t *__restrict__ nbig,
+                            const uint32_t *__restrict__ sub_cnt, int nsub_bits_cap,
+                            const Plan *__restrict__ plan, const uint32_t *__restrict__ big_base,
+                            uint32_t *__restrict__ u_lo, uint32_t *__restrict__ u_cnt,
+                            uint32_t *__restrict__ u_meta) {
+  (void)nsub_bits_cap;
+  const Plan &P = *plan;
+  const int sub = min(kSubBits, (int)P.part_shift - (int)P.rel_bits);
+  const uint32_t nsub = sub > 0 ? (1u << sub) : 1u;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < *nbig;
+       j += gridDim.x * blockDim.x) {
+    const uint64_t lo = bstart[big_list[j]];
+    uint32_t o = big_base[j];
+    greedy_units(sub_cnt + (uint64_t)j * (1u << kSubBits), nsub, [&](uint32_t off, uint32_t c) {
+      u_lo[o] = (uint32_t)(lo + off);
+      u_cnt[o] = c;
+      u_meta[o] = 1u;  // keys in the level-2 buffer
+      ++o;
+    });
+  }
+}
+
+void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *bstart,
+                     unsigned long long *keys, uint32_t *idx, unsigned long long *keys_alt,
+                     uint32_t *idx_alt, uint32_t *big_list, int *big_of, uint32_t *nbig,
+                     uint32_t *sub_cnt, uint32_t *big_units, uint32_t *big_base, uint32_t *u_lo,
+                     uint32_t *u_cnt, uint32_t *u_meta, uint32_t *nunit, uint64_t n, int sms,
+                     cudaStream_t s) {
+  (void)n;
+  note_launch();
+  k_seg_plan<<<1, 1024, 0, s>>>(plan, nb1, bstart, big_list, big_of, nbig);
+  note_launch();
+  k_split_big<<<sms, 1024, 0, s>>>(plan, bstart, big_list, nbig, keys, idx, keys_alt, idx_alt,
+                                   sub_cnt, big_units);
+  note_launch();
+  k_units_small<<<1, 1024, 0, s>>>(nb1, bstart, big_of, big_units, big_base, u_lo, u_cnt, u_meta,
+                                   nunit);
+  note_launch();
+  k_units_big<<<sms, 128, 0, s>>>(bstart, big_list, nbig, sub_cnt, 0, plan, big_base, u_lo, u_cnt,
+                                  u_meta);
+}
+
+// ---------------------------------------------------------------------------
+// in-place bitonic sort of n (a power of two) keys, optionally with payloads
+// compared as (key, payload), in shared memory
+// ---------------------------------------------------------------------------
+__device__ void bitonic_smem(unsigned long long *k, uint32_t *ix, int n) {
+  for (int size = 2; size <= n; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
+        const int a = 2 * stride * (t / stride) + (t % stride);
+        const int b = a + stride;
+        const bool up = (a & size) == 0;
+        const unsigned long long ka = k[a], kb = k[b];
+        bool gt;
+        if (ix) {
+          const uint32_t ia = ix[a], ib = ix[b];
+          gt = ka > kb || (ka == kb && ia > ib);
+          if (gt == up) {
+            k[a] = kb;
+            k[b] = ka;
+            ix[a] = ib;
+            ix[b] = ia;
+          }
+        } else {
+          gt = ka > kb;
+          if (gt == up) {
+            k[a] = kb;
+            k[b] = ka;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-unit sort + segmentation into blocks (persistent over units)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kLocalThreads) k_local(LocalArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long *sk = reinterpret_cast<unsigned long long *>(smem);
-  unsigned long long *sk2 = sk + kCap;
-  uint32_t *si = reinterpret_cast<uint32_t *>(sk2 + kCap);
-  uint32_t *si2 = si + kCap;
-  uint32_t *s_cnt = si2 + kCap;                  // 256 * warps
+  uint32_t *si = reinterpret_cast<uint32_t *>(sk + kCap);
+  uint32_t *s_cnt = si + kCap;                   // 256 * warps (global-memory path)
   uint32_t *s_hist = s_cnt + 256 * kLocalWarps;  // 4096
   __shared__ unsigned long long s_warp[32];
-  __shared__ unsigned long long s_max;
+  __shared__ unsigned long long s_max, s_kmin, s_kmax;
   __shared__ Plan sP;
   if (threadIdx.x == 0) {
     sP = *a.plan;
@@ -278,42 +567,58 @@ __global__ void __launch_bounds__(kLocalThreads, 1) k_local(LocalArgs a) {
   __syncthreads();
   if (sP.status != OK) return;
   const bool perm = a.perm != nullptr;
-  const uint32_t nb = a.nb1 - 1;
   const uint32_t rel_bits = sP.rel_bits;
   const unsigned long long rel_mask = rel_bits >= 64 ? ~0ull : ((1ull << rel_bits) - 1ull);
   const uint64_t chunk_mask = (1ull << a.log2_chunk) - 1ull;
   const int ibits = perm ? (int)bitlen64(a.n > 0 ? a.n - 1 : 0) : 0;
   const uint32_t d = sP.d;
+  const uint32_t nseg = *a.nseg;
   unsigned long long my_max = 0ull;
 
-  for (uint32_t b = blockIdx.x; b < a.nb1; b += gridDim.x) {
-    const uint64_t lo = a.bucket_start[b];
-    const int cnt = (int)(a.bucket_start[b + 1] - lo);
-    if (cnt == 0) {
-      if (threadIdx.x == 0) a.bucket_blocks[b] = 0u;
-      continue;
+  for (uint32_t sg = blockIdx.x; sg < nseg; sg += gridDim.x) {
+    const uint64_t lo = a.seg_lo[sg];
+    const int cnt = (int)a.seg_cnt[sg];
+    const uint32_t meta = a.seg_meta[sg];
+    const bool outl = (meta >> 1) & 1u;
+    const bool src_alt = meta & 1u;
+    unsigned long long *gk = (src_alt ? a.keys_alt : a.keys) + lo;
+    unsigned long long *gk2 = (src_alt ? a.keys : a.keys_alt) + lo;
+    uint32_t *gi = nullptr, *gi2 = nullptr;
+    if (perm && !outl) {
+      gi = (src_alt ? a.idx_alt : a.idx) + lo;
+      gi2 = (src_alt ? a.idx : a.idx_alt) + lo;
     }
-    const bool outl = (b == nb);
-    // local key bits: below the bucket digit (outliers: the index bits)
-    const int kbits = outl ? (int)bitlen64(a.n > 0 ? a.n - 1 : 0) : (int)sP.part_shift;
-    const int ib = outl ? 0 : ibits;
     const unsigned long long *K;
     const uint32_t *I = nullptr;
     if (cnt <= kCap) {
-      for (int j = threadIdx.x; j < cnt; j += kLocalThreads) {
-        sk[j] = a.keys[lo + j];
-        if (perm && !outl) si[j] = a.idx[lo + j];
+      int n2 = 2;
+      while (n2 < cnt) n2 <<= 1;
+      for (int j = threadIdx.x; j < n2; j += kLocalThreads) {
+        sk[j] = j < cnt ? gk[j] : ~0ull;
+        if (gi) si[j] = j < cnt ? gi[j] : ~0u;
       }
       __syncthreads();
-      int fl = cta_sort(sk, (perm && !outl) ? si : nullptr, sk2, (perm && !outl) ? si2 : nullptr,
-                        cnt, kbits, ib, s_cnt, s_warp);
-      K = fl ? sk2 : sk;
-      I = (perm && !outl) ? (fl ? si2 : si) : nullptr;
+      bitonic_smem(sk, gi ? si : nullptr, n2);
+      K = sk;
+      I = gi ? si : nullptr;
     } else {
-      unsigned long long *gk = a.keys + lo, *gk2 = a.keys_alt + lo;
-      uint32_t *gi = (perm && !outl) ? a.idx + lo : nullptr;
-      uint32_t *gi2 = (perm && !outl) ? a.idx_alt + lo : nullptr;
-      int fl = cta_sort(gk, gi, gk2, gi2, cnt, kbits, ib, s_cnt, s_warp);
+      // global-memory LSD radix sort over the bits where the unit's keys differ
+      if (threadIdx.x == 0) {
+        s_kmin = ~0ull;
+        s_kmax = 0ull;
+      }
+      __syncthreads();
+      unsigned long long mn = ~0ull, mx = 0ull;
+      for (int j = threadIdx.x; j < cnt; j += kLocalThreads) {
+        const unsigned long long v = gk[j];
+        mn = v < mn ? v : mn;
+        mx = v > mx ? v : mx;
+      }
+      atomicMin(&s_kmin, mn);
+      atomicMax(&s_kmax, mx);
+      __syncthreads();
+      const int kbits = (int)bitlen64(s_kmin ^ s_kmax);
+      int fl = cta_sort(gk, gi, gk2, gi2, cnt, kbits, outl ? 0 : ibits, s_cnt, s_warp);
       K = fl ? gk2 : gk;
       I = gi ? (fl ? gi2 : gi) : nullptr;
       __threadfence_block();
@@ -328,7 +633,7 @@ __global__ void __launch_bounds__(kLocalThreads, 1) k_local(LocalArgs a) {
           for (uint32_t f = 0; f < d; ++f)
             a.q_slot[(uint64_t)f * a.n + lo + j] = a.q_in[(uint64_t)f * a.n + idx];
       }
-      if (threadIdx.x == 0) a.bucket_blocks[b] = 0u;
+      if (threadIdx.x == 0) a.seg_blocks[sg] = 0u;
       __syncthreads();
       continue;
     }
@@ -368,7 +673,7 @@ __global__ void __launch_bounds__(kLocalThreads, 1) k_local(LocalArgs a) {
       }
       carry += tot;
     }
-    if (threadIdx.x == 0) a.bucket_blocks[b] = (uint32_t)carry;
+    if (threadIdx.x == 0) a.seg_blocks[sg] = (uint32_t)carry;
     __syncthreads();
   }
   // stream-2 histogram and max
@@ -380,7 +685,7 @@ __global__ void __launch_bounds__(kLocalThreads, 1) k_local(LocalArgs a) {
 }
 
 void launch_local(const LocalArgs &a, int ctas, cudaStream_t s) {
-  size_t smem = (size_t)kCap * (8 + 8 + 4 + 4) + 4ull * 256 * kLocalWarps + 4ull * kAlpha;
+  size_t smem = (size_t)kCap * (8 + 4) + 4ull * 256 * kLocalWarps + 4ull * kAlpha;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -391,28 +696,28 @@ void launch_local(const LocalArgs &a, int ctas, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// blocks: compact the per-bucket block lists, delta code ids and counts
+// blocks: compact the per-segment block lists, delta code ids and counts
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_blocks_scan(const uint32_t *__restrict__ bucket_blocks,
-                                                      uint32_t nb,
+__global__ void __launch_bounds__(1024) k_blocks_scan(const uint32_t *__restrict__ seg_blocks,
+                                                      const uint32_t *__restrict__ nsegp,
                                                       unsigned long long *__restrict__ block_off,
                                                       int *__restrict__ prev_nonempty,
                                                       unsigned long long *__restrict__ mcount) {
   __shared__ unsigned long long s_warp[32];
   __shared__ int s_last[1024];
-  const uint32_t per = (nb + 1023) / 1024;
-  const uint32_t lo = threadIdx.x * per, hi = min(nb, lo + per);
+  const uint32_t nseg = *nsegp;
+  const uint32_t per = (nseg + 1023) / 1024;
+  const uint32_t lo = threadIdx.x * per, hi = min(nseg, lo + per);
   unsigned long long sum = 0;
   int last = -1;
   for (uint32_t i = lo; i < hi; ++i) {
-    sum += bucket_blocks[i];
-    if (bucket_blocks[i]) last = (int)i;
+    sum += seg_blocks[i];
+    if (seg_blocks[i]) last = (int)i;
   }
   s_last[threadIdx.x] = last;
   unsigned long long total;
   unsigned long long run = block_exscan<1024>(sum, s_warp, total);
   __syncthreads();
-  // exclusive max-scan of "last non-empty bucket" (sequential over 1024 is fine)
   if (threadIdx.x == 0) {
     int m = -1;
     for (int t = 0; t < 1024; ++t) {
@@ -426,15 +731,17 @@ __global__ void __launch_bounds__(1024) k_blocks_scan(const uint32_t *__restrict
   int pl = s_last[threadIdx.x];
   for (uint32_t i = lo; i < hi; ++i) {
     block_off[i] = run;
-    run += bucket_blocks[i];
+    run += seg_blocks[i];
     prev_nonempty[i] = pl;
-    if (bucket_blocks[i]) pl = (int)i;
+    if (seg_blocks[i]) pl = (int)i;
   }
 }
 
-__global__ void __launch_bounds__(512) k_blocks(const Plan *__restrict__ plan, uint32_t nb,
-                                                const unsigned long long *__restrict__ bstart,
-                                                const uint32_t *__restrict__ bblocks,
+__global__ void __launch_bounds__(512) k_blocks(const Plan *__restrict__ plan,
+                                                const uint32_t *__restrict__ nsegp,
+                                                const uint32_t *__restrict__ seg_lo,
+                                                const uint32_t *__restrict__ seg_cnt,
+                                                const uint32_t *__restrict__ sblocks,
                                                 const unsigned long long *__restrict__ tmp_bid,
                                                 const uint32_t *__restrict__ tmp_pos,
                                                 const unsigned long long *__restrict__ block_off,
@@ -455,12 +762,13 @@ __global__ void __launch_bounds__(512) k_blocks(const Plan *__restrict__ plan, u
   }
   __syncthreads();
   if (plan->status != OK) return;
+  const uint32_t nseg = *nsegp;
   unsigned long long x0 = 0ull, x1 = 0ull;
-  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
-    const uint32_t mb = bblocks[b];
+  for (uint32_t b = blockIdx.x; b < nseg; b += gridDim.x) {
+    const uint32_t mb = sblocks[b];
     if (mb == 0) continue;
-    const uint64_t lo = bstart[b];
-    const uint32_t cntb = (uint32_t)(bstart[b + 1] - lo);
+    const uint64_t lo = seg_lo[b];
+    const uint32_t cntb = seg_cnt[b];
     for (uint32_t t = threadIdx.x; t < mb; t += blockDim.x) {
       const unsigned long long bid = tmp_bid[lo + t];
       const uint32_t pos = tmp_pos[lo + t];
@@ -474,9 +782,9 @@ __global__ void __launch_bounds__(512) k_blocks(const Plan *__restrict__ plan, u
       } else {
         const int pb = prev_nonempty[b];
         if (pb >= 0) {
-          const uint32_t pm = bblocks[pb];
-          const uint64_t plo = bstart[pb];
-          const uint32_t pcnt = (uint32_t)(bstart[pb + 1] - plo);
+          const uint32_t pm = sblocks[pb];
+          const uint64_t plo = seg_lo[pb];
+          const uint32_t pcnt = seg_cnt[pb];
           pbid = tmp_bid[plo + pm - 1];
           pc = (long long)(pcnt - tmp_pos[plo + pm - 1]);
         }
@@ -505,17 +813,16 @@ __global__ void __launch_bounds__(512) k_blocks(const Plan *__restrict__ plan, u
   }
 }
 
-void launch_blocks(const Plan *plan, uint32_t nb1, const unsigned long long *bucket_start,
-                   const uint32_t *bucket_blocks, const unsigned long long *tmp_bid,
-                   const uint32_t *tmp_pos, unsigned long long *block_off, int *prev_nonempty,
-                   unsigned long long *s_id, unsigned long long *s_cnt, uint32_t *hist,
-                   unsigned long long *maxv, unsigned long long *mcount, int ctas,
-                   cudaStream_t s) {
-  const uint32_t nb = nb1 - 1;
+void launch_blocks(const Plan *plan, const uint32_t *nseg, const uint32_t *seg_lo,
+                   const uint32_t *seg_cnt, const uint32_t *seg_blocks,
+                   const unsigned long long *tmp_bid, const uint32_t *tmp_pos,
+                   unsigned long long *block_off, int *prev_nonempty, unsigned long long *s_id,
+                   unsigned long long *s_cnt, uint32_t *hist, unsigned long long *maxv,
+                   unsigned long long *mcount, int ctas, cudaStream_t s) {
   note_launch();
-  k_blocks_scan<<<1, 1024, 0, s>>>(bucket_blocks, nb, block_off, prev_nonempty, mcount);
+  k_blocks_scan<<<1, 1024, 0, s>>>(seg_blocks, nseg, block_off, prev_nonempty, mcount);
   note_launch();
-  k_blocks<<<ctas, 512, 0, s>>>(plan, nb, bucket_start, bucket_blocks, tmp_bid, tmp_pos,
+  k_blocks<<<ctas, 512, 0, s>>>(plan, nseg, seg_lo, seg_cnt, seg_blocks, tmp_bid, tmp_pos,
                                 block_off, prev_nonempty, s_id, s_cnt, hist, maxv);
 }
 
@@ -547,23 +854,20 @@ __global__ void __launch_bounds__(kLocalThreads, 1) k_sort_pairs(
   __shared__ unsigned long long s_warp[32];
   const int cnt = (int)*cntp;
   if (cnt == 0) return;
-  // keys and payloads move together
-  {
-    unsigned long long *ka = keys, *kb = keys_alt;
-    uint32_t *ia = vals, *ib = vals_alt;
-    for (int sh = 0; sh < kbits; sh += 8) {
-      radix_pass(ka, ia, kb, ib, cnt, sh, false, s_cnt, s_warp);
-      unsigned long long *t = ka;
-      ka = kb;
-      kb = t;
-      uint32_t *u = ia;
-      ia = ib;
-      ib = u;
-    }
-    for (int j = threadIdx.x; j < cnt; j += kLocalThreads) {
-      keys_out[j] = ka[j];
-      vals_out[j] = ia[j];
-    }
+  unsigned long long *ka = keys, *kb = keys_alt;
+  uint32_t *ia = vals, *ib = vals_alt;
+  for (int sh = 0; sh < kbits; sh += 8) {
+    radix_pass(ka, ia, kb, ib, cnt, sh, false, s_cnt, s_warp);
+    unsigned long long *t = ka;
+    ka = kb;
+    kb = t;
+    uint32_t *u = ia;
+    ia = ib;
+    ib = u;
+  }
+  for (int j = threadIdx.x; j < cnt; j += kLocalThreads) {
+    keys_out[j] = ka[j];
+    vals_out[j] = ia[j];
   }
 }
 

@@ -1,6 +1,7 @@
 // lcp_api.cu -- C ABI of the B300 LCP library: contexts, workspace,
 // LCP-S / LCP-T compression and decompression, trajectories (Algorithm 1)
 // with the LCP-FSM selection.
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -43,6 +44,7 @@ T *P(DevBuf &b) {
 }
 
 struct Workspace {
+  DevBuf big_list, big_of, nbig, sub_cnt, sub_nz, seg_base, seg_lo, seg_cnt, seg_meta, nseg;
   DevBuf mm, plan, keys, keys2, idx2, idx_alt, tile_hist, btot, bstart, s_rel, tmp_bid, tmp_pos,
       bblocks, boff, prevne, s_id, s_cnt, hist, maxv, nvals, mcount, kcount, desc, codes, lens,
       tables, chunk_bits, chunk_off, outl_idx, summary, q_in, q_slot, perm, sym, patch_s,
@@ -70,12 +72,21 @@ struct DeviceGuard {
   }
 };
 
-#define CK(expr)                        \
-  do {                                  \
-    if ((expr) != cudaSuccess) {        \
-      cudaGetLastError();               \
-      return ERR_CUDA;                  \
-    }                                   \
+thread_local char g_last_error[256] = "";
+
+void note_cuda_error(cudaError_t e, const char *what, int line) {
+  snprintf(g_last_error, sizeof g_last_error, "%s at lcp_api.cu:%d: %s", what, line,
+           cudaGetErrorString(e));
+}
+
+#define CK(expr)                                  \
+  do {                                            \
+    cudaError_t _ce = (expr);                     \
+    if (_ce != cudaSuccess) {                     \
+      note_cuda_error(_ce, #expr, __LINE__);      \
+      cudaGetLastError();                         \
+      return ERR_CUDA;                            \
+    }                                             \
   } while (0)
 #define TRY(expr)            \
   do {                       \
@@ -223,9 +234,22 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   TRY(grow(w.s_rel, nn * 4));
   TRY(grow(w.tmp_bid, nn * 8));
   TRY(grow(w.tmp_pos, nn * 4));
-  TRY(grow(w.bblocks, (size_t)nb1 * 4));
-  TRY(grow(w.boff, (size_t)nb1 * 8));
-  TRY(grow(w.prevne, (size_t)nb1 * 4));
+  // segments: level-1 buckets, split ones replaced by their sub-buckets
+  const uint64_t nbig_max = n / 4096 + 1;
+  const uint64_t segcap = nb1 + nbig_max * 1024;
+  TRY(grow(w.big_list, (size_t)nb1 * 4));
+  TRY(grow(w.big_of, (size_t)nb1 * 4));
+  TRY(grow(w.nbig, 16));
+  TRY(grow(w.sub_cnt, (size_t)nbig_max * 1024 * 4));
+  TRY(grow(w.sub_nz, (size_t)nb1 * 4));    // units per split bucket
+  TRY(grow(w.seg_base, (size_t)nb1 * 4));  // first unit of each split bucket
+  TRY(grow(w.seg_lo, (size_t)segcap * 4));
+  TRY(grow(w.seg_cnt, (size_t)segcap * 4));
+  TRY(grow(w.seg_meta, (size_t)segcap * 4));
+  TRY(grow(w.nseg, 16));
+  TRY(grow(w.bblocks, (size_t)segcap * 4));
+  TRY(grow(w.boff, (size_t)segcap * 8));
+  TRY(grow(w.prevne, (size_t)segcap * 4));
   TRY(grow(w.s_id, nn * 8));
   TRY(grow(w.s_cnt, nn * 8));
   TRY(grow(w.outl_idx, nn * 4));
@@ -250,13 +274,25 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
                  want_perm ? P<uint32_t>(w.idx2) : nullptr, s);
   prof_end(c, s);
   CK(cudaGetLastError());
-  // 6. per-bucket sort + segmentation
+  // 6. level-2 split of oversized buckets, per-segment sort + segmentation
+  prof_begin(c, "s.split", s);
+  launch_segments(P<Plan>(w.plan), nb1, P<unsigned long long>(w.bstart),
+                  P<unsigned long long>(w.keys2), want_perm ? P<uint32_t>(w.idx2) : nullptr,
+                  P<unsigned long long>(w.keys), want_perm ? P<uint32_t>(w.idx_alt) : nullptr,
+                  P<uint32_t>(w.big_list), P<int>(w.big_of), P<uint32_t>(w.nbig),
+                  P<uint32_t>(w.sub_cnt), P<uint32_t>(w.sub_nz), P<uint32_t>(w.seg_base),
+                  P<uint32_t>(w.seg_lo), P<uint32_t>(w.seg_cnt), P<uint32_t>(w.seg_meta),
+                  P<uint32_t>(w.nseg), n, sms, s);
+  prof_end(c, s);
   CK(cudaMemsetAsync(w.hist.p, 0, 3ull * kAlpha * 4, s));
   CK(cudaMemsetAsync(w.maxv.p, 0, 4 * 8, s));
   LocalArgs la;
   la.plan = P<Plan>(w.plan);
-  la.nb1 = nb1;
-  la.bucket_start = P<unsigned long long>(w.bstart);
+  la.nseg = P<uint32_t>(w.nseg);
+  la.seg_lo = P<uint32_t>(w.seg_lo);
+  la.seg_cnt = P<uint32_t>(w.seg_cnt);
+  la.seg_meta = P<uint32_t>(w.seg_meta);
+  la.seg_blocks = P<uint32_t>(w.bblocks);
   la.keys = P<unsigned long long>(w.keys2);
   la.idx = want_perm ? P<uint32_t>(w.idx2) : nullptr;
   la.keys_alt = P<unsigned long long>(w.keys);  // free after the scatter
@@ -264,7 +300,6 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   la.s_rel = P<uint32_t>(w.s_rel);
   la.tmp_bid = P<unsigned long long>(w.tmp_bid);
   la.tmp_pos = P<uint32_t>(w.tmp_pos);
-  la.bucket_blocks = P<uint32_t>(w.bblocks);
   la.hist = P<uint32_t>(w.hist);
   la.maxv = P<unsigned long long>(w.maxv);
   la.perm = want_perm ? perm_out : nullptr;
@@ -274,16 +309,17 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   la.log2_chunk = kLog2Chunk;
   la.n = n;
   prof_begin(c, "s.local_sort", s);
-  launch_local(la, sms, s);
+  launch_local(la, 2 * sms, s);
   prof_end(c, s);
   CK(cudaGetLastError());
   // 7. blocks: ids and counts
   prof_begin(c, "s.blocks", s);
-  launch_blocks(P<Plan>(w.plan), nb1, P<unsigned long long>(w.bstart), P<uint32_t>(w.bblocks),
-                P<unsigned long long>(w.tmp_bid), P<uint32_t>(w.tmp_pos),
-                P<unsigned long long>(w.boff), P<int>(w.prevne), P<unsigned long long>(w.s_id),
-                P<unsigned long long>(w.s_cnt), P<uint32_t>(w.hist),
-                P<unsigned long long>(w.maxv), P<unsigned long long>(w.mcount), 2 * sms, s);
+  launch_blocks(P<Plan>(w.plan), P<uint32_t>(w.nseg), P<uint32_t>(w.seg_lo),
+                P<uint32_t>(w.seg_cnt), P<uint32_t>(w.bblocks), P<unsigned long long>(w.tmp_bid),
+                P<uint32_t>(w.tmp_pos), P<unsigned long long>(w.boff), P<int>(w.prevne),
+                P<unsigned long long>(w.s_id), P<unsigned long long>(w.s_cnt),
+                P<uint32_t>(w.hist), P<unsigned long long>(w.maxv),
+                P<unsigned long long>(w.mcount), 2 * sms, s);
   launch_counts_s(P<unsigned long long>(w.bstart), nb, n, P<unsigned long long>(w.mcount),
                   P<unsigned long long>(w.nvals), P<unsigned long long>(w.kcount), s);
   prof_end(c, s);
@@ -775,11 +811,6 @@ lcp_status lcp_select(lcp_ctx *c, lcp_traj *traj, const float *d_fields, uint64_
 // ---------------------------------------------------------------------------
 namespace {
 
-__global__ void k_counts_total(const unsigned long long *starts, const unsigned long long *counts,
-                               uint64_t M, unsigned long long *total) {
-  *total = M ? starts[M - 1] + counts[M - 1] : 0ull;
-}
-
 inline uint64_t rd64(const uint8_t *p) {
   uint64_t v;
   memcpy(&v, p, 8);
@@ -914,6 +945,7 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
   CK(cudaMemsetAsync(w.err.p, 0, 8, s));
   CK(cudaMemcpyAsync(w.dec_fields.p, hf, sizeof(DecodeFields), cudaMemcpyHostToDevice, s));
   launch_decode_plan(P<DecodeFields>(w.dec_fields), h.d, P<Plan>(w.plan), s);
+  CK(cudaGetLastError());
   int *err = P<int>(w.err);
   HuffTable *ht = P<HuffTable>(w.hufft);
   int32_t *qout = t ? P<int32_t>(t->new_q) : nullptr;
@@ -931,30 +963,25 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
     TRY(grow(w.scan_base, (tiles + 1) * 8));
     prof_begin(c, "d.streams", s);
     launch_decode_u64(in + h.off[0], h.si[0], ht + 0, P<unsigned long long>(w.s_id), err, sms, s);
+    CK(cudaGetLastError());
     launch_decode_u64(in + h.off[1], h.si[1], ht + 1, P<unsigned long long>(w.s_cnt), err, sms, s);
+    CK(cudaGetLastError());
     launch_decode_u32(in + h.off[2], h.si[2], ht + 2, P<uint32_t>(w.s_rel), err, sms, s);
+    CK(cudaGetLastError());
     prof_end(c, s);
     if (M > 0) {
-      unsigned long long *tt = P<unsigned long long>(w.scan_tmp);
-      unsigned long long *tb = P<unsigned long long>(w.scan_base);
+      TRY(grow(w.scan_tmp, (M / 4096 + 2) * 32));
+      TRY(grow(w.tmp_pos, (nb / 1024 + 2) * 4));
       prof_begin(c, "d.block_scans", s);
-      launch_scan_u64(P<unsigned long long>(w.s_id), M, 0, true, P<unsigned long long>(w.bid), tt,
-                      tb, s);
-      launch_scan_u64(P<unsigned long long>(w.s_cnt), M, 1, true,
-                      P<unsigned long long>(w.counts), tt, tb, s);
-      launch_scan_u64(P<unsigned long long>(w.counts), M, 0, false,
-                      P<unsigned long long>(w.starts), tt, tb, s);
-      note_launch();
-      k_counts_total<<<1, 1, 0, s>>>(P<unsigned long long>(w.starts),
-                                     P<unsigned long long>(w.counts), M,
-                                     P<unsigned long long>(w.btot));
-      launch_check_counts(P<unsigned long long>(w.counts), M, P<unsigned long long>(w.btot), nb,
-                          err, sms, s);
+      launch_block_scans(P<unsigned long long>(w.s_id), P<unsigned long long>(w.s_cnt), M,
+                         w.scan_tmp.p, P<unsigned long long>(w.bid),
+                         P<unsigned long long>(w.starts), P<uint32_t>(w.tmp_pos), nb, err, s);
+      CK(cudaGetLastError());
       prof_end(c, s);
       prof_begin(c, "d.expand", s);
       launch_expand_s(h.d, P<Plan>(w.plan), P<unsigned long long>(w.bid),
                       P<unsigned long long>(w.starts), M, P<uint32_t>(w.s_rel), nb, n,
-                      h.log2_chunk, out, qout, err, s);
+                      h.log2_chunk, P<uint32_t>(w.tmp_pos), out, qout, err, s);
       prof_end(c, s);
     }
     launch_outliers_decode(P<Plan>(w.plan), reinterpret_cast<const float *>(in + h.off[3]), h.K,
@@ -1063,6 +1090,8 @@ lcp_status lcp_quantize(const float *d_x, uint64_t n, float m, float e, float ma
   cudaStreamSynchronize(s);
   return r;
 }
+
+const char *lcp_last_error(void) { return g_last_error; }
 
 uint64_t lcp_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 

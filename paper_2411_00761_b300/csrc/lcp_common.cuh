@@ -51,6 +51,9 @@ struct FieldPlan {
   uint32_t pad0;
   unsigned long long bn;      // blocks along this axis
   unsigned long long stride;  // block-id stride of this axis
+  unsigned long long bmagic;  // r / bn = umulhi(r, bmagic) >> bshift (r < 2^63, bn >= 2)
+  uint32_t bshift;            // 255 when bn == 1
+  uint32_t pad1;
 };
 
 struct MinMax {

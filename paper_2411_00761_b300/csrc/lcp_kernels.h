@@ -55,18 +55,25 @@ void launch_bucket_offsets(uint32_t *tile_hist, int tiles, uint32_t nb1,
 void launch_scatter(const unsigned long long *keys, uint64_t n, const Plan *plan, uint32_t nb1,
                     int tiles, const uint32_t *tile_off, unsigned long long *keys_out,
                     uint32_t *idx_out, cudaStream_t s);
+// level-2 split of oversized buckets and the ordered segment list
+void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *bstart,
+                     unsigned long long *keys, uint32_t *idx, unsigned long long *keys_alt,
+                     uint32_t *idx_alt, uint32_t *big_list, int *big_of, uint32_t *nbig,
+                     uint32_t *sub_cnt, uint32_t *big_units, uint32_t *big_base, uint32_t *u_lo,
+                     uint32_t *u_cnt, uint32_t *u_meta, uint32_t *nunit, uint64_t n, int sms,
+                     cudaStream_t s);
 struct LocalArgs {
   const Plan *plan;
-  uint32_t nb1;                            // buckets + 1 (outliers last)
-  const unsigned long long *bucket_start;  // [nb1 + 1]
-  unsigned long long *keys;                // partitioned keys
+  const uint32_t *nseg;                    // segments (device count)
+  const uint32_t *seg_lo, *seg_cnt, *seg_meta;
+  uint32_t *seg_blocks;                    // [segments] blocks per segment
+  unsigned long long *keys;                // partitioned keys (level 1)
   uint32_t *idx;                           // partitioned input indices (perm mode)
-  unsigned long long *keys_alt;            // scratch for large buckets
+  unsigned long long *keys_alt;            // level-2 split keys / scratch
   uint32_t *idx_alt;
   uint32_t *s_rel;                         // [n]
   unsigned long long *tmp_bid;             // [n] block ids per bucket region
-  uint32_t *tmp_pos;                       // [n] block start (bucket-local)
-  uint32_t *bucket_blocks;                 // [nb1]
+  uint32_t *tmp_pos;                       // [n] block start (segment-local)
   uint32_t *hist;                          // [3][4096]
   unsigned long long *maxv;                // [3]
   uint32_t *perm;                          // [n] slot -> input index (perm mode) or null
@@ -77,12 +84,12 @@ struct LocalArgs {
   uint64_t n;
 };
 void launch_local(const LocalArgs &a, int ctas, cudaStream_t s);
-void launch_blocks(const Plan *plan, uint32_t nb1, const unsigned long long *bucket_start,
-                   const uint32_t *bucket_blocks, const unsigned long long *tmp_bid,
-                   const uint32_t *tmp_pos, unsigned long long *block_off, int *prev_nonempty,
-                   unsigned long long *s_id, unsigned long long *s_cnt, uint32_t *hist,
-                   unsigned long long *maxv, unsigned long long *mcount, int ctas,
-                   cudaStream_t s);
+void launch_blocks(const Plan *plan, const uint32_t *nseg, const uint32_t *seg_lo,
+                   const uint32_t *seg_cnt, const uint32_t *seg_blocks,
+                   const unsigned long long *tmp_bid, const uint32_t *tmp_pos,
+                   unsigned long long *block_off, int *prev_nonempty, unsigned long long *s_id,
+                   unsigned long long *s_cnt, uint32_t *hist, unsigned long long *maxv,
+                   unsigned long long *mcount, int ctas, cudaStream_t s);
 // value counts of the three LCP-S streams and K
 void launch_counts_s(const unsigned long long *bucket_start, uint32_t nb, uint64_t n,
                      const unsigned long long *mcount, unsigned long long *nvals,
@@ -151,10 +158,13 @@ void launch_scan_u64(const unsigned long long *in, uint64_t n, int mode, bool in
 void launch_check_counts(const unsigned long long *counts, uint64_t m,
                          const unsigned long long *starts_total, uint64_t nb, int *err, int sms,
                          cudaStream_t s);
+void launch_block_scans(const unsigned long long *sid, const unsigned long long *scnt, uint64_t M,
+                        void *agg, unsigned long long *bid, unsigned long long *bstart,
+                        uint32_t *tile_first, uint64_t nb, int *err, cudaStream_t s);
 void launch_expand_s(uint32_t d, const Plan *plan, const unsigned long long *bid,
                      const unsigned long long *bstart, uint64_t M, const uint32_t *s_rel,
-                     uint64_t nb, uint64_t n, uint32_t log2_chunk, float *out, int32_t *qout,
-                     int *err, cudaStream_t s);
+                     uint64_t nb, uint64_t n, uint32_t log2_chunk, const uint32_t *tile_first,
+                     float *out, int32_t *qout, int *err, cudaStream_t s);
 void launch_outliers_decode(const Plan *plan, const float *raw, uint64_t K, uint64_t n, uint32_t d,
                             float *out, int32_t *qout, int sms, cudaStream_t s);
 

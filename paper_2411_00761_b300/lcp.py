@@ -43,6 +43,7 @@ SIGNATURES = {
     "lcp_quantize": (C.c_int, [_vp, _u64, C.c_float, C.c_float, C.c_float, _vp, _vp, _vp, _vp]),
     "lcp_ctx_profile": (C.c_int, [_vp, C.c_int]),
     "lcp_kernel_launches": (_u64, []),
+    "lcp_last_error": (C.c_char_p, []),
     "lcp_quantize_noalloc": (C.c_int, [_vp, _u64, C.c_float, C.c_float, C.c_float, _vp, _vp, _vp,
                                        C.POINTER(_u64), _vp]),
     "lcp_ctx_profile_read": (C.c_int, [_vp, C.c_char_p, C.POINTER(C.c_float), C.c_int]),
@@ -52,6 +53,8 @@ SIGNATURES = {
 class LcpError(RuntimeError):
     def __init__(self, status: int, where: str):
         msg = _lib.lcp_status_str(status).decode() if _lib is not None else str(status)
+        if _lib is not None and status == ERR_CUDA:
+            msg += " [" + _lib.lcp_last_error().decode() + "]"
         super().__init__(f"{where}: {msg} ({status})")
         self.status = status
 
