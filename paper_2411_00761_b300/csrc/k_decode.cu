@@ -167,21 +167,100 @@ struct BitReader {
   }
 };
 
-// One warp decodes 32 consecutive chunks, lane l the chunk c0 + l, 32 symbols
-// per round into shared memory; the warp then writes each lane's 32 values
-// with coalesced stores.
+// Bit reader over a 16-byte aligned u32 payload that keeps one 16-byte load
+// in flight ahead of the window (loads past the end read zero).
+struct BitReader4 {
+  const uint4 *p4;
+  unsigned long long n4, next4;
+  uint4 b0, b1;
+  int bi;
+  unsigned long long win;
+  int nb;
+  __device__ __forceinline__ uint4 load(unsigned long long i) const {
+    return i < n4 ? __ldg(p4 + i) : make_uint4(0, 0, 0, 0);
+  }
+  __device__ __forceinline__ uint32_t take() {
+    if (bi == 4) {
+      b0 = b1;
+      b1 = load(next4++);
+      bi = 0;
+    }
+    const int i = bi++;
+    return i == 0 ? b0.x : i == 1 ? b0.y : i == 2 ? b0.z : b0.w;
+  }
+  __device__ __forceinline__ void init(const uint32_t *pl, unsigned long long nwords,
+                                       unsigned long long pos) {
+    p4 = reinterpret_cast<const uint4 *>(pl);
+    n4 = (nwords + 3) >> 2;
+    const unsigned long long w = pos >> 5;
+    b0 = load(w >> 2);
+    b1 = load((w >> 2) + 1);
+    next4 = (w >> 2) + 2;
+    bi = (int)(w & 3);
+    win = ((unsigned long long)take() << 32);
+    win |= take();
+    const int off = (int)(pos & 31);
+    win <<= off;
+    nb = 64 - off;
+    if (nb <= 32) {
+      win |= (unsigned long long)take() << (32 - nb);
+      nb += 32;
+    }
+  }
+  __device__ __forceinline__ uint32_t peek(int n) const { return (uint32_t)(win >> (64 - n)); }
+  __device__ __forceinline__ void skip(int n) {
+    win <<= n;
+    nb -= n;
+    if (nb <= 32) {
+      win |= (unsigned long long)take() << (32 - nb);
+      nb += 32;
+    }
+  }
+  __device__ __forceinline__ unsigned long long read(int n) {
+    unsigned long long v = 0;
+    if (n > 32) {
+      v = (unsigned long long)peek(n - 32) << 32;
+      skip(n - 32);
+      n = 32;
+    }
+    if (n > 0) {
+      v |= peek(n);
+      skip(n);
+    }
+    return v;
+  }
+};
+
+// All Huffman streams of a container in one launch.  CTA b serves stream s
+// with cta_base[s] <= b < cta_base[s+1]; inside it, a warp decodes 32
+// consecutive chunks, lane l the chunk c0 + l, 32 symbols per round into
+// shared memory, then writes each lane's 32 values with coalesced stores.
 constexpr int kDecWarps = 2;
 
-template <typename T>
-__global__ void __launch_bounds__(32 * kDecWarps) k_huff_decode(const uint8_t *__restrict__ sec,
-                                                                StreamInfo info,
-                                                                const HuffTable *__restrict__ HT,
-                                                                T *__restrict__ out,
+struct HuffJob {
+  const uint8_t *sec;
+  StreamInfo info;
+  const HuffTable *ht;
+  void *out;
+  int wide;  // 8-byte outputs
+  unsigned cta_base;
+};
+struct HuffJobs {
+  HuffJob j[3];
+  int n;
+};
+
+__global__ void __launch_bounds__(32 * kDecWarps) k_huff_decode(HuffJobs jobs,
                                                                 int *__restrict__ err) {
   __shared__ uint32_t fast[1 << kFastBits];
   __shared__ uint32_t first[kLmax + 1], index[kLmax + 1], count[kLmax + 1];
   __shared__ uint16_t syms[kAlpha];
-  __shared__ T stage[kDecWarps][32][33];
+  __shared__ unsigned long long stage[kDecWarps][32][33];
+  int js = 0;
+  while (js + 1 < jobs.n && blockIdx.x >= jobs.j[js + 1].cta_base) ++js;
+  const HuffJob &J = jobs.j[js];
+  const HuffTable *HT = J.ht;
+  const StreamInfo info = J.info;
   for (int i = threadIdx.x; i < (1 << kFastBits); i += blockDim.x) fast[i] = HT->fast[i];
   for (int i = threadIdx.x; i < (int)HT->used && i < kAlpha; i += blockDim.x) syms[i] = HT->syms[i];
   if (threadIdx.x <= kLmax) {
@@ -196,69 +275,70 @@ __global__ void __launch_bounds__(32 * kDecWarps) k_huff_decode(const uint8_t *_
   }
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const unsigned long long cs = 1ull << info.log2_chunk;
-  const uint8_t *ct = sec + pad16(80ull + 2ull * info.used);
+  const uint8_t *ct = J.sec + pad16(80ull + 2ull * info.used);
   const uint32_t *pl = reinterpret_cast<const uint32_t *>(ct + pad16(8ull * info.n_chunks));
   const unsigned long long nwords = words_of(info.payload_bits);
+  const unsigned long long g = (unsigned long long)(blockIdx.x - J.cta_base) * kDecWarps + wl;
   const unsigned long long groups = (info.n_chunks + 31) / 32;
-  for (unsigned long long g = (unsigned long long)blockIdx.x * kDecWarps + wl; g < groups;
-       g += (unsigned long long)gridDim.x * kDecWarps) {
-    const unsigned long long c = g * 32 + lane;
-    const bool act = c < info.n_chunks;
-    const unsigned long long lo = c * cs;
-    const unsigned long long hi = act ? min(info.n, lo + cs) : lo;
-    BitReader br;
-    bool ok = true;
-    if (act) {
-      const unsigned long long pos =
-          (unsigned long long)reinterpret_cast<const uint32_t *>(ct)[2 * c] |
-          ((unsigned long long)reinterpret_cast<const uint32_t *>(ct)[2 * c + 1] << 32);
-      if (pos > info.payload_bits) {
-        atomicExch(err, 1);
-        ok = false;
-      }
-      br.init(pl, nwords, ok ? pos : 0ull);
+  if (g >= groups) return;
+  const unsigned long long c = g * 32 + lane;
+  const bool act = c < info.n_chunks;
+  const unsigned long long lo = c * cs;
+  const unsigned long long hi = act ? min(info.n, lo + cs) : lo;
+  BitReader4 br;
+  bool ok = true;
+  if (act) {
+    const unsigned long long pos = (unsigned long long)reinterpret_cast<const uint32_t *>(ct)[2 * c] |
+                                   ((unsigned long long)reinterpret_cast<const uint32_t *>(ct)[2 * c + 1] << 32);
+    if (pos > info.payload_bits) {
+      atomicExch(err, 1);
+      ok = false;
     }
-    const unsigned long long mine = (act && ok) ? hi - lo : 0ull;
-    for (unsigned long long r0 = 0; r0 < cs; r0 += 32) {
-      // decode up to 32 symbols of this lane's chunk
-      for (int k = 0; k < 32; ++k) {
-        if (r0 + k >= mine) break;
-        uint32_t e = fast[br.peek(kFastBits)];
-        uint32_t sym;
-        if (e) {
-          sym = e >> 5;
-          br.skip((int)(e & 31u));
-        } else {
-          int L = kFastBits + 1;
-          uint32_t code = 0;
-          for (; L <= kLmax; ++L) {
-            code = br.peek(L);
-            if (code - first[L] < count[L]) break;
-          }
-          if (L > kLmax) {
-            atomicExch(err, 1);
-            sym = 0;
-            L = 1;
-          } else {
-            sym = syms[index[L] + (code - first[L])];
-          }
-          br.skip(L);
+    br.init(pl, nwords, ok ? pos : 0ull);
+  }
+  const unsigned long long mine = (act && ok) ? hi - lo : 0ull;
+  unsigned long long *o64 = reinterpret_cast<unsigned long long *>(J.out);
+  uint32_t *o32 = reinterpret_cast<uint32_t *>(J.out);
+  for (unsigned long long r0 = 0; r0 < cs; r0 += 32) {
+    for (int k = 0; k < 32; ++k) {
+      if (r0 + k >= mine) break;
+      uint32_t e = fast[br.peek(kFastBits)];
+      uint32_t sym;
+      if (e) {
+        sym = e >> 5;
+        br.skip((int)(e & 31u));
+      } else {
+        int L = kFastBits + 1;
+        uint32_t code = 0;
+        for (; L <= kLmax; ++L) {
+          code = br.peek(L);
+          if (code - first[L] < count[L]) break;
         }
-        unsigned long long v = sym;
-        if (sym == (uint32_t)kEsc) v = br.read((int)info.width);
-        stage[wl][lane][k] = (T)v;
+        if (L > kLmax) {
+          atomicExch(err, 1);
+          sym = 0;
+          L = 1;
+        } else {
+          sym = syms[index[L] + (code - first[L])];
+        }
+        br.skip(L);
       }
-      __syncwarp();
-      // coalesced write-out: row l holds chunk (g*32 + l) symbols r0..r0+31
-      for (int l = 0; l < 32; ++l) {
-        const unsigned long long cl = g * 32 + l;
-        if (cl >= info.n_chunks) break;
-        const unsigned long long base = cl * cs + r0;
-        const unsigned long long lim = min(info.n, cl * cs + cs);
-        if (base + lane < lim) out[base + lane] = stage[wl][l][lane];
-      }
-      __syncwarp();
+      unsigned long long v = sym;
+      if (sym == (uint32_t)kEsc) v = br.read((int)info.width);
+      stage[wl][lane][k] = v;
     }
+    __syncwarp();
+    for (int l = 0; l < 32; ++l) {
+      const unsigned long long cl = g * 32 + l;
+      if (cl >= info.n_chunks) break;
+      const unsigned long long base = cl * cs + r0;
+      const unsigned long long lim = min(info.n, cl * cs + cs);
+      if (base + lane < lim) {
+        if (J.wide) o64[base + lane] = stage[wl][l][lane];
+        else o32[base + lane] = (uint32_t)stage[wl][l][lane];
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -295,31 +375,41 @@ __global__ void k_fixed_decode(const uint8_t *__restrict__ sec, StreamInfo info,
   }
 }
 
-template <typename T>
-static void decode_stream_t(const uint8_t *sec, const StreamInfo &info, HuffTable *ht, T *out,
-                            int *err, int sms, cudaStream_t s) {
-  if (info.n == 0) return;
-  if (info.coder == 0) {
-    unsigned g = (unsigned)std::min<unsigned long long>((info.n + 255) / 256, 8ull * sms);
-    note_launch();
-    k_fixed_decode<T><<<g, 256, 0, s>>>(sec, info, out);
-  } else {
-    launch_huff_table(sec, ht, s);
-    const unsigned long long groups = (info.n_chunks + 31) / 32;
-    unsigned g = (unsigned)std::min<unsigned long long>((groups + kDecWarps - 1) / kDecWarps,
-                                                        64ull * sms);
-    note_launch();
-    k_huff_decode<T><<<g, 32 * kDecWarps, 0, s>>>(sec, info, ht, out, err);
+void launch_decode_streams(int ns, const uint8_t *const *secs, const StreamInfo *infos,
+                           HuffTable *ht, void *const *outs, const int *wide, int *err, int sms,
+                           cudaStream_t s) {
+  HuffJobs jobs;
+  jobs.n = 0;
+  unsigned ctas = 0;
+  for (int k = 0; k < ns; ++k) {
+    const StreamInfo &I = infos[k];
+    if (I.n == 0) continue;
+    if (I.coder == 0) {
+      unsigned g = (unsigned)std::min<unsigned long long>((I.n + 255) / 256, 8ull * sms);
+      note_launch();
+      if (wide[k])
+        k_fixed_decode<unsigned long long><<<g, 256, 0, s>>>(secs[k], I,
+                                                            (unsigned long long *)outs[k]);
+      else
+        k_fixed_decode<uint32_t><<<g, 256, 0, s>>>(secs[k], I, (uint32_t *)outs[k]);
+      continue;
+    }
+    launch_huff_table(secs[k], ht + k, s);
+    HuffJob &J = jobs.j[jobs.n++];
+    J.sec = secs[k];
+    J.info = I;
+    J.ht = ht + k;
+    J.out = outs[k];
+    J.wide = wide[k];
+    J.cta_base = ctas;
+    const unsigned long long groups = (I.n_chunks + 31) / 32;
+    ctas += (unsigned)((groups + kDecWarps - 1) / kDecWarps);
   }
-}
-
-void launch_decode_u64(const uint8_t *sec, const StreamInfo &info, HuffTable *ht,
-                       unsigned long long *out, int *err, int sms, cudaStream_t s) {
-  decode_stream_t<unsigned long long>(sec, info, ht, out, err, sms, s);
-}
-void launch_decode_u32(const uint8_t *sec, const StreamInfo &info, HuffTable *ht, uint32_t *out,
-                       int *err, int sms, cudaStream_t s) {
-  decode_stream_t<uint32_t>(sec, info, ht, out, err, sms, s);
+  (void)sms;
+  if (jobs.n) {
+    note_launch();
+    k_huff_decode<<<ctas, 32 * kDecWarps, 0, s>>>(jobs, err);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -629,88 +719,97 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_s(
     const unsigned long long *__restrict__ bstart, uint64_t M, const uint32_t *__restrict__ s_rel,
     uint64_t nb, uint64_t n, uint32_t log2_chunk, const uint32_t *__restrict__ tile_first,
     float *__restrict__ out, int32_t *__restrict__ qout, int *__restrict__ err) {
-  __shared__ Plan sP;
-  __shared__ unsigned long long sb_start[kExpThreads + 1];
-  __shared__ uint32_t sb_f[kExpThreads + 1][D];
-  __shared__ uint32_t s_wv[32], s_wf[32];
-  if (threadIdx.x == 0) sP = *plan;
+  __shared__ FieldPlan sF[D];
+  __shared__ uint32_t sb_f[kExpThreads][D];
+  __shared__ uint8_t s_flag[kExpThreads];
+  __shared__ uint32_t s_wv[32], s_wf[32], s_wb[32];
+  __shared__ uint32_t s_lp;
+  if (threadIdx.x < D) sF[threadIdx.x] = plan->f[threadIdx.x];
+  if (threadIdx.x == 0) s_lp = plan->lp;
   // tiles of kExpThreads particles; the chunk size divides the tile, so every
   // tile starts a chunk (relative locations restart there)
   const uint64_t cmask = (1ull << log2_chunk) - 1ull;
   const uint64_t lo = (uint64_t)blockIdx.x * kExpThreads;
   const uint64_t hi = min(nb, lo + kExpThreads);
   const uint64_t first = tile_first[blockIdx.x];
+  s_flag[threadIdx.x] = 0;
   __syncthreads();
-  const uint32_t lp = sP.lp;
-  // load the blocks overlapping [lo, hi); block-id -> per-axis block indices
-  // by multiply-shift division (field 0 fastest)
+  const uint32_t lp = s_lp;
+  // block first + t: its per-axis block indices (multiply-shift division,
+  // field 0 fastest) and, for t > 0, a start flag at its first particle
   const uint64_t bi = first + threadIdx.x;
-  bool have = bi < M && bstart[bi] < hi;
-  if (have) {
-    sb_start[threadIdx.x] = bstart[bi];
-    unsigned long long r = bid[bi];
+  if (bi < M) {
+    const unsigned long long st = bstart[bi];
+    if (st < hi) {
+      if (threadIdx.x > 0 && st > lo) s_flag[st - lo] = 1;
+      unsigned long long r = bid[bi];
 #pragma unroll
-    for (int f = 0; f < D; ++f) {
-      const FieldPlan &F = sP.f[f];
-      unsigned long long qd = F.bshift == 255u ? r : (__umul64hi(r, F.bmagic) >> F.bshift);
-      unsigned long long bf = r - qd * F.bn;
-      sb_f[threadIdx.x][f] = (uint32_t)(bf << lp);
-      r = qd;
+      for (int f = 0; f < D; ++f) {
+        const FieldPlan &F = sF[f];
+        unsigned long long qd = F.bshift == 255u ? r : (__umul64hi(r, F.bmagic) >> F.bshift);
+        unsigned long long bf = r - qd * F.bn;
+        sb_f[threadIdx.x][f] = (uint32_t)(bf << lp);
+        r = qd;
+      }
     }
   }
-  const int nblk = __syncthreads_count(have);
-  // particle of this thread
+  __syncthreads();
+  // particle of this thread: block ordinal = inclusive count of start flags;
+  // relative code = segmented inclusive sum (segments at block and chunk starts)
   const uint64_t k = lo + threadIdx.x;
   const bool valid = k < hi;
-  int blk = 0;
-  unsigned long long v = 0;
-  bool seg = true;
-  if (valid) {
-    int a = 0, b = nblk;
-    while (b - a > 1) {
-      int mid = (a + b) >> 1;
-      if (sb_start[mid] <= k) a = mid;
-      else b = mid;
-    }
-    blk = a;
-    seg = (k == lo) || (sb_start[blk] == k) || ((k & cmask) == 0);
-    v = s_rel[k];
-  }
-  // segmented inclusive scan of v (segments start at block starts / chunk start)
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t x = (uint32_t)v;
+  const uint32_t flag = valid ? s_flag[threadIdx.x] : 0u;
+  const bool seg = (k == lo) || flag || ((k & cmask) == 0);
+  uint32_t x = valid ? s_rel[k] : 0u;
   uint32_t fl = seg ? 1u : 0u;
+  uint32_t cb = flag;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
     uint32_t g = __shfl_up_sync(0xffffffffu, fl, o);
-    if (lane >= o && !fl) x += y;
-    if (lane >= o) fl |= g;
+    uint32_t c = __shfl_up_sync(0xffffffffu, cb, o);
+    if (lane >= o) {
+      if (!fl) x += y;
+      fl |= g;
+      cb += c;
+    }
   }
   if (lane == 31) {
     s_wv[w] = x;
     s_wf[w] = fl;
+    s_wb[w] = cb;
   }
   __syncthreads();
   if (w == 0) {
-    uint32_t xv = s_wv[lane], xf = s_wf[lane];
+    uint32_t xv = s_wv[lane], xf = s_wf[lane], xb = s_wb[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t y = __shfl_up_sync(0xffffffffu, xv, o);
       uint32_t g = __shfl_up_sync(0xffffffffu, xf, o);
-      if (lane >= o && !xf) xv += y;
-      if (lane >= o) xf |= g;
+      uint32_t c = __shfl_up_sync(0xffffffffu, xb, o);
+      if (lane >= o) {
+        if (!xf) xv += y;
+        xf |= g;
+        xb += c;
+      }
     }
     s_wv[lane] = xv;  // inclusive carry-out of warps 0..lane
+    s_wb[lane] = xb;
   }
   __syncthreads();
-  if (w > 0 && !fl) x += s_wv[w - 1];
+  if (w > 0) {
+    if (!fl) x += s_wv[w - 1];
+    cb += s_wb[w - 1];
+  }
   if (!valid) return;
   const uint32_t rel = x;
+  const uint32_t blk = cb;
+  const uint32_t pm = (1u << lp) - 1u;
 #pragma unroll
   for (int f = 0; f < D; ++f) {
-    const FieldPlan &F = sP.f[f];
-    const uint32_t q = sb_f[blk][f] + ((rel >> (f * lp)) & ((1u << lp) - 1u));
+    const FieldPlan &F = sF[f];
+    const uint32_t q = sb_f[blk][f] + ((rel >> (f * lp)) & pm);
     if (q > F.qmax) atomicExch(err, 1);
     out[(uint64_t)f * n + k] = reconstruct((long long)q, F);
     if (qout) qout[(uint64_t)f * n + k] = (int32_t)q;

@@ -513,49 +513,17 @@ void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *b
 }
 
 // ---------------------------------------------------------------------------
-// in-place bitonic sort of n (a power of two) keys, optionally with payloads
-// compared as (key, payload), in shared memory
-// ---------------------------------------------------------------------------
-__device__ void bitonic_smem(unsigned long long *k, uint32_t *ix, int n) {
-  for (int size = 2; size <= n; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
-        const int a = 2 * stride * (t / stride) + (t % stride);
-        const int b = a + stride;
-        const bool up = (a & size) == 0;
-        const unsigned long long ka = k[a], kb = k[b];
-        bool gt;
-        if (ix) {
-          const uint32_t ia = ix[a], ib = ix[b];
-          gt = ka > kb || (ka == kb && ia > ib);
-          if (gt == up) {
-            k[a] = kb;
-            k[b] = ka;
-            ix[a] = ib;
-            ix[b] = ia;
-          }
-        } else {
-          gt = ka > kb;
-          if (gt == up) {
-            k[a] = kb;
-            k[b] = ka;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // per-unit sort + segmentation into blocks (persistent over units)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kLocalThreads) k_local(LocalArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  const bool perm = a.perm != nullptr;
   unsigned long long *sk = reinterpret_cast<unsigned long long *>(smem);
-  uint32_t *si = reinterpret_cast<uint32_t *>(sk + kCap);
-  uint32_t *s_cnt = si + kCap;                   // 256 * warps (global-memory path)
-  uint32_t *s_hist = s_cnt + 256 * kLocalWarps;  // 4096
+  unsigned long long *sk2 = sk + kCap;
+  uint32_t *s_cnt = reinterpret_cast<uint32_t *>(sk2 + kCap);  // 256 * warps
+  uint32_t *s_hist = s_cnt + 256 * kLocalWarps;                // 4096
+  uint32_t *si = s_hist + kAlpha;                               // perm mode only
+  uint32_t *si2 = si + kCap;
   __shared__ unsigned long long s_warp[32];
   __shared__ unsigned long long s_max, s_kmin, s_kmax;
   __shared__ Plan sP;
@@ -566,7 +534,6 @@ __global__ void __launch_bounds__(kLocalThreads) k_local(LocalArgs a) {
   for (int b = threadIdx.x; b < kAlpha; b += kLocalThreads) s_hist[b] = 0u;
   __syncthreads();
   if (sP.status != OK) return;
-  const bool perm = a.perm != nullptr;
   const uint32_t rel_bits = sP.rel_bits;
   const unsigned long long rel_mask = rel_bits >= 64 ? ~0ull : ((1ull << rel_bits) - 1ull);
   const uint64_t chunk_mask = (1ull << a.log2_chunk) - 1ull;
@@ -588,36 +555,35 @@ __global__ void __launch_bounds__(kLocalThreads) k_local(LocalArgs a) {
       gi = (src_alt ? a.idx_alt : a.idx) + lo;
       gi2 = (src_alt ? a.idx : a.idx_alt) + lo;
     }
+    // the radix passes cover only the bits where the unit's keys differ
+    if (threadIdx.x == 0) {
+      s_kmin = ~0ull;
+      s_kmax = 0ull;
+    }
+    __syncthreads();
+    const bool in_smem = cnt <= kCap;
+    unsigned long long mn = ~0ull, mx = 0ull;
+    for (int j = threadIdx.x; j < cnt; j += kLocalThreads) {
+      const unsigned long long v = gk[j];
+      if (in_smem) {
+        sk[j] = v;
+        if (gi) si[j] = gi[j];
+      }
+      mn = v < mn ? v : mn;
+      mx = v > mx ? v : mx;
+    }
+    atomicMin(&s_kmin, mn);
+    atomicMax(&s_kmax, mx);
+    __syncthreads();
+    const int kbits = (int)bitlen64(s_kmin ^ s_kmax);
     const unsigned long long *K;
     const uint32_t *I = nullptr;
-    if (cnt <= kCap) {
-      int n2 = 2;
-      while (n2 < cnt) n2 <<= 1;
-      for (int j = threadIdx.x; j < n2; j += kLocalThreads) {
-        sk[j] = j < cnt ? gk[j] : ~0ull;
-        if (gi) si[j] = j < cnt ? gi[j] : ~0u;
-      }
-      __syncthreads();
-      bitonic_smem(sk, gi ? si : nullptr, n2);
-      K = sk;
-      I = gi ? si : nullptr;
+    if (in_smem) {
+      int fl = cta_sort(sk, gi ? si : nullptr, sk2, gi ? si2 : nullptr, cnt, kbits,
+                        outl ? 0 : ibits, s_cnt, s_warp);
+      K = fl ? sk2 : sk;
+      I = gi ? (fl ? si2 : si) : nullptr;
     } else {
-      // global-memory LSD radix sort over the bits where the unit's keys differ
-      if (threadIdx.x == 0) {
-        s_kmin = ~0ull;
-        s_kmax = 0ull;
-      }
-      __syncthreads();
-      unsigned long long mn = ~0ull, mx = 0ull;
-      for (int j = threadIdx.x; j < cnt; j += kLocalThreads) {
-        const unsigned long long v = gk[j];
-        mn = v < mn ? v : mn;
-        mx = v > mx ? v : mx;
-      }
-      atomicMin(&s_kmin, mn);
-      atomicMax(&s_kmax, mx);
-      __syncthreads();
-      const int kbits = (int)bitlen64(s_kmin ^ s_kmax);
       int fl = cta_sort(gk, gi, gk2, gi2, cnt, kbits, outl ? 0 : ibits, s_cnt, s_warp);
       K = fl ? gk2 : gk;
       I = gi ? (fl ? gi2 : gi) : nullptr;
@@ -685,14 +651,17 @@ __global__ void __launch_bounds__(kLocalThreads) k_local(LocalArgs a) {
 }
 
 void launch_local(const LocalArgs &a, int ctas, cudaStream_t s) {
-  size_t smem = (size_t)kCap * (8 + 4) + 4ull * 256 * kLocalWarps + 4ull * kAlpha;
+  // keys ping-pong, radix counters, stream histogram; payload ping-pong in perm mode
+  const size_t base = (size_t)kCap * 16 + 4ull * 256 * kLocalWarps + 4ull * kAlpha;
+  const size_t smem = base + (a.perm ? (size_t)kCap * 8 : 0);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_local, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(base + (size_t)kCap * 8));
     attr = true;
   }
   note_launch();
-  k_local<<<ctas, kLocalThreads, smem, s>>>(a);
+  k_local<<<a.perm ? ctas / 2 : ctas, kLocalThreads, smem, s>>>(a);
 }
 
 // ---------------------------------------------------------------------------

@@ -962,12 +962,13 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
     TRY(grow(w.scan_tmp, tiles * 8));
     TRY(grow(w.scan_base, (tiles + 1) * 8));
     prof_begin(c, "d.streams", s);
-    launch_decode_u64(in + h.off[0], h.si[0], ht + 0, P<unsigned long long>(w.s_id), err, sms, s);
-    CK(cudaGetLastError());
-    launch_decode_u64(in + h.off[1], h.si[1], ht + 1, P<unsigned long long>(w.s_cnt), err, sms, s);
-    CK(cudaGetLastError());
-    launch_decode_u32(in + h.off[2], h.si[2], ht + 2, P<uint32_t>(w.s_rel), err, sms, s);
-    CK(cudaGetLastError());
+    {
+      const uint8_t *secs[3] = {in + h.off[0], in + h.off[1], in + h.off[2]};
+      void *outs[3] = {w.s_id.p, w.s_cnt.p, w.s_rel.p};
+      const int wide[3] = {1, 1, 0};
+      launch_decode_streams(3, secs, h.si, ht, outs, wide, err, sms, s);
+      CK(cudaGetLastError());
+    }
     prof_end(c, s);
     if (M > 0) {
       TRY(grow(w.scan_tmp, (M / 4096 + 2) * 32));
@@ -990,7 +991,12 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
     const uint64_t nd = std::max<uint64_t>(n * h.d, 1);
     TRY(grow(w.sym, nd * 4));
     prof_begin(c, "t.decode_stream", s);
-    launch_decode_u32(in + h.off[0], h.si[0], ht, P<uint32_t>(w.sym), err, sms, s);
+    {
+      const uint8_t *secs[1] = {in + h.off[0]};
+      void *outs[1] = {w.sym.p};
+      const int wide[1] = {0};
+      launch_decode_streams(1, secs, h.si, ht, outs, wide, err, sms, s);
+    }
     prof_end(c, s);
     const int32_t *qref = ra ? P<int32_t>(t->anc_q) : P<int32_t>(t->prev_q);
     prof_begin(c, "t.recon", s);

@@ -147,10 +147,11 @@ void launch_patches_apply(const uint8_t *sec, uint64_t K, uint64_t nd, float *ou
 // --- decode (k_decode.cu) --------------------------------------------------
 void launch_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan, cudaStream_t s);
 void launch_huff_table(const uint8_t *sec, HuffTable *T, cudaStream_t s);
-void launch_decode_u64(const uint8_t *sec, const StreamInfo &info, HuffTable *ht,
-                       unsigned long long *out, int *err, int sms, cudaStream_t s);
-void launch_decode_u32(const uint8_t *sec, const StreamInfo &info, HuffTable *ht, uint32_t *out,
-                       int *err, int sms, cudaStream_t s);
+// decodes ns streams (secs[k], infos[k]) into outs[k] (8-byte values when
+// wide[k], else 4-byte); Huffman streams share one launch (tables ht[k])
+void launch_decode_streams(int ns, const uint8_t *const *secs, const StreamInfo *infos,
+                           HuffTable *ht, void *const *outs, const int *wide, int *err, int sms,
+                           cudaStream_t s);
 // mode 1: values are zigzag codes, scanned after unzigzag
 void launch_scan_u64(const unsigned long long *in, uint64_t n, int mode, bool inclusive,
                      unsigned long long *out, unsigned long long *tile_tmp,
