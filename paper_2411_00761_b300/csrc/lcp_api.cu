@@ -235,7 +235,7 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   TRY(grow(w.tmp_bid, nn * 8));
   TRY(grow(w.tmp_pos, nn * 4));
   // segments: level-1 buckets, split ones replaced by their sub-buckets
-  const uint64_t nbig_max = n / 4096 + 1;
+  const uint64_t nbig_max = n / kUnitCap + 1;
   const uint64_t segcap = nb1 + nbig_max * 1024;
   TRY(grow(w.big_list, (size_t)nb1 * 4));
   TRY(grow(w.big_of, (size_t)nb1 * 4));
@@ -309,7 +309,7 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   la.log2_chunk = kLog2Chunk;
   la.n = n;
   prof_begin(c, "s.local_sort", s);
-  launch_local(la, 2 * sms, s);
+  launch_local(la, 4 * sms, s);
   prof_end(c, s);
   CK(cudaGetLastError());
   // 7. blocks: ids and counts

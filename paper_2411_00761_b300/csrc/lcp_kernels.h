@@ -7,6 +7,10 @@
 
 namespace lcp {
 
+// largest sort unit held in shared memory; partition buckets above it are
+// split by further key bits
+constexpr int kUnitCap = 2048;
+
 // kernels launched by this library in this process (all threads)
 extern unsigned long long g_launches;
 inline void note_launch() { __atomic_add_fetch(&g_launches, 1ull, __ATOMIC_RELAXED); }

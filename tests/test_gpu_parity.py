@@ -80,8 +80,11 @@ def frames_s():
 
 
 def check_s(ctx, orc, Xf, eb, mode, p):
-    r = ctx.compress(to_dev(Xf), eb, mode, p, perm=True)
     o = orc.compress_s(Xf, eb, mode, p)
+    # without the slot permutation (keys only) and with it (keys and indices)
+    r0 = ctx.compress(to_dev(Xf), eb, mode, p)
+    assert gpu_bytes(r0) == o["bytes"]
+    r = ctx.compress(to_dev(Xf), eb, mode, p, perm=True)
     gb = gpu_bytes(r)
     assert len(gb) == len(o["bytes"])
     assert gb == o["bytes"]
@@ -165,6 +168,30 @@ def test_block_size_autotune_matches_oracle(ctx, orc):
     r = ctx.compress(to_dev(Xf), 1e-4, "rel", p=0)
     assert r["size"] == sizes[best]
     assert gpu_bytes(r) == orc.compress_s(Xf, 1e-4, "rel", best)["bytes"]
+
+
+def test_sort_paths(ctx, orc):
+    """Sort units whose digit groups need every path of the unit sort:
+    windows of 2..512 particles sorted by one warp (32- and 64-bit keys,
+    with and without indices), windows too large for a warp (one digit
+    group of identical keys), and units beyond shared memory."""
+    rng = np.random.default_rng(12)
+    # many identical particles (one key) among random ones
+    a = np.concatenate([np.full((3, 3000), 0.4321, np.float32), rng.random((3, 2000))], axis=1)
+    check_s(ctx, orc, a[:, rng.permutation(a.shape[1])].astype(np.float32), 1e-3, "abs", 8)
+    # more identical particles than one shared-memory unit holds
+    b = np.concatenate([np.full((3, 9000), 0.25, np.float32), rng.random((3, 3000))], axis=1)
+    check_s(ctx, orc, b[:, rng.permutation(b.shape[1])].astype(np.float32), 1e-3, "abs", 8)
+    # keys wider than 32 bits inside a unit (small frame, fine bound)
+    check_s(ctx, orc, rng.random((3, 30000)).astype(np.float32), 1e-5, "abs", 4)
+    # dense blocks of 200..500 particles: large windows
+    cl = []
+    for k in range(48):
+        c = rng.random(3) * 0.9
+        m = int(rng.integers(200, 500))
+        cl.append(c[:, None] + rng.random((3, m)) * 0.015)
+    c = np.concatenate(cl + [rng.random((3, 5000))], axis=1).astype(np.float32)
+    check_s(ctx, orc, c[:, rng.permutation(c.shape[1])], 1e-3, "abs", 8)
 
 
 # ---------------------------------------------------------------------------
