@@ -1,13 +1,19 @@
-// k_sort.cu -- partition by the key's top bits, per-bucket sort, segmentation.
+// k_sort.cu -- partition by the key's top bits, sorting, segmentation.
 //
 // Sec. "Design of spatial blocks": the non-empty blocks are kept in id order
 // with their particle counts and the particles' locations relative to the
 // block corner; Sec. "Block coding": each array is delta coded.  The keys
-// (block_id * p^d + rel) are sorted with one most-significant-digit partition
-// pass into buckets of consecutive block ids, then every bucket is sorted by
-// one CTA (in shared memory when it fits) and segmented into blocks in the
-// same CTA.  The output bytes depend only on the multiset of keys, so the
-// partition pass needs no stable order.
+// (block_id * p^d + rel) are sorted most-significant digit first: one
+// partition pass into buckets of consecutive block ids; buckets above
+// kSplitMin keys are partitioned again by the next block-id bits into
+// sub-buckets, and runs of sub-buckets are sorted by one warp each in
+// registers; small buckets are merged into units that one CTA sorts in
+// shared memory.  Every sorted run starts at a block boundary, so it is
+// segmented where it is sorted: a start flag and the block id at each
+// block's first particle, the relative-location deltas for every particle.
+// A scan of the start flags then numbers the blocks.  The output bytes
+// depend only on the multiset of keys, so no partition pass needs a stable
+// order.
 #include <type_traits>
 
 #include "lcp_kernels.h"
@@ -17,9 +23,12 @@ namespace lcp {
 constexpr int kLocalThreads = 256;
 constexpr int kLocalWarps = kLocalThreads / 32;
 constexpr int kCap = kUnitCap;  // keys of a unit sorted in shared memory
-constexpr int kSubBits = 10;    // level-2 split of oversized buckets
+constexpr int kSubBits = 10;    // level-2 split of buckets above kSplitMin keys
+constexpr int kSplitMin = 256;
 constexpr int kSplitThreads = 512;
 constexpr int kSplitIlp = 4;    // keys in flight per thread in the split passes
+constexpr int kSubThreads = 256;
+constexpr int kSubSpan = 16;    // sub-bucket runs: a new run where the offset enters a new span
 
 // ---------------------------------------------------------------------------
 // block-wide exclusive scan of u64 values held one per thread
@@ -267,15 +276,16 @@ __device__ int cta_sort(unsigned long long *k, uint32_t *i, unsigned long long *
 }
 
 // ---------------------------------------------------------------------------
-// level-2 partition of buckets larger than the shared-memory sort: each such
-// bucket is split by the next kSubBits key bits (still block-id bits, so no
-// block crosses a sub-bucket).  Sort units: the ordered list of key ranges
-// that k_local sorts -- consecutive small level-1 buckets merged greedily up
-// to kCap keys, runs of consecutive sub-buckets of a split bucket, and the
-// outlier bucket.  A split bucket's units start at every sub-bucket whose
-// offset enters a new span of kCap/2 slots, so a unit holds fewer than
-// kCap/2 keys plus its last sub-bucket.
+// level-2 partition of buckets above kSplitMin keys: each such bucket is
+// split by the next kSubBits key bits (still block-id bits, so no block
+// crosses a sub-bucket), one CTA per bucket.  Sort units (k_local): the
+// ordered list of key ranges holding consecutive unsplit buckets merged
+// greedily up to kCap keys, and the outlier bucket.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int split_bits(const Plan &P) {
+  return min(kSubBits, (int)P.part_shift - (int)P.rel_bits);
+}
+
 __global__ void __launch_bounds__(1024) k_seg_plan(const Plan *__restrict__ plan, uint32_t nb1,
                                                    const unsigned long long *__restrict__ bstart,
                                                    uint32_t *__restrict__ big_list,
@@ -284,18 +294,20 @@ __global__ void __launch_bounds__(1024) k_seg_plan(const Plan *__restrict__ plan
   __shared__ unsigned long long s_warp[32];
   const Plan &P = *plan;
   const uint32_t nb = nb1 - 1;
-  const int sub = min(kSubBits, (int)P.part_shift - (int)P.rel_bits);
+  const int sub = split_bits(P);
   const uint32_t per = (nb1 + 1023) / 1024;
   const uint32_t lo = threadIdx.x * per, hi = min(nb1, lo + per);
   unsigned long long c = 0;
   for (uint32_t b = lo; b < hi; ++b) {
-    const bool big = sub > 0 && b < nb && (bstart[b + 1] - bstart[b]) > (unsigned long long)kCap;
+    const bool big =
+        sub > 0 && b < nb && (bstart[b + 1] - bstart[b]) > (unsigned long long)kSplitMin;
     c += big;
   }
   unsigned long long tot;
   unsigned long long run = block_exscan<1024>(c, s_warp, tot);
   for (uint32_t b = lo; b < hi; ++b) {
-    const bool big = sub > 0 && b < nb && (bstart[b + 1] - bstart[b]) > (unsigned long long)kCap;
+    const bool big =
+        sub > 0 && b < nb && (bstart[b + 1] - bstart[b]) > (unsigned long long)kSplitMin;
     big_of[b] = big ? (int)run : -1;
     if (big) big_list[run++] = b;
   }
@@ -306,26 +318,25 @@ __global__ void __launch_bounds__(1024) k_seg_plan(const Plan *__restrict__ plan
 }
 
 // One CTA per split bucket (fetched from a work counter): sub-bucket
-// histogram, offsets, unit starts (unit_off[j][u], offsets within the
-// bucket), then the scatter.  Loads are issued kSplitIlp at a time.
+// histogram, offsets (sub_off[j][digit], within the bucket), scatter.
+// Loads are issued kSplitIlp at a time.
 __global__ void __launch_bounds__(kSplitThreads) k_split_big(
     const Plan *__restrict__ plan, const unsigned long long *__restrict__ bstart,
     const uint32_t *__restrict__ big_list, uint32_t *__restrict__ nbig,
     const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ idx,
     unsigned long long *__restrict__ keys_out, uint32_t *__restrict__ idx_out,
-    uint32_t *__restrict__ unit_off, uint32_t *__restrict__ big_units) {
+    uint32_t *__restrict__ sub_off) {
   constexpr int kSub = 1 << kSubBits;
   constexpr int per = kSub / kSplitThreads;
   __shared__ uint32_t h[kSub];
   __shared__ unsigned long long s_warp[32];
   __shared__ uint32_t s_j;
   const Plan &P = *plan;
-  const int sub = min(kSubBits, (int)P.part_shift - (int)P.rel_bits);
+  const int sub = split_bits(P);
   const int shift2 = (int)P.part_shift - sub;
   const uint32_t mask = (1u << sub) - 1u;
   const uint32_t nsub = 1u << sub;
   const uint32_t total_big = nbig[0];
-  const uint32_t G = (uint32_t)kCap / 2;
   for (;;) {
     if (threadIdx.x == 0) s_j = atomicAdd(&nbig[1], 1u);
     for (int d = threadIdx.x; d < kSub; d += kSplitThreads) h[d] = 0u;
@@ -350,8 +361,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
       }
     }
     __syncthreads();
-    // offsets and unit starts; thread t owns sub-buckets t*per .. t*per+per-1
-    uint32_t c[per], off[per];
+    // offsets; thread t owns sub-buckets t*per .. t*per+per-1
+    uint32_t c[per];
     unsigned long long sum = 0;
 #pragma unroll
     for (int q = 0; q < per; ++q) {
@@ -361,37 +372,15 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
     }
     unsigned long long tot;
     uint32_t run = (uint32_t)block_exscan<kSplitThreads>(sum, s_warp, tot);
+    uint32_t *so = sub_off + (uint64_t)j * kSub;
 #pragma unroll
     for (int q = 0; q < per; ++q) {
-      off[q] = run;
+      const uint32_t dg = threadIdx.x * per + q;
+      if (dg < nsub) {
+        so[dg] = run;
+        h[dg] = run;
+      }
       run += c[q];
-    }
-    // the offset of the sub-bucket before this thread's first one
-    __syncthreads();
-    if (threadIdx.x * per + per - 1 < (uint32_t)kSub) h[threadIdx.x * per + per - 1] = off[per - 1];
-    __syncthreads();
-    const uint32_t prev0 = threadIdx.x > 0 ? h[threadIdx.x * per - 1] : 0u;
-    uint32_t ncut = 0;
-    bool cut[per];
-#pragma unroll
-    for (int q = 0; q < per; ++q) {
-      const uint32_t dg = threadIdx.x * per + q;
-      const uint32_t pv = q ? off[q - 1] : prev0;
-      cut[q] = dg < nsub && off[q] < cnt && (dg == 0 || off[q] / G != pv / G);
-      ncut += cut[q];
-    }
-    __syncthreads();
-    unsigned long long nunits;
-    uint32_t uo = (uint32_t)block_exscan<kSplitThreads>(ncut, s_warp, nunits);
-    uint32_t *uj = unit_off + (uint64_t)j * kSub;
-#pragma unroll
-    for (int q = 0; q < per; ++q)
-      if (cut[q]) uj[uo++] = off[q];
-    if (threadIdx.x == 0) big_units[j] = (uint32_t)nunits;
-#pragma unroll
-    for (int q = 0; q < per; ++q) {
-      const uint32_t dg = threadIdx.x * per + q;
-      if (dg < nsub) h[dg] = off[q];
     }
     __syncthreads();
     for (uint32_t t0 = 0; t0 < cnt; t0 += kSplitThreads * kSplitIlp) {
@@ -418,15 +407,12 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
 }
 
 // Unit list (one CTA).  Thread t owns buckets [t*per, (t+1)*per); within that
-// range consecutive small buckets merge greedily up to kCap keys (a single
+// range consecutive unsplit buckets merge greedily up to kCap keys (a single
 // bucket above kCap that cannot be split forms its own unit); a split bucket
-// contributes its units, written by k_units_big at big_base[j]; the outlier
-// bucket is a unit of its own.
+// ends the run; the outlier bucket is a unit of its own.
 __global__ void __launch_bounds__(1024) k_units_small(uint32_t nb1,
                                                       const unsigned long long *__restrict__ bstart,
                                                       const int *__restrict__ big_of,
-                                                      const uint32_t *__restrict__ big_units,
-                                                      uint32_t *__restrict__ big_base,
                                                       uint32_t *__restrict__ u_lo,
                                                       uint32_t *__restrict__ u_cnt,
                                                       uint32_t *__restrict__ u_meta,
@@ -439,14 +425,12 @@ __global__ void __launch_bounds__(1024) k_units_small(uint32_t nb1,
   uint64_t ucnt = 0;
   for (uint32_t b = lo; b < hi; ++b) {
     const uint64_t c = bstart[b + 1] - bstart[b];
-    const int j = big_of[b];
-    if (j >= 0 || b == nb) {
+    if (big_of[b] >= 0 || b == nb) {
       if (ucnt) {
         ++count;
         ucnt = 0;
       }
-      if (j >= 0) count += big_units[j];
-      else if (c) ++count;
+      if (b == nb && c) ++count;
       continue;
     }
     if (!c) continue;
@@ -464,8 +448,7 @@ __global__ void __launch_bounds__(1024) k_units_small(uint32_t nb1,
   ucnt = 0;
   for (uint32_t b = lo; b < hi; ++b) {
     const uint64_t c = bstart[b + 1] - bstart[b];
-    const int j = big_of[b];
-    if (j >= 0 || b == nb) {
+    if (big_of[b] >= 0 || b == nb) {
       if (ucnt) {
         u_lo[out] = (uint32_t)ulo;
         u_cnt[out] = (uint32_t)ucnt;
@@ -473,10 +456,7 @@ __global__ void __launch_bounds__(1024) k_units_small(uint32_t nb1,
         ++out;
         ucnt = 0;
       }
-      if (j >= 0) {
-        big_base[j] = (uint32_t)out;
-        out += big_units[j];
-      } else if (c) {
+      if (b == nb && c) {
         u_lo[out] = (uint32_t)bstart[b];
         u_cnt[out] = (uint32_t)c;
         u_meta[out] = 2u;  // the outlier bucket
@@ -502,49 +482,18 @@ __global__ void __launch_bounds__(1024) k_units_small(uint32_t nb1,
   }
 }
 
-// units of the split buckets: one warp per bucket, lanes over its units
-__global__ void k_units_big(const unsigned long long *__restrict__ bstart,
-                            const uint32_t *__restrict__ big_list,
-                            const uint32_t *__restrict__ nbig,
-                            const uint32_t *__restrict__ unit_off,
-                            const uint32_t *__restrict__ big_units,
-                            const uint32_t *__restrict__ big_base, uint32_t *__restrict__ u_lo,
-                            uint32_t *__restrict__ u_cnt, uint32_t *__restrict__ u_meta) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
-  for (uint32_t j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < nbig[0]; j += warps) {
-    const uint32_t b = big_list[j];
-    const uint64_t lo = bstart[b];
-    const uint32_t cnt = (uint32_t)(bstart[b + 1] - lo);
-    const uint32_t nu = big_units[j], o = big_base[j];
-    const uint32_t *uj = unit_off + (uint64_t)j * (1u << kSubBits);
-    for (uint32_t u = lane; u < nu; u += 32) {
-      const uint32_t a = uj[u], e = u + 1 < nu ? uj[u + 1] : cnt;
-      u_lo[o + u] = (uint32_t)(lo + a);
-      u_cnt[o + u] = e - a;
-      u_meta[o + u] = 1u;  // keys in the level-2 buffer
-    }
-  }
-}
-
 void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *bstart,
                      unsigned long long *keys, uint32_t *idx, unsigned long long *keys_alt,
                      uint32_t *idx_alt, uint32_t *big_list, int *big_of, uint32_t *nbig,
-                     uint32_t *sub_cnt, uint32_t *big_units, uint32_t *big_base, uint32_t *u_lo,
-                     uint32_t *u_cnt, uint32_t *u_meta, uint32_t *nunit, uint64_t n, int sms,
-                     cudaStream_t s) {
-  (void)n;
+                     uint32_t *sub_off, uint32_t *u_lo, uint32_t *u_cnt, uint32_t *u_meta,
+                     uint32_t *nunit, int sms, cudaStream_t s) {
   note_launch();
   k_seg_plan<<<1, 1024, 0, s>>>(plan, nb1, bstart, big_list, big_of, nbig);
   note_launch();
   k_split_big<<<4 * sms, kSplitThreads, 0, s>>>(plan, bstart, big_list, nbig, keys, idx, keys_alt,
-                                                idx_alt, sub_cnt, big_units);
+                                                idx_alt, sub_off);
   note_launch();
-  k_units_small<<<1, 1024, 0, s>>>(nb1, bstart, big_of, big_units, big_base, u_lo, u_cnt, u_meta,
-                                   nunit);
-  note_launch();
-  k_units_big<<<sms, 256, 0, s>>>(bstart, big_list, nbig, sub_cnt, big_units, big_base, u_lo,
-                                  u_cnt, u_meta);
+  k_units_small<<<1, 1024, 0, s>>>(nb1, bstart, big_of, u_lo, u_cnt, u_meta, nunit);
 }
 
 // ---------------------------------------------------------------------------
@@ -622,13 +571,12 @@ struct WinElem {
 };
 
 template <int MODE>
-__device__ __forceinline__ typename WinElem<MODE>::T win_load(const unsigned long long *sk,
-                                                              const uint32_t *si, int j,
+__device__ __forceinline__ typename WinElem<MODE>::T win_make(unsigned long long key, uint32_t ix,
                                                               unsigned long long base) {
-  if constexpr (MODE == 0) return (uint32_t)(sk[j] - base);
-  else if constexpr (MODE == 1) return sk[j];
-  else if constexpr (MODE == 2) return ((sk[j] - base) << 32) | (unsigned long long)si[j];
-  else return KeyIdx{sk[j], si[j]};
+  if constexpr (MODE == 0) return (uint32_t)(key - base);
+  else if constexpr (MODE == 1) return key;
+  else if constexpr (MODE == 2) return ((key - base) << 32) | (unsigned long long)ix;
+  else return KeyIdx{key, ix};
 }
 template <int MODE>
 __device__ __forceinline__ typename WinElem<MODE>::T win_pad() {
@@ -637,24 +585,36 @@ __device__ __forceinline__ typename WinElem<MODE>::T win_pad() {
   else return ~0ull;
 }
 template <int MODE>
-__device__ __forceinline__ void win_store(unsigned long long *sk, uint32_t *si, int j,
-                                          const typename WinElem<MODE>::T &v,
-                                          unsigned long long base) {
+__device__ __forceinline__ void win_split(const typename WinElem<MODE>::T &v,
+                                          unsigned long long base, unsigned long long &key,
+                                          uint32_t &ix) {
   if constexpr (MODE == 0) {
-    sk[j] = base + v;
+    key = base + v;
+    ix = 0u;
   } else if constexpr (MODE == 1) {
-    sk[j] = v;
+    key = v;
+    ix = 0u;
   } else if constexpr (MODE == 2) {
-    sk[j] = base + (v >> 32);
-    si[j] = (uint32_t)v;
+    key = base + (v >> 32);
+    ix = (uint32_t)v;
   } else {
-    sk[j] = v.k;
-    si[j] = v.i;
+    key = v.k;
+    ix = v.i;
   }
 }
 
+// largest window one warp sorts in registers
+__host__ __device__ constexpr int window_cap(int mode) { return mode == 3 ? 256 : 512; }
+
+// the element form of a window whose keys lie in [base, base + span)
+__device__ __forceinline__ int window_mode(unsigned long long span, bool with_idx) {
+  const bool narrow = span <= (1ull << 32);
+  return narrow ? (with_idx ? 2 : 0) : (with_idx ? 3 : 1);
+}
+
+// sorts the shared-memory window [w0, w0 + c) in place
 template <int R, int MODE>
-__device__ __forceinline__ void sort_window_r(unsigned long long *sk, uint32_t *si, int w0, int c,
+__device__ __forceinline__ void smem_window_r(unsigned long long *sk, uint32_t *si, int w0, int c,
                                               unsigned long long base) {
   using T = typename WinElem<MODE>::T;
   const int lane = threadIdx.x & 31;
@@ -662,31 +622,236 @@ __device__ __forceinline__ void sort_window_r(unsigned long long *sk, uint32_t *
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int i = lane * R + r;
-    v[r] = i < c ? win_load<MODE>(sk, si, w0 + i, base) : win_pad<MODE>();
+    v[r] = i < c ? win_make<MODE>(sk[w0 + i], MODE >= 2 ? si[w0 + i] : 0u, base)
+                 : win_pad<MODE>();
   }
   warp_bitonic<R>(v);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int i = lane * R + r;
-    if (i < c) win_store<MODE>(sk, si, w0 + i, v[r], base);
+    if (i < c) {
+      unsigned long long key;
+      uint32_t ix;
+      win_split<MODE>(v[r], base, key, ix);
+      sk[w0 + i] = key;
+      if (MODE >= 2) si[w0 + i] = ix;
+    }
   }
 }
 
-// largest window one warp sorts in registers
-__device__ __forceinline__ int window_cap(int mode) { return mode == 3 ? 256 : 512; }
-
 template <int MODE>
-__device__ __noinline__ void sort_window(unsigned long long *sk, uint32_t *si, int w0, int c,
+__device__ __noinline__ void smem_window(unsigned long long *sk, uint32_t *si, int w0, int c,
                                          unsigned long long base) {
-  if (c <= 32) sort_window_r<1, MODE>(sk, si, w0, c, base);
-  else if (c <= 64) sort_window_r<2, MODE>(sk, si, w0, c, base);
-  else if (c <= 128) sort_window_r<4, MODE>(sk, si, w0, c, base);
-  else if (c <= 256) sort_window_r<8, MODE>(sk, si, w0, c, base);
-  else if constexpr (MODE != 3) sort_window_r<16, MODE>(sk, si, w0, c, base);
+  if (c <= 32) smem_window_r<1, MODE>(sk, si, w0, c, base);
+  else if (c <= 64) smem_window_r<2, MODE>(sk, si, w0, c, base);
+  else if (c <= 128) smem_window_r<4, MODE>(sk, si, w0, c, base);
+  else if (c <= 256) smem_window_r<8, MODE>(sk, si, w0, c, base);
+  else if constexpr (MODE != 3) smem_window_r<16, MODE>(sk, si, w0, c, base);
 }
 
 // ---------------------------------------------------------------------------
-// per-unit sort + segmentation into blocks (persistent over units).
+// segmentation outputs of one sorted particle at slot g (its predecessor in
+// sorted order is prev; start: the particle opens a block)
+// ---------------------------------------------------------------------------
+struct SegOut {
+  uint32_t *s_rel;
+  uint8_t *bflag;
+  unsigned long long *tmp_bid;
+  uint32_t *perm;
+  const int32_t *q_in;
+  int32_t *q_slot;
+  uint64_t n;
+  uint32_t d, rel_bits;
+  unsigned long long rel_mask;
+  uint64_t chunk_mask;
+};
+
+template <bool PERM>
+__device__ __forceinline__ void seg_emit(const SegOut &o, bool valid, uint64_t g,
+                                         unsigned long long key, unsigned long long prev,
+                                         bool start, uint32_t ix, uint32_t *s_hist,
+                                         unsigned long long &my_max) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long v = 0ull;
+  if (valid) {
+    const unsigned long long rel = key & o.rel_mask;
+    v = (start || (g & o.chunk_mask) == 0) ? rel : rel - (prev & o.rel_mask);
+    o.s_rel[g] = (uint32_t)v;
+    o.bflag[g] = start ? 1 : 0;
+    if (start) o.tmp_bid[g] = key >> o.rel_bits;
+    my_max = v > my_max ? v : my_max;
+    if (PERM) {
+      o.perm[g] = ix;
+      if (o.q_slot)
+        for (uint32_t f = 0; f < o.d; ++f)
+          o.q_slot[(uint64_t)f * o.n + g] = o.q_in[(uint64_t)f * o.n + ix];
+    }
+  }
+  // stream-2 histogram: escapes counted per warp, other values per lane
+  const bool esc = valid && v >= (unsigned long long)kEsc;
+  const uint32_t nesc = __popc(__ballot_sync(0xffffffffu, esc));
+  if (lane == 0 && nesc) atomicAdd(&s_hist[kEsc], nesc);
+  if (valid && !esc) atomicAdd(&s_hist[(uint32_t)v], 1u);
+}
+
+// ---------------------------------------------------------------------------
+// sub-bucket runs of the split buckets: one warp per run, sorted and
+// segmented in registers.  Warp tasks are (split bucket, 32 consecutive
+// sub-buckets); a run starts at the first non-empty sub-bucket of the task
+// and wherever a sub-bucket's offset enters a new kSubSpan-slot span, so a
+// run holds fewer than kSubSpan particles plus its last sub-bucket.  A run
+// too large for a warp becomes a k_local unit.
+// ---------------------------------------------------------------------------
+template <int R, int MODE, bool PERM>
+__device__ __forceinline__ void sub_run_r(const unsigned long long *ks, const uint32_t *is, int c,
+                                          unsigned long long base, uint64_t g0, const SegOut &o,
+                                          uint32_t *s_hist, unsigned long long &my_max) {
+  using T = typename WinElem<MODE>::T;
+  const int lane = threadIdx.x & 31;
+  T v[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane * R + r;
+    v[r] = i < c ? win_make<MODE>(ks[i], PERM ? is[i] : 0u, base) : win_pad<MODE>();
+  }
+  if (c > 1) warp_bitonic<R>(v);
+  unsigned long long key[R];
+  uint32_t ix[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) win_split<MODE>(v[r], base, key[r], ix[r]);
+  const unsigned long long lp = __shfl_up_sync(0xffffffffu, key[R - 1], 1);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int i = lane * R + r;
+    const unsigned long long prev = r ? key[r - 1] : lp;
+    const bool start = i == 0 || (key[r] >> o.rel_bits) != (prev >> o.rel_bits);
+    seg_emit<PERM>(o, i < c, g0 + (uint64_t)i, key[r], prev, start, ix[r], s_hist, my_max);
+  }
+}
+
+template <int MODE, bool PERM>
+__device__ __noinline__ void sub_run(const unsigned long long *ks, const uint32_t *is, int c,
+                                     unsigned long long base, uint64_t g0, const SegOut &o,
+                                     uint32_t *s_hist, unsigned long long &my_max) {
+  if (c <= 32) sub_run_r<1, MODE, PERM>(ks, is, c, base, g0, o, s_hist, my_max);
+  else if (c <= 64) sub_run_r<2, MODE, PERM>(ks, is, c, base, g0, o, s_hist, my_max);
+  else if (c <= 128) sub_run_r<4, MODE, PERM>(ks, is, c, base, g0, o, s_hist, my_max);
+  else if (c <= 256) sub_run_r<8, MODE, PERM>(ks, is, c, base, g0, o, s_hist, my_max);
+  else if constexpr (MODE != 3) sub_run_r<16, MODE, PERM>(ks, is, c, base, g0, o, s_hist, my_max);
+}
+
+template <bool PERM>
+__global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
+  constexpr int kSub = 1 << kSubBits;
+  __shared__ uint32_t s_hist[kAlpha];
+  __shared__ unsigned long long s_max;
+  __shared__ int s_status;
+  __shared__ uint32_t s_part, s_rel, s_d, s_nbig;
+  if (threadIdx.x == 0) {
+    s_status = A.plan->status;
+    s_part = A.plan->part_shift;
+    s_rel = A.plan->rel_bits;
+    s_d = A.plan->d;
+    s_nbig = A.nbig[0];
+    s_max = 0ull;
+  }
+  for (int b = threadIdx.x; b < kAlpha; b += kSubThreads) s_hist[b] = 0u;
+  __syncthreads();
+  if (s_status != OK) return;
+  const int lane = threadIdx.x & 31;
+  const uint32_t part_shift = s_part, rel_bits = s_rel;
+  const int sub = min(kSubBits, (int)part_shift - (int)rel_bits);
+  const uint32_t nsub = 1u << sub;
+  const int shift2 = (int)part_shift - sub;
+  SegOut o;
+  o.s_rel = A.s_rel;
+  o.bflag = A.bflag;
+  o.tmp_bid = A.tmp_bid;
+  o.perm = A.perm;
+  o.q_in = A.q_in;
+  o.q_slot = A.q_slot;
+  o.n = A.n;
+  o.d = s_d;
+  o.rel_bits = rel_bits;
+  o.rel_mask = (1ull << rel_bits) - 1ull;
+  o.chunk_mask = (1ull << A.log2_chunk) - 1ull;
+  unsigned long long my_max = 0ull;
+  const uint32_t ntask = s_nbig * 32u;
+  const uint32_t warps = gridDim.x * (kSubThreads / 32);
+  for (uint32_t t = blockIdx.x * (kSubThreads / 32) + (threadIdx.x >> 5); t < ntask; t += warps) {
+    const uint32_t j = t >> 5, ch = t & 31u;
+    if (ch * 32u >= nsub) continue;
+    const uint32_t b = A.big_list[j];
+    const uint64_t lo = A.bstart[b];
+    const uint32_t cnt = (uint32_t)(A.bstart[b + 1] - lo);
+    const uint32_t *so = A.sub_off + (uint64_t)j * kSub;
+    const uint32_t dg = ch * 32u + lane;
+    const uint32_t off = dg < nsub ? so[dg] : cnt;
+    uint32_t nx = __shfl_down_sync(0xffffffffu, off, 1);
+    if (lane == 31) nx = dg + 1 < nsub ? so[dg + 1] : cnt;
+    const uint32_t c = nx - off;
+    const uint32_t ne = __ballot_sync(0xffffffffu, c > 0);
+    if (!ne) continue;
+    const uint32_t pv = __shfl_up_sync(0xffffffffu, off, 1);
+    const bool cut =
+        c > 0 && ((uint32_t)lane == (uint32_t)(__ffs(ne) - 1) || off / kSubSpan != pv / kSubSpan);
+    uint32_t M = __ballot_sync(0xffffffffu, cut);
+    const uint32_t chunk_end = __shfl_sync(0xffffffffu, nx, 31);
+    const unsigned long long bucket_base = (unsigned long long)b << part_shift;
+    const unsigned long long *ks = A.keys_alt + lo;
+    const uint32_t *is = PERM ? A.idx_alt + lo : nullptr;
+    while (M) {
+      const int l0 = __ffs(M) - 1;
+      M &= M - 1u;
+      const int l1 = M ? __ffs(M) - 1 : 32;
+      const uint32_t w0 = __shfl_sync(0xffffffffu, off, l0);
+      const uint32_t wend = __shfl_sync(0xffffffffu, off, l1 & 31);
+      const uint32_t w1 = l1 == 32 ? chunk_end : wend;
+      const int wc = (int)(w1 - w0);
+      // digits of the run: l0 .. last non-empty lane before l1
+      const uint32_t below = l1 == 32 ? ne : (ne & ((1u << l1) - 1u));
+      const uint32_t g0 = ch * 32u + (uint32_t)l0;
+      const uint32_t g1 = ch * 32u + (uint32_t)(32 - __clz(below));
+      const unsigned long long base = bucket_base | ((unsigned long long)g0 << shift2);
+      const int mode = window_mode((unsigned long long)(g1 - g0) << shift2, PERM);
+      if (wc > window_cap(mode)) {
+        if (lane == 0) {
+          const uint32_t u = atomicAdd(A.nunit, 1u);
+          A.u_lo[u] = (uint32_t)(lo + w0);
+          A.u_cnt[u] = (uint32_t)wc;
+          A.u_meta[u] = 1u;  // keys in the level-2 buffer
+        }
+        continue;
+      }
+      const uint64_t g = lo + w0;
+      if (mode == 0) {
+        sub_run<0, PERM>(ks + w0, PERM ? is + w0 : nullptr, wc, base, g, o, s_hist, my_max);
+      } else if (mode == 1) {
+        sub_run<1, PERM>(ks + w0, PERM ? is + w0 : nullptr, wc, base, g, o, s_hist, my_max);
+      } else {
+        if constexpr (PERM) {
+          if (mode == 2) sub_run<2, true>(ks + w0, is + w0, wc, base, g, o, s_hist, my_max);
+          else sub_run<3, true>(ks + w0, is + w0, wc, base, g, o, s_hist, my_max);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < kAlpha; s += kSubThreads)
+    if (s_hist[s]) atomicAdd(&A.hist[2 * kAlpha + s], s_hist[s]);
+  atomicMax(&s_max, my_max);
+  __syncthreads();
+  if (threadIdx.x == 0 && s_max) atomicMax(&A.maxv[2], s_max);
+}
+
+void launch_subsort(const SubsortArgs &a, int sms, cudaStream_t s) {
+  note_launch();
+  if (a.perm) k_subsort<true><<<4 * sms, kSubThreads, 0, s>>>(a);
+  else k_subsort<false><<<4 * sms, kSubThreads, 0, s>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// per-unit sort + segmentation (persistent over units).
 //
 // A unit of up to kCap keys is sorted in shared memory: the keys are loaded
 // into registers, partitioned by their top 8 varying bits (one counting
@@ -696,7 +861,8 @@ __device__ __noinline__ void sort_window(unsigned long long *sk, uint32_t *si, i
 // on 32-bit offsets from the window's base key when its key span allows.
 // Windows too large for a warp (a digit group of hundreds of keys) fall back
 // to the CTA radix sort.  Sorting each window sorts the unit because the
-// windows are ordered by digit.
+// windows are ordered by digit.  Larger units are sorted by the CTA radix
+// sort in global memory.
 // ---------------------------------------------------------------------------
 constexpr int kPer = kCap / kLocalThreads;  // keys per thread of a unit
 constexpr int kWinSpan = 32;
@@ -715,25 +881,32 @@ __global__ void __launch_bounds__(kLocalThreads, 4) k_local(LocalArgs a) {
   __shared__ uint32_t s_win[kMaxWin];
   __shared__ uint8_t s_wdg[kMaxWin];
   __shared__ uint32_t s_nwin;
-  __shared__ uint32_t s_wcnt[kLocalWarps];
-  __shared__ uint32_t s_status;
-  __shared__ uint32_t s_relb;
-  __shared__ uint32_t s_nseg;
+  __shared__ int s_status;
+  __shared__ uint32_t s_relb, s_d, s_nseg;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) {
-    s_status = (uint32_t)a.plan->status;
+    s_status = a.plan->status;
     s_relb = a.plan->rel_bits;
+    s_d = a.plan->d;
     s_nseg = *a.nseg;
     s_max = 0ull;
   }
   for (int b = threadIdx.x; b < kAlpha; b += kLocalThreads) s_hist[b] = 0u;
   __syncthreads();
-  if ((int)s_status != OK) return;
-  const uint32_t rel_bits = s_relb;
-  const unsigned long long rel_mask = rel_bits >= 64 ? ~0ull : ((1ull << rel_bits) - 1ull);
-  const uint64_t chunk_mask = (1ull << a.log2_chunk) - 1ull;
+  if (s_status != OK) return;
+  SegOut o;
+  o.s_rel = a.s_rel;
+  o.bflag = a.bflag;
+  o.tmp_bid = a.tmp_bid;
+  o.perm = a.perm;
+  o.q_in = a.q_in;
+  o.q_slot = a.q_slot;
+  o.n = a.n;
+  o.d = s_d;
+  o.rel_bits = s_relb;
+  o.rel_mask = (1ull << s_relb) - 1ull;
+  o.chunk_mask = (1ull << a.log2_chunk) - 1ull;
   const int ibits = PERM ? (int)bitlen64(a.n > 0 ? a.n - 1 : 0) : 0;
-  const uint32_t d = a.plan->d;
   const uint32_t nseg = s_nseg;
   const uint32_t lt = lanemask_lt();
   unsigned long long my_max = 0ull;
@@ -777,9 +950,9 @@ __global__ void __launch_bounds__(kLocalThreads, 4) k_local(LocalArgs a) {
         }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long a1 = __shfl_xor_sync(0xffffffffu, mn, o);
-        const unsigned long long b1 = __shfl_xor_sync(0xffffffffu, mx, o);
+      for (int q = 16; q > 0; q >>= 1) {
+        const unsigned long long a1 = __shfl_xor_sync(0xffffffffu, mn, q);
+        const unsigned long long b1 = __shfl_xor_sync(0xffffffffu, mx, q);
         mn = a1 < mn ? a1 : mn;
         mx = b1 > mx ? b1 : mx;
       }
@@ -812,9 +985,9 @@ __global__ void __launch_bounds__(kLocalThreads, 4) k_local(LocalArgs a) {
         }
         uint32_t incl = sum;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
+        for (int q = 1; q < 32; q <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, incl, q);
+          if (lane >= q) incl += y;
         }
         uint32_t run = incl - sum;
 #pragma unroll
@@ -837,9 +1010,9 @@ __global__ void __launch_bounds__(kLocalThreads, 4) k_local(LocalArgs a) {
         const uint32_t nc = __popc(cutm);
         uint32_t ci = nc;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, ci, o);
-          if (lane >= o) ci += y;
+        for (int q = 1; q < 32; q <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, ci, q);
+          if (lane >= q) ci += y;
         }
         uint32_t wpos = ci - nc;
 #pragma unroll
@@ -872,28 +1045,26 @@ __global__ void __launch_bounds__(kLocalThreads, 4) k_local(LocalArgs a) {
         }
       }
       __syncthreads();
-      // windows, one warp each: keys of the window w lie in
+      // windows, one warp each: keys of window w lie in
       // [top | g0 << sh, top | g1 << sh) for its first and end digits g0, g1
       const uint32_t nwin = s_nwin;
       const unsigned long long top = sh + 8 >= 64 ? 0ull : (kmin >> (sh + 8)) << (sh + 8);
       const uint32_t gend = (uint32_t)((kmax >> sh) & 255ull) + 1u;
-      const int wide_mode = use_idx ? 3 : 1;
       for (uint32_t wi = warp; wi < nwin; wi += kLocalWarps) {
         const int w0 = (int)s_win[wi], c = (int)s_win[wi + 1] - w0;
         if (c < 2) continue;
         const uint32_t g0 = s_wdg[wi], g1 = wi + 1 < nwin ? s_wdg[wi + 1] : gend;
         const unsigned long long base = top | ((unsigned long long)g0 << sh);
-        const bool narrow = ((unsigned long long)(g1 - g0) << sh) <= (1ull << 32);
-        const int mode = narrow ? (use_idx ? 2 : 0) : wide_mode;
+        const int mode = window_mode((unsigned long long)(g1 - g0) << sh, use_idx);
         if (c > window_cap(mode)) continue;
         if (mode == 0) {
-          sort_window<0>(sk, si, w0, c, base);
+          smem_window<0>(sk, si, w0, c, base);
         } else if (mode == 1) {
-          sort_window<1>(sk, si, w0, c, base);
+          smem_window<1>(sk, si, w0, c, base);
         } else {
           if constexpr (PERM) {
-            if (mode == 2) sort_window<2>(sk, si, w0, c, base);
-            else sort_window<3>(sk, si, w0, c, base);
+            if (mode == 2) smem_window<2>(sk, si, w0, c, base);
+            else smem_window<3>(sk, si, w0, c, base);
           }
         }
       }
@@ -902,8 +1073,7 @@ __global__ void __launch_bounds__(kLocalThreads, 4) k_local(LocalArgs a) {
       for (uint32_t wi = 0; wi < nwin; ++wi) {
         const int w0 = (int)s_win[wi], c = (int)s_win[wi + 1] - w0;
         const uint32_t g0 = s_wdg[wi], g1 = wi + 1 < nwin ? s_wdg[wi + 1] : gend;
-        const bool narrow = ((unsigned long long)(g1 - g0) << sh) <= (1ull << 32);
-        const int mode = narrow ? (use_idx ? 2 : 0) : wide_mode;
+        const int mode = window_mode((unsigned long long)(g1 - g0) << sh, use_idx);
         if (c <= window_cap(mode)) continue;
         const int fl = cta_sort(sk + w0, use_idx ? si + w0 : nullptr, gk2 + w0,
                                 use_idx ? gi2 + w0 : nullptr, c, kbits, use_idx ? ibits : 0,
@@ -941,71 +1111,27 @@ __global__ void __launch_bounds__(kLocalThreads, 4) k_local(LocalArgs a) {
         a.outl_idx[j] = idx;
         if (PERM) a.perm[lo + j] = idx;
         if (a.q_slot)
-          for (uint32_t f = 0; f < d; ++f)
+          for (uint32_t f = 0; f < o.d; ++f)
             a.q_slot[(uint64_t)f * a.n + lo + j] = a.q_in[(uint64_t)f * a.n + idx];
       }
-      if (threadIdx.x == 0) a.seg_blocks[sg] = 0u;
       __syncthreads();
       continue;
     }
-    // segmentation: warp w owns positions [w*S, (w+1)*S), S a multiple of 32
-    const int S = (cnt + kLocalWarps * 32 - 1) / (kLocalWarps * 32) * 32;
-    const int wlo = min(cnt, warp * S), whi = min(cnt, wlo + S);
-    uint32_t nstart = 0u;
-    for (int j0 = wlo; j0 < whi; j0 += 32) {
-      const int j = j0 + lane;
-      bool start = false;
-      if (j < whi) start = j == 0 || (K[j] >> rel_bits) != (K[j - 1] >> rel_bits);
-      nstart += __popc(__ballot_sync(0xffffffffu, start));
-    }
-    if (lane == 0) s_wcnt[warp] = nstart;
-    __syncthreads();
-    uint32_t run = 0u, total = 0u;
-#pragma unroll
-    for (int w2 = 0; w2 < kLocalWarps; ++w2) {
-      const uint32_t v = s_wcnt[w2];
-      run += w2 < warp ? v : 0u;
-      total += v;
-    }
-    for (int j0 = wlo; j0 < whi; j0 += 32) {
-      const int j = j0 + lane;
-      const bool valid = j < whi;
+    // segmentation; the unit's first particle opens a block
+    for (int j0 = 0; j0 < cnt; j0 += kLocalThreads) {
+      const int j = j0 + threadIdx.x;
+      const bool valid = j < cnt;
       unsigned long long key = 0ull, prev = 0ull;
       bool start = false;
+      uint32_t ix = 0u;
       if (valid) {
         key = K[j];
         if (j > 0) prev = K[j - 1];
-        start = j == 0 || (key >> rel_bits) != (prev >> rel_bits);
+        start = j == 0 || (key >> o.rel_bits) != (prev >> o.rel_bits);
+        if (PERM) ix = I[j];
       }
-      const uint32_t bal = __ballot_sync(0xffffffffu, start);
-      unsigned long long v = 0ull;
-      if (valid) {
-        const uint64_t g = lo + (uint64_t)j;
-        const unsigned long long rel = key & rel_mask;
-        v = (start || (g & chunk_mask) == 0) ? rel : rel - (prev & rel_mask);
-        a.s_rel[g] = (uint32_t)v;
-        my_max = v > my_max ? v : my_max;
-        if (start) {
-          const uint64_t t = lo + run + __popc(bal & lt);
-          a.tmp_bid[t] = key >> rel_bits;
-          a.tmp_pos[t] = (uint32_t)j;
-        }
-        if (PERM) {
-          const uint32_t idx = I[j];
-          a.perm[g] = idx;
-          if (a.q_slot)
-            for (uint32_t f = 0; f < d; ++f)
-              a.q_slot[(uint64_t)f * a.n + g] = a.q_in[(uint64_t)f * a.n + idx];
-        }
-      }
-      // stream-2 histogram: escapes counted per warp, other values per lane
-      const bool esc = valid && v >= (unsigned long long)kEsc;
-      const uint32_t nesc = __popc(__ballot_sync(0xffffffffu, esc));
-      if (lane == 0 && nesc) atomicAdd(&s_hist[kEsc], nesc);
-      if (valid && !esc) atomicAdd(&s_hist[(uint32_t)v], 1u);
-      run += __popc(bal);
+      seg_emit<PERM>(o, valid, lo + (uint64_t)j, key, prev, start, ix, s_hist, my_max);
     }
-    if (threadIdx.x == 0) a.seg_blocks[sg] = total;
     __syncthreads();
   }
   // stream-2 histogram and max
@@ -1033,60 +1159,78 @@ void launch_local(const LocalArgs &a, int ctas, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// blocks: compact the per-segment block lists, delta code ids and counts
+// blocks: number the block starts (scan of the start flags over the nbk
+// non-outlier slots), then delta code ids and counts (Sec. "Block coding")
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_blocks_scan(const uint32_t *__restrict__ seg_blocks,
-                                                      const uint32_t *__restrict__ nsegp,
-                                                      unsigned long long *__restrict__ block_off,
-                                                      int *__restrict__ prev_nonempty,
-                                                      unsigned long long *__restrict__ mcount) {
+constexpr int kFlagThreads = 256;
+constexpr int kFlagPer = 16;  // slots per thread (one 16-byte load)
+constexpr int kFlagTile = kFlagThreads * kFlagPer;
+
+__device__ __forceinline__ uint32_t flag_count16(const uint8_t *flag, uint64_t g, uint64_t nbk,
+                                                 uint32_t &bits) {
+  // flags of slots g .. g+15 (g a multiple of 16) as a bit mask
+  bits = 0u;
+  if (g >= nbk) return 0u;
+  const uint4 w = *reinterpret_cast<const uint4 *>(flag + g);
+  const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) bits |= ((ws[q] >> (8 * b)) & 1u) << (4 * q + b);
+  const uint64_t left = nbk - g;
+  if (left < 16) bits &= (1u << left) - 1u;
+  return __popc(bits);
+}
+
+__global__ void __launch_bounds__(kFlagThreads) k_flag_count(
+    const uint8_t *__restrict__ flag, const unsigned long long *__restrict__ nbkp,
+    unsigned long long *__restrict__ tile_cnt) {
   __shared__ unsigned long long s_warp[32];
-  __shared__ int s_last[1024];
-  const uint32_t nseg = *nsegp;
-  const uint32_t per = (nseg + 1023) / 1024;
-  const uint32_t lo = threadIdx.x * per, hi = min(nseg, lo + per);
-  unsigned long long sum = 0;
-  int last = -1;
-  for (uint32_t i = lo; i < hi; ++i) {
-    sum += seg_blocks[i];
-    if (seg_blocks[i]) last = (int)i;
+  const uint64_t nbk = *nbkp;
+  const uint64_t g = (uint64_t)blockIdx.x * kFlagTile + (uint64_t)threadIdx.x * kFlagPer;
+  uint32_t bits;
+  const uint32_t c = flag_count16(flag, g, nbk, bits);
+  unsigned long long tot;
+  block_exscan<kFlagThreads>(c, s_warp, tot);
+  if (threadIdx.x == 0) tile_cnt[blockIdx.x] = tot;
+}
+
+// bpos[B] = slot of block B's first particle, bidv[B] = its block id;
+// bpos[M] = nbk; mcount = M
+__global__ void __launch_bounds__(kFlagThreads) k_flag_apply(
+    const uint8_t *__restrict__ flag, const unsigned long long *__restrict__ nbkp,
+    const unsigned long long *__restrict__ tile_base, uint32_t ntiles,
+    const unsigned long long *__restrict__ tmp_bid, uint32_t *__restrict__ bpos,
+    unsigned long long *__restrict__ bidv, unsigned long long *__restrict__ mcount) {
+  __shared__ unsigned long long s_warp[32];
+  const uint64_t nbk = *nbkp;
+  const uint64_t g = (uint64_t)blockIdx.x * kFlagTile + (uint64_t)threadIdx.x * kFlagPer;
+  uint32_t bits;
+  const uint32_t c = flag_count16(flag, g, nbk, bits);
+  unsigned long long tot;
+  unsigned long long B = tile_base[blockIdx.x] + block_exscan<kFlagThreads>(c, s_warp, tot);
+  while (bits) {
+    const int b = __ffs(bits) - 1;
+    bits &= bits - 1u;
+    bpos[B] = (uint32_t)(g + b);
+    bidv[B] = tmp_bid[g + b];
+    ++B;
   }
-  s_last[threadIdx.x] = last;
-  unsigned long long total;
-  unsigned long long run = block_exscan<1024>(sum, s_warp, total);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int m = -1;
-    for (int t = 0; t < 1024; ++t) {
-      int v = s_last[t];
-      s_last[t] = m;
-      if (v > m) m = v;
-    }
-    *mcount = total;
-  }
-  __syncthreads();
-  int pl = s_last[threadIdx.x];
-  for (uint32_t i = lo; i < hi; ++i) {
-    block_off[i] = run;
-    run += seg_blocks[i];
-    prev_nonempty[i] = pl;
-    if (seg_blocks[i]) pl = (int)i;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long M = tile_base[ntiles];
+    bpos[M] = (uint32_t)nbk;
+    *mcount = M;
   }
 }
 
-__global__ void __launch_bounds__(512) k_blocks(const Plan *__restrict__ plan,
-                                                const uint32_t *__restrict__ nsegp,
-                                                const uint32_t *__restrict__ seg_lo,
-                                                const uint32_t *__restrict__ seg_cnt,
-                                                const uint32_t *__restrict__ sblocks,
-                                                const unsigned long long *__restrict__ tmp_bid,
-                                                const uint32_t *__restrict__ tmp_pos,
-                                                const unsigned long long *__restrict__ block_off,
-                                                const int *__restrict__ prev_nonempty,
-                                                unsigned long long *__restrict__ s_id,
-                                                unsigned long long *__restrict__ s_cnt,
-                                                uint32_t *__restrict__ hist,
-                                                unsigned long long *__restrict__ maxv) {
+__global__ void __launch_bounds__(512) k_blocks_map(const Plan *__restrict__ plan,
+                                                    const uint32_t *__restrict__ bpos,
+                                                    const unsigned long long *__restrict__ bidv,
+                                                    const unsigned long long *__restrict__ mcount,
+                                                    unsigned long long *__restrict__ s_id,
+                                                    unsigned long long *__restrict__ s_cnt,
+                                                    uint32_t *__restrict__ hist,
+                                                    unsigned long long *__restrict__ maxv) {
   __shared__ uint32_t h0[kAlpha], h1[kAlpha];
   __shared__ unsigned long long m0, m1;
   for (int i = threadIdx.x; i < kAlpha; i += blockDim.x) {
@@ -1099,43 +1243,42 @@ __global__ void __launch_bounds__(512) k_blocks(const Plan *__restrict__ plan,
   }
   __syncthreads();
   if (plan->status != OK) return;
-  const uint32_t nseg = *nsegp;
+  const int lane = threadIdx.x & 31;
+  const uint64_t M = *mcount;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   unsigned long long x0 = 0ull, x1 = 0ull;
-  for (uint32_t b = blockIdx.x; b < nseg; b += gridDim.x) {
-    const uint32_t mb = sblocks[b];
-    if (mb == 0) continue;
-    const uint64_t lo = seg_lo[b];
-    const uint32_t cntb = seg_cnt[b];
-    for (uint32_t t = threadIdx.x; t < mb; t += blockDim.x) {
-      const unsigned long long bid = tmp_bid[lo + t];
-      const uint32_t pos = tmp_pos[lo + t];
-      const uint32_t end = (t + 1 < mb) ? tmp_pos[lo + t + 1] : cntb;
-      const long long c = (long long)(end - pos);
+  // trip count uniform across the warp (ballots below)
+  const uint64_t iters = (M + stride - 1) / stride;
+  for (uint64_t it = 0; it < iters; ++it) {
+    const uint64_t B = it * stride + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = B < M;
+    unsigned long long v0 = 0ull, v1 = 0ull;
+    if (valid) {
+      const uint32_t p = bpos[B], pn = bpos[B + 1];
+      const long long c = (long long)(pn - p);
       unsigned long long pbid = 0ull;
       long long pc = 0;
-      if (t > 0) {
-        pbid = tmp_bid[lo + t - 1];
-        pc = (long long)(pos - tmp_pos[lo + t - 1]);
-      } else {
-        const int pb = prev_nonempty[b];
-        if (pb >= 0) {
-          const uint32_t pm = sblocks[pb];
-          const uint64_t plo = seg_lo[pb];
-          const uint32_t pcnt = seg_cnt[pb];
-          pbid = tmp_bid[plo + pm - 1];
-          pc = (long long)(pcnt - tmp_pos[plo + pm - 1]);
-        }
+      if (B > 0) {
+        pbid = bidv[B - 1];
+        pc = (long long)(p - bpos[B - 1]);
       }
-      const uint64_t g = block_off[b] + t;
-      const unsigned long long v0 = bid - pbid;
-      const unsigned long long v1 = zigzag(c - pc);
-      s_id[g] = v0;
-      s_cnt[g] = v1;
-      atomicAdd(&h0[v0 < (unsigned long long)kEsc ? (uint32_t)v0 : (uint32_t)kEsc], 1u);
-      atomicAdd(&h1[v1 < (unsigned long long)kEsc ? (uint32_t)v1 : (uint32_t)kEsc], 1u);
+      v0 = bidv[B] - pbid;
+      v1 = zigzag(c - pc);
+      s_id[B] = v0;
+      s_cnt[B] = v1;
       x0 = v0 > x0 ? v0 : x0;
       x1 = v1 > x1 ? v1 : x1;
     }
+    const bool e0 = valid && v0 >= (unsigned long long)kEsc;
+    const bool e1 = valid && v1 >= (unsigned long long)kEsc;
+    const uint32_t n0 = __popc(__ballot_sync(0xffffffffu, e0));
+    const uint32_t n1 = __popc(__ballot_sync(0xffffffffu, e1));
+    if (lane == 0) {
+      if (n0) atomicAdd(&h0[kEsc], n0);
+      if (n1) atomicAdd(&h1[kEsc], n1);
+    }
+    if (valid && !e0) atomicAdd(&h0[(uint32_t)v0], 1u);
+    if (valid && !e1) atomicAdd(&h1[(uint32_t)v1], 1u);
   }
   atomicMax(&m0, x0);
   atomicMax(&m1, x1);
@@ -1150,17 +1293,24 @@ __global__ void __launch_bounds__(512) k_blocks(const Plan *__restrict__ plan,
   }
 }
 
-void launch_blocks(const Plan *plan, const uint32_t *nseg, const uint32_t *seg_lo,
-                   const uint32_t *seg_cnt, const uint32_t *seg_blocks,
-                   const unsigned long long *tmp_bid, const uint32_t *tmp_pos,
-                   unsigned long long *block_off, int *prev_nonempty, unsigned long long *s_id,
-                   unsigned long long *s_cnt, uint32_t *hist, unsigned long long *maxv,
-                   unsigned long long *mcount, int ctas, cudaStream_t s) {
+uint64_t flag_tiles(uint64_t n) { return (n + kFlagTile - 1) / kFlagTile + 1; }
+
+void launch_blocks(const Plan *plan, const uint8_t *bflag, const unsigned long long *nbk,
+                   uint64_t n, const unsigned long long *tmp_bid, unsigned long long *tile_cnt,
+                   unsigned long long *tile_base, uint32_t *bpos, unsigned long long *bidv,
+                   unsigned long long *s_id, unsigned long long *s_cnt, uint32_t *hist,
+                   unsigned long long *maxv, unsigned long long *mcount, int sms,
+                   cudaStream_t s) {
+  const uint32_t ntiles = (uint32_t)((n + kFlagTile - 1) / kFlagTile);
+  const uint32_t nt = ntiles ? ntiles : 1u;
   note_launch();
-  k_blocks_scan<<<1, 1024, 0, s>>>(seg_blocks, nseg, block_off, prev_nonempty, mcount);
+  k_flag_count<<<nt, kFlagThreads, 0, s>>>(bflag, nbk, tile_cnt);
+  launch_scan_small(tile_cnt, nt, tile_base, s);
   note_launch();
-  k_blocks<<<ctas, 512, 0, s>>>(plan, nseg, seg_lo, seg_cnt, seg_blocks, tmp_bid, tmp_pos,
-                                block_off, prev_nonempty, s_id, s_cnt, hist, maxv);
+  k_flag_apply<<<nt, kFlagThreads, 0, s>>>(bflag, nbk, tile_base, nt, tmp_bid, bpos, bidv,
+                                            mcount);
+  note_launch();
+  k_blocks_map<<<2 * sms, 512, 0, s>>>(plan, bpos, bidv, mcount, s_id, s_cnt, hist, maxv);
 }
 
 // value counts: ids and counts have M values, relative locations n - K

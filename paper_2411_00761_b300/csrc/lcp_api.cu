@@ -44,9 +44,9 @@ T *P(DevBuf &b) {
 }
 
 struct Workspace {
-  DevBuf big_list, big_of, nbig, sub_cnt, sub_nz, seg_base, seg_lo, seg_cnt, seg_meta, nseg;
+  DevBuf big_list, big_of, nbig, sub_cnt, seg_lo, seg_cnt, seg_meta, nseg, bflag, ftile, fbase;
   DevBuf mm, plan, keys, keys2, idx2, idx_alt, tile_hist, btot, bstart, s_rel, tmp_bid, tmp_pos,
-      bblocks, boff, prevne, s_id, s_cnt, hist, maxv, nvals, mcount, kcount, desc, codes, lens,
+      s_id, s_cnt, hist, maxv, nvals, mcount, kcount, desc, codes, lens,
       tables, chunk_bits, chunk_off, outl_idx, summary, q_in, q_slot, perm, sym, patch_s,
       patch_i, patch_x, patch_s2, patch_i2, patch_so, patch_io, dec_fields, hufft, err,
       scan_tmp, scan_base, bid, counts, starts, cand, tq, fplan, fstatus;
@@ -233,23 +233,22 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   TRY(grow(w.bstart, (size_t)(nb1 + 1) * 8));
   TRY(grow(w.s_rel, nn * 4));
   TRY(grow(w.tmp_bid, nn * 8));
-  TRY(grow(w.tmp_pos, nn * 4));
-  // segments: level-1 buckets, split ones replaced by their sub-buckets
-  const uint64_t nbig_max = n / kUnitCap + 1;
-  const uint64_t segcap = nb1 + nbig_max * 1024;
+  TRY(grow(w.tmp_pos, (nn + 1) * 4));  // block start slots
+  TRY(grow(w.bflag, (nn + 4096) & ~(uint64_t)4095));
+  TRY(grow(w.ftile, flag_tiles(nn) * 8));
+  TRY(grow(w.fbase, (flag_tiles(nn) + 1) * 8));
+  // split buckets (each above 256 keys) and the units: unsplit buckets
+  // merged, the outlier bucket, runs of sub-buckets too large for a warp
+  const uint64_t nbig_max = n / 256 + 1;
+  const uint64_t segcap = nb1 + n / 256 + 2;
   TRY(grow(w.big_list, (size_t)nb1 * 4));
   TRY(grow(w.big_of, (size_t)nb1 * 4));
   TRY(grow(w.nbig, 16));
-  TRY(grow(w.sub_cnt, (size_t)nbig_max * 1024 * 4));
-  TRY(grow(w.sub_nz, (size_t)nb1 * 4));    // units per split bucket
-  TRY(grow(w.seg_base, (size_t)nb1 * 4));  // first unit of each split bucket
+  TRY(grow(w.sub_cnt, (size_t)std::min<uint64_t>(nbig_max, nb1) * 1024 * 4));
   TRY(grow(w.seg_lo, (size_t)segcap * 4));
   TRY(grow(w.seg_cnt, (size_t)segcap * 4));
   TRY(grow(w.seg_meta, (size_t)segcap * 4));
   TRY(grow(w.nseg, 16));
-  TRY(grow(w.bblocks, (size_t)segcap * 4));
-  TRY(grow(w.boff, (size_t)segcap * 8));
-  TRY(grow(w.prevne, (size_t)segcap * 4));
   TRY(grow(w.s_id, nn * 8));
   TRY(grow(w.s_cnt, nn * 8));
   TRY(grow(w.outl_idx, nn * 4));
@@ -274,32 +273,55 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
                  want_perm ? P<uint32_t>(w.idx2) : nullptr, s);
   prof_end(c, s);
   CK(cudaGetLastError());
-  // 6. level-2 split of oversized buckets, per-segment sort + segmentation
+  // 6. level-2 split of the large buckets, sorting + segmentation
   prof_begin(c, "s.split", s);
   launch_segments(P<Plan>(w.plan), nb1, P<unsigned long long>(w.bstart),
                   P<unsigned long long>(w.keys2), want_perm ? P<uint32_t>(w.idx2) : nullptr,
                   P<unsigned long long>(w.keys), want_perm ? P<uint32_t>(w.idx_alt) : nullptr,
                   P<uint32_t>(w.big_list), P<int>(w.big_of), P<uint32_t>(w.nbig),
-                  P<uint32_t>(w.sub_cnt), P<uint32_t>(w.sub_nz), P<uint32_t>(w.seg_base),
-                  P<uint32_t>(w.seg_lo), P<uint32_t>(w.seg_cnt), P<uint32_t>(w.seg_meta),
-                  P<uint32_t>(w.nseg), n, sms, s);
+                  P<uint32_t>(w.sub_cnt), P<uint32_t>(w.seg_lo), P<uint32_t>(w.seg_cnt),
+                  P<uint32_t>(w.seg_meta), P<uint32_t>(w.nseg), sms, s);
   prof_end(c, s);
   CK(cudaMemsetAsync(w.hist.p, 0, 3ull * kAlpha * 4, s));
   CK(cudaMemsetAsync(w.maxv.p, 0, 4 * 8, s));
+  SubsortArgs sa;
+  sa.plan = P<Plan>(w.plan);
+  sa.big_list = P<uint32_t>(w.big_list);
+  sa.nbig = P<uint32_t>(w.nbig);
+  sa.bstart = P<unsigned long long>(w.bstart);
+  sa.sub_off = P<uint32_t>(w.sub_cnt);
+  sa.keys_alt = P<unsigned long long>(w.keys);
+  sa.idx_alt = want_perm ? P<uint32_t>(w.idx_alt) : nullptr;
+  sa.nunit = P<uint32_t>(w.nseg);
+  sa.u_lo = P<uint32_t>(w.seg_lo);
+  sa.u_cnt = P<uint32_t>(w.seg_cnt);
+  sa.u_meta = P<uint32_t>(w.seg_meta);
+  sa.s_rel = P<uint32_t>(w.s_rel);
+  sa.bflag = P<uint8_t>(w.bflag);
+  sa.tmp_bid = P<unsigned long long>(w.tmp_bid);
+  sa.hist = P<uint32_t>(w.hist);
+  sa.maxv = P<unsigned long long>(w.maxv);
+  sa.perm = want_perm ? perm_out : nullptr;
+  sa.q_in = want_q ? P<int32_t>(w.q_in) : nullptr;
+  sa.q_slot = want_q ? q_slot_out : nullptr;
+  sa.log2_chunk = kLog2Chunk;
+  sa.n = n;
+  prof_begin(c, "s.subsort", s);
+  launch_subsort(sa, sms, s);
+  prof_end(c, s);
   LocalArgs la;
   la.plan = P<Plan>(w.plan);
   la.nseg = P<uint32_t>(w.nseg);
   la.seg_lo = P<uint32_t>(w.seg_lo);
   la.seg_cnt = P<uint32_t>(w.seg_cnt);
   la.seg_meta = P<uint32_t>(w.seg_meta);
-  la.seg_blocks = P<uint32_t>(w.bblocks);
   la.keys = P<unsigned long long>(w.keys2);
   la.idx = want_perm ? P<uint32_t>(w.idx2) : nullptr;
   la.keys_alt = P<unsigned long long>(w.keys);  // free after the scatter
   la.idx_alt = want_perm ? P<uint32_t>(w.idx_alt) : nullptr;
   la.s_rel = P<uint32_t>(w.s_rel);
+  la.bflag = P<uint8_t>(w.bflag);
   la.tmp_bid = P<unsigned long long>(w.tmp_bid);
-  la.tmp_pos = P<uint32_t>(w.tmp_pos);
   la.hist = P<uint32_t>(w.hist);
   la.maxv = P<unsigned long long>(w.maxv);
   la.perm = want_perm ? perm_out : nullptr;
@@ -312,14 +334,14 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   launch_local(la, 4 * sms, s);
   prof_end(c, s);
   CK(cudaGetLastError());
-  // 7. blocks: ids and counts
+  // 7. blocks: ids and counts (the level-1 keys are free: block ids there)
   prof_begin(c, "s.blocks", s);
-  launch_blocks(P<Plan>(w.plan), P<uint32_t>(w.nseg), P<uint32_t>(w.seg_lo),
-                P<uint32_t>(w.seg_cnt), P<uint32_t>(w.bblocks), P<unsigned long long>(w.tmp_bid),
-                P<uint32_t>(w.tmp_pos), P<unsigned long long>(w.boff), P<int>(w.prevne),
-                P<unsigned long long>(w.s_id), P<unsigned long long>(w.s_cnt),
-                P<uint32_t>(w.hist), P<unsigned long long>(w.maxv),
-                P<unsigned long long>(w.mcount), 2 * sms, s);
+  launch_blocks(P<Plan>(w.plan), P<uint8_t>(w.bflag), P<unsigned long long>(w.bstart) + nb, n,
+                P<unsigned long long>(w.tmp_bid), P<unsigned long long>(w.ftile),
+                P<unsigned long long>(w.fbase), P<uint32_t>(w.tmp_pos),
+                P<unsigned long long>(w.keys2), P<unsigned long long>(w.s_id),
+                P<unsigned long long>(w.s_cnt), P<uint32_t>(w.hist),
+                P<unsigned long long>(w.maxv), P<unsigned long long>(w.mcount), sms, s);
   launch_counts_s(P<unsigned long long>(w.bstart), nb, n, P<unsigned long long>(w.mcount),
                   P<unsigned long long>(w.nvals), P<unsigned long long>(w.kcount), s);
   prof_end(c, s);

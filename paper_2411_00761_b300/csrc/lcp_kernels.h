@@ -59,25 +59,28 @@ void launch_bucket_offsets(uint32_t *tile_hist, int tiles, uint32_t nb1,
 void launch_scatter(const unsigned long long *keys, uint64_t n, const Plan *plan, uint32_t nb1,
                     int tiles, const uint32_t *tile_off, unsigned long long *keys_out,
                     uint32_t *idx_out, cudaStream_t s);
-// level-2 split of oversized buckets and the ordered segment list
+// level-2 split of the buckets above the split threshold (sub_off: per
+// split bucket, the offset of each sub-bucket) and the unit list of the
+// unsplit buckets and the outlier bucket
 void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *bstart,
                      unsigned long long *keys, uint32_t *idx, unsigned long long *keys_alt,
                      uint32_t *idx_alt, uint32_t *big_list, int *big_of, uint32_t *nbig,
-                     uint32_t *sub_cnt, uint32_t *big_units, uint32_t *big_base, uint32_t *u_lo,
-                     uint32_t *u_cnt, uint32_t *u_meta, uint32_t *nunit, uint64_t n, int sms,
-                     cudaStream_t s);
+                     uint32_t *sub_off, uint32_t *u_lo, uint32_t *u_cnt, uint32_t *u_meta,
+                     uint32_t *nunit, int sms, cudaStream_t s);
+// sorting and segmentation outputs, per sorted slot g: s_rel[g] (relative
+// location deltas), bflag[g] (1 where a block starts), tmp_bid[g] (the block
+// id, at block starts only), perm[g] and q_slot (perm mode)
 struct LocalArgs {
   const Plan *plan;
-  const uint32_t *nseg;                    // segments (device count)
+  const uint32_t *nseg;                    // units (device count)
   const uint32_t *seg_lo, *seg_cnt, *seg_meta;
-  uint32_t *seg_blocks;                    // [segments] blocks per segment
   unsigned long long *keys;                // partitioned keys (level 1)
   uint32_t *idx;                           // partitioned input indices (perm mode)
   unsigned long long *keys_alt;            // level-2 split keys / scratch
   uint32_t *idx_alt;
   uint32_t *s_rel;                         // [n]
-  unsigned long long *tmp_bid;             // [n] block ids per bucket region
-  uint32_t *tmp_pos;                       // [n] block start (segment-local)
+  uint8_t *bflag;                          // [n]
+  unsigned long long *tmp_bid;             // [n]
   uint32_t *hist;                          // [3][4096]
   unsigned long long *maxv;                // [3]
   uint32_t *perm;                          // [n] slot -> input index (perm mode) or null
@@ -88,12 +91,38 @@ struct LocalArgs {
   uint64_t n;
 };
 void launch_local(const LocalArgs &a, int ctas, cudaStream_t s);
-void launch_blocks(const Plan *plan, const uint32_t *nseg, const uint32_t *seg_lo,
-                   const uint32_t *seg_cnt, const uint32_t *seg_blocks,
-                   const unsigned long long *tmp_bid, const uint32_t *tmp_pos,
-                   unsigned long long *block_off, int *prev_nonempty, unsigned long long *s_id,
-                   unsigned long long *s_cnt, uint32_t *hist, unsigned long long *maxv,
-                   unsigned long long *mcount, int ctas, cudaStream_t s);
+// runs of sub-buckets of the split buckets, sorted and segmented by warps;
+// runs too large for a warp are appended to the unit list
+struct SubsortArgs {
+  const Plan *plan;
+  const uint32_t *big_list, *nbig;
+  const unsigned long long *bstart;
+  const uint32_t *sub_off;
+  const unsigned long long *keys_alt;      // split keys
+  const uint32_t *idx_alt;                 // split input indices (perm mode)
+  uint32_t *nunit, *u_lo, *u_cnt, *u_meta;
+  uint32_t *s_rel;
+  uint8_t *bflag;
+  unsigned long long *tmp_bid;
+  uint32_t *hist;
+  unsigned long long *maxv;
+  uint32_t *perm;
+  const int32_t *q_in;
+  int32_t *q_slot;
+  uint32_t log2_chunk;
+  uint64_t n;
+};
+void launch_subsort(const SubsortArgs &a, int sms, cudaStream_t s);
+// block numbering from the start flags of the nbk = *nbk non-outlier slots
+// and the delta-coded ids and counts with their histograms; tile_cnt and
+// tile_base hold flag_tiles(n) values, bpos n + 1, bidv n
+uint64_t flag_tiles(uint64_t n);
+void launch_blocks(const Plan *plan, const uint8_t *bflag, const unsigned long long *nbk,
+                   uint64_t n, const unsigned long long *tmp_bid, unsigned long long *tile_cnt,
+                   unsigned long long *tile_base, uint32_t *bpos, unsigned long long *bidv,
+                   unsigned long long *s_id, unsigned long long *s_cnt, uint32_t *hist,
+                   unsigned long long *maxv, unsigned long long *mcount, int sms,
+                   cudaStream_t s);
 // value counts of the three LCP-S streams and K
 void launch_counts_s(const unsigned long long *bucket_start, uint32_t nb, uint64_t n,
                      const unsigned long long *mcount, unsigned long long *nvals,
