@@ -38,24 +38,145 @@ __device__ void bitonic_sort_u64(unsigned long long *a, int n /*power of two*/) 
   }
 }
 
+// Code lengths of one stream for one number of halvings k (blockIdx.x):
+// weights ceil(count / 2^k) -- k halvings (w + 1) >> 1 -- then the
+// two-queue construction and the leaf depths.  All k in [0, kHalvings) are
+// built at once; the codebook takes the smallest k whose longest code fits
+// kLmax bits, which is where halving one step at a time stops (k = 32 leaves
+// all weights equal: depth <= 12).
+constexpr int kHalvings = 33;
+
+__global__ void __launch_bounds__(kCbThreads) k_cb_build(const uint32_t *__restrict__ hist,
+                                                         const unsigned long long *__restrict__ nv,
+                                                         uint8_t *__restrict__ lens_k,
+                                                         uint32_t *__restrict__ maxlen_k) {
+  const int k = blockIdx.x, s = blockIdx.y;
+  extern __shared__ __align__(16) unsigned char cb_smem[];
+  unsigned long long *sk = reinterpret_cast<unsigned long long *>(cb_smem);  // weight<<12|sym
+  uint32_t *nodew = reinterpret_cast<uint32_t *>(sk + kAlpha);              // leaves, internal
+  uint32_t *dist = nodew + 2 * kAlpha;
+  uint16_t *parent = reinterpret_cast<uint16_t *>(dist + 2 * kAlpha);
+  __shared__ int s_U, s_maxlen;
+  uint8_t *lens = lens_k + ((uint64_t)s * kHalvings + k) * kAlpha;
+  const unsigned long long n = nv[s];
+  const uint32_t *h = hist + (uint64_t)s * kAlpha;
+  if (threadIdx.x == 0) {
+    s_U = 0;
+    s_maxlen = 0;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kAlpha; i += blockDim.x) {
+    const unsigned long long c = n ? h[i] : 0u;
+    const unsigned long long wk = (c + (1ull << k) - 1ull) >> k;
+    sk[i] = c ? ((wk << 12) | (unsigned long long)i) : ~0ull;
+    if (c) atomicAdd(&s_U, 1);
+  }
+  __syncthreads();
+  const int U = s_U;
+  if (U <= 1) {
+    for (int i = threadIdx.x; i < kAlpha; i += blockDim.x) lens[i] = sk[i] != ~0ull ? 1 : 0;
+    if (threadIdx.x == 0) maxlen_k[s * kHalvings + k] = (uint32_t)U;
+    return;
+  }
+  bitonic_sort_u64(sk, kAlpha);
+  for (int i = threadIdx.x; i < U; i += blockDim.x) nodew[i] = (uint32_t)(sk[i] >> 12);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // leaves nodew[0..U) ascending; internal node j (id U + j) has weight
+    // nodew[U + j], created in non-decreasing order.  The heads of both
+    // queues and the next entry of each are kept in registers.
+    const uint32_t *lw = nodew;
+    uint32_t *iw = nodew + U;
+    int nl = 0, ni = 0;
+    uint32_t L0 = lw[0], L1 = lw[1];
+    uint32_t I0 = 0u, I1 = 0u;
+    for (int nn = 0; nn < U - 1; ++nn) {
+      uint32_t sum = 0u;
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        int id;
+        if (nl < U && (ni == nn || L0 <= I0)) {
+          sum += L0;
+          id = nl++;
+          L0 = L1;
+          L1 = nl + 1 < U ? lw[nl + 1] : 0u;
+        } else {
+          sum += I0;
+          id = U + ni++;
+          I0 = I1;
+          I1 = ni + 1 < nn ? iw[ni + 1] : 0u;
+        }
+        parent[id] = (uint16_t)(U + nn);
+      }
+      iw[nn] = sum;
+      if (ni == nn) I0 = sum;
+      else if (ni + 1 == nn) I1 = sum;
+    }
+    parent[2 * U - 2] = (uint16_t)(2 * U - 2);
+  }
+  __syncthreads();
+  // depths by pointer jumping: distance to the root
+  constexpr int kPer = (2 * kAlpha + kCbThreads - 1) / kCbThreads;
+  const int nodes = 2 * U - 1;
+  uint32_t anc[kPer];
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int i = threadIdx.x + q * kCbThreads;
+    if (i < nodes) {
+      anc[q] = parent[i];
+      dist[i] = (i == nodes - 1) ? 0u : 1u;
+    }
+  }
+  __syncthreads();
+  for (int round = 0; round < 14; ++round) {
+    uint32_t nd[kPer], na[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = threadIdx.x + q * kCbThreads;
+      if (i < nodes) {
+        nd[q] = dist[i] + dist[anc[q]];
+        na[q] = parent[anc[q]];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = threadIdx.x + q * kCbThreads;
+      if (i < nodes) {
+        dist[i] = nd[q];
+        anc[q] = na[q];
+        parent[i] = (uint16_t)na[q];
+      }
+    }
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < kAlpha; i += blockDim.x) lens[i] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < U; i += blockDim.x) {
+    const uint32_t sym = (uint32_t)(sk[i] & 4095ull);
+    const uint32_t L = dist[i];
+    lens[sym] = (uint8_t)(L > 255 ? 255 : L);
+    atomicMax(&s_maxlen, (int)L);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) maxlen_k[s * kHalvings + k] = (uint32_t)s_maxlen;
+}
+
 __global__ void __launch_bounds__(kCbThreads) k_codebook(const uint32_t *__restrict__ hist,
                                                          const unsigned long long *__restrict__ maxv,
                                                          const unsigned long long *__restrict__ nv,
                                                          uint32_t log2_chunk,
+                                                         const uint8_t *__restrict__ lens_k,
+                                                         const uint32_t *__restrict__ maxlen_k,
                                                          StreamDesc *__restrict__ desc,
                                                          uint32_t *__restrict__ codes,
                                                          uint8_t *__restrict__ lens,
                                                          uint16_t *__restrict__ tables) {
   const int s = blockIdx.x;
-  extern __shared__ __align__(16) unsigned char cb_smem[];
-  unsigned long long *sk = reinterpret_cast<unsigned long long *>(cb_smem);  // weight<<12|sym
-  uint32_t *w = reinterpret_cast<uint32_t *>(sk + kAlpha);         // weights per symbol
-  uint32_t *nodew = w + kAlpha;                                    // leaves then internal
-  uint16_t *parent = reinterpret_cast<uint16_t *>(nodew + 2 * kAlpha);
-  uint8_t *depth8 = reinterpret_cast<uint8_t *>(parent + 2 * kAlpha);  // code lengths
+  __shared__ uint8_t depth8[kAlpha];
   __shared__ uint32_t s_lc[kLmax + 2];
   __shared__ uint32_t s_first[kLmax + 2], s_index[kLmax + 2];
-  __shared__ int s_U, s_maxlen;
+  __shared__ int s_U, s_k;
   __shared__ unsigned long long s_bits;
   const unsigned long long n = nv[s];
   const unsigned long long mx = n ? maxv[s] : 0ull;
@@ -76,107 +197,28 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const uint32_t *__restr
   if (threadIdx.x == 0) {
     s_U = 0;
     s_bits = 0ull;
-  }
-  for (int i = threadIdx.x; i < kAlpha; i += blockDim.x) {
-    w[i] = n ? h[i] : 0u;
-    depth8[i] = 0;
+    int kk = kHalvings - 1;
+    for (int q = 0; q < kHalvings; ++q)
+      if (maxlen_k[s * kHalvings + q] <= (uint32_t)kLmax) {
+        kk = q;
+        break;
+      }
+    s_k = kk;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kAlpha; i += blockDim.x)
-    if (w[i]) atomicAdd(&s_U, 1);
+  const uint8_t *lk = lens_k + ((uint64_t)s * kHalvings + s_k) * kAlpha;
+  for (int i = threadIdx.x; i < kAlpha; i += blockDim.x) {
+    const bool used = n && h[i];
+    depth8[i] = used ? lk[i] : 0;
+    if (used) atomicAdd(&s_U, 1);
+  }
   __syncthreads();
   const int U = s_U;
   if (U == 0) {
     if (threadIdx.x == 0) desc[s] = D;
     return;
   }
-  const uint32_t wesc = w[kEsc] ? wfix : 0u;
-  if (U == 1) {
-    for (int i = threadIdx.x; i < kAlpha; i += blockDim.x)
-      if (w[i]) depth8[i] = 1;
-  } else {
-    for (;;) {
-      for (int i = threadIdx.x; i < kAlpha; i += blockDim.x)
-        sk[i] = w[i] ? (((unsigned long long)w[i] << 12) | (unsigned long long)i) : ~0ull;
-      __syncthreads();
-      bitonic_sort_u64(sk, kAlpha);
-      for (int i = threadIdx.x; i < U; i += blockDim.x) nodew[i] = (uint32_t)(sk[i] >> 12);
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        // two-queue merge: leaves nodew[0..U), internal nodes nodew[U..2U-1)
-        int nl = 0, ni = U, nn = U;
-        while (nn < 2 * U - 1) {
-          int pick[2];
-#pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            if (nl < U && (ni == nn || nodew[nl] <= nodew[ni])) pick[t] = nl++;
-            else pick[t] = ni++;
-          }
-          nodew[nn] = nodew[pick[0]] + nodew[pick[1]];
-          parent[pick[0]] = (uint16_t)nn;
-          parent[pick[1]] = (uint16_t)nn;
-          ++nn;
-        }
-        parent[2 * U - 2] = (uint16_t)(2 * U - 2);
-      }
-      __syncthreads();
-      // depths by pointer jumping: dist to the root
-      constexpr int kPer = (2 * kAlpha + kCbThreads - 1) / kCbThreads;
-      uint32_t dist[kPer], anc[kPer];
-      const int nodes = 2 * U - 1;
-#pragma unroll
-      for (int k = 0; k < kPer; ++k) {
-        int i = threadIdx.x + k * kCbThreads;
-        if (i < nodes) {
-          anc[k] = parent[i];
-          dist[k] = (i == nodes - 1) ? 0u : 1u;
-        }
-      }
-      // store dist in nodew (weights are no longer needed)
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < kPer; ++k) {
-        int i = threadIdx.x + k * kCbThreads;
-        if (i < nodes) nodew[i] = dist[k];
-      }
-      __syncthreads();
-      for (int round = 0; round < 14; ++round) {
-        uint32_t nd[kPer], na[kPer];
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-          int i = threadIdx.x + k * kCbThreads;
-          if (i < nodes) {
-            nd[k] = nodew[i] + nodew[anc[k]];
-            na[k] = parent[anc[k]];
-          }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-          int i = threadIdx.x + k * kCbThreads;
-          if (i < nodes) {
-            nodew[i] = nd[k];
-            anc[k] = na[k];
-            parent[i] = (uint16_t)na[k];
-          }
-        }
-        __syncthreads();
-      }
-      if (threadIdx.x == 0) s_maxlen = 0;
-      __syncthreads();
-      for (int i = threadIdx.x; i < U; i += blockDim.x) {
-        uint32_t sym = (uint32_t)(sk[i] & 4095ull);
-        uint32_t L = nodew[i];
-        depth8[sym] = (uint8_t)(L > 255 ? 255 : L);
-        atomicMax(&s_maxlen, (int)L);
-      }
-      __syncthreads();
-      if (s_maxlen <= kLmax) break;
-      for (int i = threadIdx.x; i < kAlpha; i += blockDim.x)
-        if (w[i]) w[i] = (w[i] + 1u) >> 1;
-      __syncthreads();
-    }
-  }
+  const uint32_t wesc = (n && h[kEsc]) ? wfix : 0u;
   __syncthreads();
   // canonical codes: per length, symbols in increasing order
   if (threadIdx.x < kLmax + 2) s_lc[threadIdx.x] = 0u;
@@ -263,18 +305,26 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const uint32_t *__restr
   }
 }
 
+size_t codebook_work_size(int ns) { return (size_t)ns * kHalvings * (kAlpha + 4); }
+
 void launch_codebook(int ns, const uint32_t *hist, const unsigned long long *maxv,
-                     const unsigned long long *n_vals, uint32_t log2_chunk, StreamDesc *desc,
-                     uint32_t *codes, uint8_t *lens, uint16_t *tables, cudaStream_t s) {
-  const size_t smem = 8ull * kAlpha + 4ull * kAlpha + 8ull * kAlpha + 4ull * kAlpha + kAlpha;
+                     const unsigned long long *n_vals, uint32_t log2_chunk, uint8_t *work,
+                     StreamDesc *desc, uint32_t *codes, uint8_t *lens, uint16_t *tables,
+                     cudaStream_t s) {
+  // sort keys, node weights, distances, parents
+  const size_t smem = 8ull * kAlpha + 4ull * 2 * kAlpha + 4ull * 2 * kAlpha + 2ull * 2 * kAlpha;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_cb_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
+  uint8_t *lens_k = work;
+  uint32_t *maxlen_k = reinterpret_cast<uint32_t *>(work + (size_t)ns * kHalvings * kAlpha);
   note_launch();
-  k_codebook<<<ns, kCbThreads, smem, s>>>(hist, maxv, n_vals, log2_chunk, desc, codes, lens,
-                                          tables);
+  k_cb_build<<<dim3(kHalvings, ns), kCbThreads, smem, s>>>(hist, n_vals, lens_k, maxlen_k);
+  note_launch();
+  k_codebook<<<ns, kCbThreads, 0, s>>>(hist, maxv, n_vals, log2_chunk, lens_k, maxlen_k, desc,
+                                       codes, lens, tables);
 }
 
 // ---------------------------------------------------------------------------
@@ -393,44 +443,83 @@ void launch_layout(const LayoutArgs &a, int sms, bool size_only, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------------------
-// fixed-length payload: one thread per output word
+// fixed-length payload: a warp packs 32 consecutive values (32 * w bits, w
+// whole words) in shared memory and writes the w words out
 // ---------------------------------------------------------------------------
+constexpr int kFixWarps = 8;
+
 template <typename T>
-__global__ void k_encode_fixed(const T *__restrict__ vals, const StreamDesc *__restrict__ dp,
-                               uint8_t *__restrict__ out, const Summary *__restrict__ summary) {
+__global__ void __launch_bounds__(32 * kFixWarps) k_encode_fixed(
+    const T *__restrict__ vals, const StreamDesc *__restrict__ dp, uint8_t *__restrict__ out,
+    const Summary *__restrict__ summary) {
+  __shared__ uint32_t stage[kFixWarps][64];
   if (summary->status != OK) return;
   const StreamDesc D = *dp;
   if (D.coder != 0 || D.width == 0 || D.n == 0) return;
   const uint32_t w = D.width;
-  const unsigned long long words = words_of(D.payload_bits);
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  uint32_t *buf = stage[wl];
   uint32_t *pl = reinterpret_cast<uint32_t *>(out + D.offset + 32);
-  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < words;
-       i += (unsigned long long)gridDim.x * blockDim.x) {
-    const unsigned long long b0 = i * 32ull;
-    unsigned long long v0 = b0 / w, v1 = (b0 + 31ull) / w;
-    if (v1 >= D.n) v1 = D.n - 1;
-    uint32_t word = 0;
-    for (unsigned long long v = v0; v <= v1; ++v) {
-      unsigned long long val = (unsigned long long)vals[v];
-      long long sh = (long long)(b0 + 32ull) - (long long)(v * w + w);
-      word |= sh >= 0 ? (uint32_t)(val << sh) : (uint32_t)(val >> (-sh));
+  const unsigned long long words = words_of(D.payload_bits);
+  const unsigned long long groups = (D.n + 31) >> 5;
+  const unsigned long long nw = (unsigned long long)gridDim.x * kFixWarps;
+  for (unsigned long long g = (unsigned long long)blockIdx.x * kFixWarps + wl; g < groups; g += nw) {
+    buf[lane] = 0u;
+    buf[lane + 32] = 0u;
+    __syncwarp();
+    const unsigned long long i = g * 32ull + lane;
+    if (i < D.n) {
+      const unsigned long long v = (unsigned long long)vals[i];
+      // bits [lane*w, lane*w + w) of the group, MSB first
+      const uint32_t b0 = (uint32_t)lane * w;
+      uint32_t left = w, pos = b0;
+      while (left) {
+        const uint32_t wi = pos >> 5, off = pos & 31u;
+        const uint32_t take = min(left, 32u - off);
+        const unsigned long long part = (v >> (left - take)) & ((1ull << take) - 1ull);
+        atomicOr(&buf[wi], (uint32_t)part << (32u - off - take));
+        pos += take;
+        left -= take;
+      }
     }
-    pl[i] = word;
+    __syncwarp();
+    const unsigned long long wbase = g * (unsigned long long)w;
+    for (uint32_t k = lane; k < w; k += 32)
+      if (wbase + k < words) pl[wbase + k] = buf[k];
+    __syncwarp();
   }
 }
 
 // ---------------------------------------------------------------------------
 // Huffman payload: per-chunk bit counts, their scan (the chunk table), then
-// one warp per chunk assembling words in shared memory
+// one warp per chunk: rounds of 32 consecutive symbols (one per lane), bit
+// positions from a warp scan, codes assembled in a shared-memory stage
 // ---------------------------------------------------------------------------
+constexpr int kEncWarps = 8;
+constexpr int kStageWords = 2848;  // >= (1024 * (24 + 64)) / 32 + 2
+constexpr size_t kEncSmem = sizeof(uint32_t) * ((size_t)kEncWarps * kStageWords + kAlpha);
+
+// code table of the stream in shared memory: (code << 5) | length
+__device__ __forceinline__ void load_code_table(uint32_t *t, const uint32_t *codes,
+                                                const uint8_t *lens) {
+  for (int k = threadIdx.x; k < kAlpha; k += blockDim.x)
+    t[k] = (codes[k] << 5) | (uint32_t)lens[k];
+}
+
 template <typename T>
-__global__ void k_chunk_bits(const T *__restrict__ vals, const StreamDesc *__restrict__ dp,
-                             const uint8_t *__restrict__ lens, uint32_t log2_chunk,
-                             unsigned long long *__restrict__ chunk_bits,
-                             const Summary *__restrict__ summary) {
+__global__ void __launch_bounds__(256) k_chunk_bits(const T *__restrict__ vals,
+                                                    const StreamDesc *__restrict__ dp,
+                                                    const uint32_t *__restrict__ codes,
+                                                    const uint8_t *__restrict__ lens,
+                                                    uint32_t log2_chunk,
+                                                    unsigned long long *__restrict__ chunk_bits,
+                                                    const Summary *__restrict__ summary) {
+  __shared__ uint32_t tab[kAlpha];
   if (summary->status != OK) return;
   const StreamDesc D = *dp;
   if (D.coder != 1) return;
+  load_code_table(tab, codes, lens);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   const unsigned long long warp = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const unsigned long long nw = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
@@ -439,9 +528,9 @@ __global__ void k_chunk_bits(const T *__restrict__ vals, const StreamDesc *__res
     const unsigned long long lo = c * cs, hi = min(D.n, lo + cs);
     unsigned long long bits = 0;
     for (unsigned long long i = lo + lane; i < hi; i += 32) {
-      unsigned long long v = (unsigned long long)vals[i];
-      uint32_t sym = v < (unsigned long long)kEsc ? (uint32_t)v : (uint32_t)kEsc;
-      bits += lens[sym] + (sym == kEsc ? D.width : 0u);
+      const unsigned long long v = (unsigned long long)vals[i];
+      const uint32_t sym = v < (unsigned long long)kEsc ? (uint32_t)v : (uint32_t)kEsc;
+      bits += (tab[sym] & 31u) + (sym == kEsc ? D.width : 0u);
     }
     for (int o = 16; o; o >>= 1) bits += __shfl_down_sync(0xffffffffu, bits, o);
     if (lane == 0) chunk_bits[c] = bits;
@@ -460,21 +549,18 @@ __global__ void k_chunk_table(const unsigned long long *__restrict__ chunk_off,
     st_u64(ct + 8 * c, chunk_off[c]);
 }
 
-// writes nbits of v (MSB first) at bit position pos of a u32 word array
-__device__ __forceinline__ void put_bits_smem(uint32_t *buf, unsigned long long pos,
-                                              unsigned long long v, uint32_t nbits) {
+// ORs nbits (<= 64) of v, MSB first, at bit position pos of a u32 word array
+__device__ __forceinline__ void put_bits_smem(uint32_t *buf, uint32_t pos, unsigned long long v,
+                                              uint32_t nbits) {
   while (nbits) {
-    uint32_t wi = (uint32_t)(pos >> 5), off = (uint32_t)(pos & 31);
-    uint32_t take = min(nbits, 32u - off);
-    uint32_t part = (uint32_t)((v >> (nbits - take)) & ((take == 32) ? 0xffffffffull : ((1ull << take) - 1ull)));
-    atomicOr(&buf[wi], part << (32 - off - take));
+    const uint32_t wi = pos >> 5, off = pos & 31u;
+    const uint32_t take = min(nbits, 32u - off);
+    const uint32_t part = (uint32_t)((v >> (nbits - take)) & ((1ull << take) - 1ull));
+    atomicOr(&buf[wi], part << (32u - off - take));
     pos += take;
     nbits -= take;
   }
 }
-
-constexpr int kEncWarps = 4;
-constexpr int kStageWords = 2848;  // >= (1024 * (24 + 64)) / 32 + 2
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kEncWarps) k_huff_encode(
@@ -482,16 +568,19 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_huff_encode(
     const uint32_t *__restrict__ codes, const uint8_t *__restrict__ lens, uint32_t log2_chunk,
     const unsigned long long *__restrict__ chunk_off, uint8_t *__restrict__ out,
     const Summary *__restrict__ summary) {
-  __shared__ uint32_t stage[kEncWarps][kStageWords];
+  extern __shared__ uint32_t enc_smem[];  // per-warp stages, then the code table
+  uint32_t *tab = enc_smem + (size_t)kEncWarps * kStageWords;
   if (summary->status != OK) return;
   const StreamDesc D = *dp;
   if (D.coder != 1) return;
+  load_code_table(tab, codes, lens);
+  __syncthreads();
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const unsigned long long cs = 1ull << log2_chunk;
-  const uint32_t per = (uint32_t)(cs >> 5);  // symbols per lane
-  uint32_t *buf = stage[wl];
+  uint32_t *buf = enc_smem + (size_t)wl * kStageWords;
   uint32_t *pl = reinterpret_cast<uint32_t *>(out + D.offset + pad16(80ull + 2ull * D.used) +
                                               pad16(8ull * D.n_chunks));
+  const unsigned long long total_words = words_of(D.payload_bits);
   const unsigned long long warp = (unsigned long long)blockIdx.x * kEncWarps + wl;
   const unsigned long long nw = (unsigned long long)gridDim.x * kEncWarps;
   for (unsigned long long c = warp; c < D.n_chunks; c += nw) {
@@ -500,34 +589,32 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_huff_encode(
     const unsigned long long end = (c + 1 < D.n_chunks) ? chunk_off[c + 1] : D.payload_bits;
     const unsigned long long w0 = start >> 5, w1 = (end + 31) >> 5;  // [w0, w1)
     const uint32_t nwords = (uint32_t)(w1 - w0);
-    if (nwords > (uint32_t)kStageWords || w1 > words_of(D.payload_bits)) continue;  // cannot happen
+    if (nwords > (uint32_t)kStageWords || w1 > total_words) continue;  // cannot happen
     for (uint32_t i = lane; i < nwords; i += 32) buf[i] = 0u;
     __syncwarp();
-    // this lane's symbols and bit count
-    const unsigned long long slo = lo + (unsigned long long)lane * per;
-    const unsigned long long shi = min(hi, slo + per);
-    unsigned long long mybits = 0;
-    for (unsigned long long i = slo; i < shi; ++i) {
-      unsigned long long v = (unsigned long long)vals[i];
-      uint32_t sym = v < (unsigned long long)kEsc ? (uint32_t)v : (uint32_t)kEsc;
-      mybits += lens[sym] + (sym == kEsc ? D.width : 0u);
-    }
-    unsigned long long x = mybits;
-    for (int o = 1; o < 32; o <<= 1) {
-      unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    unsigned long long pos = (start & 31ull) + (x - mybits);  // relative to word w0
-    for (unsigned long long i = slo; i < shi; ++i) {
-      unsigned long long v = (unsigned long long)vals[i];
-      uint32_t sym = v < (unsigned long long)kEsc ? (uint32_t)v : (uint32_t)kEsc;
-      uint32_t L = lens[sym];
-      put_bits_smem(buf, pos, codes[sym], L);
-      pos += L;
-      if (sym == kEsc) {
-        put_bits_smem(buf, pos, v, D.width);
-        pos += D.width;
+    uint32_t base = (uint32_t)(start & 31ull);  // bit position relative to word w0
+    for (unsigned long long r0 = lo; r0 < hi; r0 += 32) {
+      const unsigned long long i = r0 + lane;
+      unsigned long long v = 0ull;
+      uint32_t sym = 0u, L = 0u, nb = 0u;
+      if (i < hi) {
+        v = (unsigned long long)vals[i];
+        sym = v < (unsigned long long)kEsc ? (uint32_t)v : (uint32_t)kEsc;
+        L = tab[sym] & 31u;
+        nb = L + (sym == kEsc ? D.width : 0u);
       }
+      uint32_t x = nb;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      const uint32_t pos = base + x - nb;
+      if (nb) {
+        put_bits_smem(buf, pos, tab[sym] >> 5, L);
+        if (sym == kEsc) put_bits_smem(buf, pos + L, v, D.width);
+      }
+      base += __shfl_sync(0xffffffffu, x, 31);
     }
     __syncwarp();
     for (uint32_t i = lane; i < nwords; i += 32) {
@@ -548,25 +635,32 @@ static void encode_stream(const T *vals, uint64_t n, const StreamDesc *desc, con
                           const Summary *summary, unsigned long long *chunk_bits,
                           unsigned long long *chunk_off, int sms, cudaStream_t s) {
   // fixed-length (no-op unless chosen)
-  unsigned long long words_max = (n * 64ull + 31ull) / 32ull;
-  unsigned g = (unsigned)std::min<unsigned long long>((words_max + 255) / 256, 8ull * sms);
+  const unsigned long long groups = (n + 31ull) / 32ull;
+  unsigned g = (unsigned)std::min<unsigned long long>((groups + kFixWarps - 1) / kFixWarps,
+                                                      8ull * sms);
   if (g == 0) g = 1;
   note_launch();
-  k_encode_fixed<T><<<g, 256, 0, s>>>(vals, desc, out, summary);
+  k_encode_fixed<T><<<g, 32 * kFixWarps, 0, s>>>(vals, desc, out, summary);
   // Huffman (no-op unless chosen)
   unsigned long long chunks = (n + (1ull << log2_chunk) - 1ull) >> log2_chunk;
   if (chunks == 0) return;
   unsigned gc = (unsigned)std::min<unsigned long long>((chunks * 32 + 255) / 256, 16ull * sms);
   note_launch();
-  k_chunk_bits<T><<<gc, 256, 0, s>>>(vals, desc, lens, log2_chunk, chunk_bits, summary);
+  k_chunk_bits<T><<<gc, 256, 0, s>>>(vals, desc, codes, lens, log2_chunk, chunk_bits, summary);
   launch_scan_small(chunk_bits, (uint32_t)chunks, chunk_off, s);
   unsigned gt = (unsigned)std::min<unsigned long long>((chunks + 255) / 256, 4ull * sms);
   note_launch();
   k_chunk_table<<<gt, 256, 0, s>>>(chunk_off, desc, out, summary);
-  unsigned ge = (unsigned)std::min<unsigned long long>((chunks + kEncWarps - 1) / kEncWarps, 16ull * sms);
+  unsigned ge = (unsigned)std::min<unsigned long long>((chunks + kEncWarps - 1) / kEncWarps, 2ull * sms);
+  static bool attr = false;  // per instantiation
+  if (!attr) {
+    cudaFuncSetAttribute(k_huff_encode<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kEncSmem);
+    attr = true;
+  }
   note_launch();
-  k_huff_encode<T><<<ge, 32 * kEncWarps, 0, s>>>(vals, desc, codes, lens, log2_chunk, chunk_off,
-                                                  out, summary);
+  k_huff_encode<T><<<ge, 32 * kEncWarps, kEncSmem, s>>>(vals, desc, codes, lens, log2_chunk,
+                                                         chunk_off, out, summary);
 }
 
 void launch_encode_u64(const unsigned long long *vals, uint64_t n, const StreamDesc *desc,

@@ -14,6 +14,7 @@
 // A scan of the start flags then numbers the blocks.  The output bytes
 // depend only on the multiset of keys, so no partition pass needs a stable
 // order.
+#include <algorithm>
 #include <type_traits>
 
 #include "lcp_kernels.h"
@@ -23,8 +24,10 @@ namespace lcp {
 constexpr int kLocalThreads = 256;
 constexpr int kLocalWarps = kLocalThreads / 32;
 constexpr int kCap = kUnitCap;  // keys of a unit sorted in shared memory
-constexpr int kSubBits = 10;    // level-2 split of buckets above kSplitMin keys
-constexpr int kSplitMin = 256;
+constexpr int kSplitMin = 256;  // buckets above this many keys are split again
+constexpr int kSubMinBits = 5;  // level-2 digit width: about 8 keys per sub-bucket,
+constexpr int kSubMaxBits = 12; // within these bounds
+constexpr int kSubMax = 1 << kSubMaxBits;
 constexpr int kSplitThreads = 512;
 constexpr int kSplitIlp = 4;    // keys in flight per thread in the split passes
 constexpr int kSubThreads = 256;
@@ -140,12 +143,36 @@ __global__ void __launch_bounds__(512) k_scatter(const unsigned long long *__res
   const uint32_t shift = plan->part_shift, nb = nb1 - 1;
   const uint64_t lo = (uint64_t)blockIdx.x * span;
   const uint64_t hi = min(n, lo + span);
-  for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    unsigned long long k = __ldcs(keys + i);
-    uint32_t b = (k & kOutlierBit) ? nb : (uint32_t)(k >> shift);
-    uint32_t pos = atomicAdd(&s_cur[b], 1u);
-    keys_out[pos] = k;
-    if (idx_out) idx_out[pos] = (uint32_t)i;
+  constexpr int kIlp = 8;  // loads, then cursor updates, in flight per thread
+  for (uint64_t i0 = lo; i0 < hi; i0 += (uint64_t)kIlp * blockDim.x) {
+    unsigned long long k[kIlp];
+#pragma unroll
+    for (int r = 0; r < kIlp; ++r) {
+      const uint64_t i = i0 + (uint64_t)r * blockDim.x + threadIdx.x;
+      k[r] = i < hi ? __ldcs(keys + i) : 0ull;
+    }
+    // one cursor update per run of lanes with the same bucket
+    uint32_t pos[kIlp];
+#pragma unroll
+    for (int r = 0; r < kIlp; ++r) {
+      const uint64_t i = i0 + (uint64_t)r * blockDim.x + threadIdx.x;
+      const bool valid = i < hi;
+      const uint32_t b = (k[r] & kOutlierBit) ? nb : (uint32_t)(k[r] >> shift);
+      int leader;
+      uint32_t rank, len;
+      lane_runs(b, valid, leader, rank, len);
+      uint32_t base = 0u;
+      if (valid && rank == 0u) base = atomicAdd(&s_cur[b], len);
+      pos[r] = __shfl_sync(0xffffffffu, base, leader) + rank;
+    }
+#pragma unroll
+    for (int r = 0; r < kIlp; ++r) {
+      const uint64_t i = i0 + (uint64_t)r * blockDim.x + threadIdx.x;
+      if (i < hi) {
+        keys_out[pos[r]] = k[r];
+        if (idx_out) idx_out[pos[r]] = (uint32_t)i;
+      }
+    }
   }
 }
 
@@ -277,75 +304,94 @@ __device__ int cta_sort(unsigned long long *k, uint32_t *i, unsigned long long *
 
 // ---------------------------------------------------------------------------
 // level-2 partition of buckets above kSplitMin keys: each such bucket is
-// split by the next kSubBits key bits (still block-id bits, so no block
-// crosses a sub-bucket), one CTA per bucket.  Sort units (k_local): the
+// split by the next sub_bits_for(count) key bits (still block-id bits, so no
+// block crosses a sub-bucket), one CTA per bucket.  Sort units (k_local): the
 // ordered list of key ranges holding consecutive unsplit buckets merged
 // greedily up to kCap keys, and the outlier bucket.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int split_bits(const Plan &P) {
-  return min(kSubBits, (int)P.part_shift - (int)P.rel_bits);
+// level-2 digit width of a split bucket of cnt keys (maxsub: block-id bits
+// below the level-1 digit)
+__device__ __forceinline__ int sub_bits_for(uint64_t cnt, int maxsub) {
+  int b = (int)bitlen64(cnt >> 3);
+  b = b < kSubMinBits ? kSubMinBits : (b > kSubMaxBits ? kSubMaxBits : b);
+  return b < maxsub ? b : maxsub;
+}
+__device__ __forceinline__ uint32_t sub_chunks(int sub) {
+  return sub > 5 ? (1u << (sub - 5)) : 1u;  // 32-digit chunks
 }
 
+// split buckets: big_list[j] = bucket, big_cb[j] = first 32-digit chunk of
+// its sub-bucket offsets (big_cb[nbig] = all chunks); nbig[0] = split
+// buckets, nbig[1] = work counter, nbig[2] = chunks
 __global__ void __launch_bounds__(1024) k_seg_plan(const Plan *__restrict__ plan, uint32_t nb1,
                                                    const unsigned long long *__restrict__ bstart,
                                                    uint32_t *__restrict__ big_list,
+                                                   uint32_t *__restrict__ big_cb,
                                                    int *__restrict__ big_of,
                                                    uint32_t *__restrict__ nbig) {
   __shared__ unsigned long long s_warp[32];
   const Plan &P = *plan;
   const uint32_t nb = nb1 - 1;
-  const int sub = split_bits(P);
+  const int maxsub = (int)P.part_shift - (int)P.rel_bits;
   const uint32_t per = (nb1 + 1023) / 1024;
   const uint32_t lo = threadIdx.x * per, hi = min(nb1, lo + per);
+  // (chunks << 32) | buckets
   unsigned long long c = 0;
   for (uint32_t b = lo; b < hi; ++b) {
-    const bool big =
-        sub > 0 && b < nb && (bstart[b + 1] - bstart[b]) > (unsigned long long)kSplitMin;
-    c += big;
+    const uint64_t cnt = bstart[b + 1] - bstart[b];
+    if (maxsub > 0 && b < nb && cnt > (uint64_t)kSplitMin)
+      c += ((unsigned long long)sub_chunks(sub_bits_for(cnt, maxsub)) << 32) | 1ull;
   }
   unsigned long long tot;
   unsigned long long run = block_exscan<1024>(c, s_warp, tot);
   for (uint32_t b = lo; b < hi; ++b) {
-    const bool big =
-        sub > 0 && b < nb && (bstart[b + 1] - bstart[b]) > (unsigned long long)kSplitMin;
-    big_of[b] = big ? (int)run : -1;
-    if (big) big_list[run++] = b;
+    const uint64_t cnt = bstart[b + 1] - bstart[b];
+    const bool big = maxsub > 0 && b < nb && cnt > (uint64_t)kSplitMin;
+    const uint32_t j = (uint32_t)run;
+    big_of[b] = big ? (int)j : -1;
+    if (big) {
+      big_list[j] = b;
+      big_cb[j] = (uint32_t)(run >> 32);
+      run += ((unsigned long long)sub_chunks(sub_bits_for(cnt, maxsub)) << 32) | 1ull;
+    }
   }
   if (threadIdx.x == 0) {
     nbig[0] = (uint32_t)tot;
     nbig[1] = 0u;  // work counter of k_split_big
+    nbig[2] = (uint32_t)(tot >> 32);
+    big_cb[(uint32_t)tot] = (uint32_t)(tot >> 32);
   }
 }
 
 // One CTA per split bucket (fetched from a work counter): sub-bucket
-// histogram, offsets (sub_off[j][digit], within the bucket), scatter.
-// Loads are issued kSplitIlp at a time.
+// histogram, offsets (sub_off[32 * big_cb[j] + digit], within the bucket),
+// scatter.  Loads are issued kSplitIlp at a time.
 __global__ void __launch_bounds__(kSplitThreads) k_split_big(
     const Plan *__restrict__ plan, const unsigned long long *__restrict__ bstart,
-    const uint32_t *__restrict__ big_list, uint32_t *__restrict__ nbig,
-    const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ idx,
-    unsigned long long *__restrict__ keys_out, uint32_t *__restrict__ idx_out,
-    uint32_t *__restrict__ sub_off) {
-  constexpr int kSub = 1 << kSubBits;
-  constexpr int per = kSub / kSplitThreads;
-  __shared__ uint32_t h[kSub];
+    const uint32_t *__restrict__ big_list, const uint32_t *__restrict__ big_cb,
+    uint32_t *__restrict__ nbig, const unsigned long long *__restrict__ keys,
+    const uint32_t *__restrict__ idx, unsigned long long *__restrict__ keys_out,
+    uint32_t *__restrict__ idx_out, uint32_t *__restrict__ sub_off) {
+  constexpr int per = kSubMax / kSplitThreads;
+  __shared__ uint32_t h[kSubMax];
   __shared__ unsigned long long s_warp[32];
   __shared__ uint32_t s_j;
   const Plan &P = *plan;
-  const int sub = split_bits(P);
-  const int shift2 = (int)P.part_shift - sub;
-  const uint32_t mask = (1u << sub) - 1u;
-  const uint32_t nsub = 1u << sub;
+  const int maxsub = (int)P.part_shift - (int)P.rel_bits;
   const uint32_t total_big = nbig[0];
   for (;;) {
     if (threadIdx.x == 0) s_j = atomicAdd(&nbig[1], 1u);
-    for (int d = threadIdx.x; d < kSub; d += kSplitThreads) h[d] = 0u;
+    for (int d = threadIdx.x; d < kSubMax; d += kSplitThreads) h[d] = 0u;
     __syncthreads();
     const uint32_t j = s_j;
     if (j >= total_big) break;
     const uint32_t b = big_list[j];
     const uint64_t lo = bstart[b];
     const uint32_t cnt = (uint32_t)(bstart[b + 1] - lo);
+    const int sub = sub_bits_for(cnt, maxsub);
+    const int shift2 = (int)P.part_shift - sub;
+    const uint32_t mask = (1u << sub) - 1u;
+    const uint32_t nsub = 1u << sub;
     const unsigned long long *kb = keys + lo;
     for (uint32_t t0 = 0; t0 < cnt; t0 += kSplitThreads * kSplitIlp) {
       unsigned long long k[kSplitIlp];
@@ -357,7 +403,11 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
 #pragma unroll
       for (int r = 0; r < kSplitIlp; ++r) {
         const uint32_t t = t0 + r * kSplitThreads + threadIdx.x;
-        if (t < cnt) atomicAdd(&h[(uint32_t)(k[r] >> shift2) & mask], 1u);
+        const uint32_t dg = (uint32_t)(k[r] >> shift2) & mask;
+        int leader;
+        uint32_t rank, len;
+        lane_runs(dg, t < cnt, leader, rank, len);
+        if (t < cnt && rank == 0u) atomicAdd(&h[dg], len);
       }
     }
     __syncthreads();
@@ -372,7 +422,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
     }
     unsigned long long tot;
     uint32_t run = (uint32_t)block_exscan<kSplitThreads>(sum, s_warp, tot);
-    uint32_t *so = sub_off + (uint64_t)j * kSub;
+    uint32_t *so = sub_off + (uint64_t)big_cb[j] * 32u;
 #pragma unroll
     for (int q = 0; q < per; ++q) {
       const uint32_t dg = threadIdx.x * per + q;
@@ -392,13 +442,24 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
         k[r] = t < cnt ? kb[t] : 0ull;
         ix[r] = (idx_out && t < cnt) ? idx[lo + t] : 0u;
       }
+      uint32_t pos[kSplitIlp];
+#pragma unroll
+      for (int r = 0; r < kSplitIlp; ++r) {
+        const uint32_t t = t0 + r * kSplitThreads + threadIdx.x;
+        const uint32_t dg = (uint32_t)(k[r] >> shift2) & mask;
+        int leader;
+        uint32_t rank, len;
+        lane_runs(dg, t < cnt, leader, rank, len);
+        uint32_t base = 0u;
+        if (t < cnt && rank == 0u) base = atomicAdd(&h[dg], len);
+        pos[r] = __shfl_sync(0xffffffffu, base, leader) + rank;
+      }
 #pragma unroll
       for (int r = 0; r < kSplitIlp; ++r) {
         const uint32_t t = t0 + r * kSplitThreads + threadIdx.x;
         if (t < cnt) {
-          const uint32_t pos = atomicAdd(&h[(uint32_t)(k[r] >> shift2) & mask], 1u);
-          keys_out[lo + pos] = k[r];
-          if (idx_out) idx_out[lo + pos] = ix[r];
+          keys_out[lo + pos[r]] = k[r];
+          if (idx_out) idx_out[lo + pos[r]] = ix[r];
         }
       }
     }
@@ -482,16 +543,23 @@ __global__ void __launch_bounds__(1024) k_units_small(uint32_t nb1,
   }
 }
 
+// every split bucket holds more than kSplitMin keys and at most
+// max(32, 2^kSubMaxBits) offsets, about one per 4..8 keys
+uint64_t sub_off_size(uint64_t n, uint32_t nb1) {
+  const uint64_t nbig = std::min<uint64_t>(nb1, n / (kSplitMin + 1) + 1);
+  return nbig * 32 + n / 4 + 64;
+}
+
 void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *bstart,
                      unsigned long long *keys, uint32_t *idx, unsigned long long *keys_alt,
-                     uint32_t *idx_alt, uint32_t *big_list, int *big_of, uint32_t *nbig,
-                     uint32_t *sub_off, uint32_t *u_lo, uint32_t *u_cnt, uint32_t *u_meta,
-                     uint32_t *nunit, int sms, cudaStream_t s) {
+                     uint32_t *idx_alt, uint32_t *big_list, uint32_t *big_cb, int *big_of,
+                     uint32_t *nbig, uint32_t *sub_off, uint32_t *u_lo, uint32_t *u_cnt,
+                     uint32_t *u_meta, uint32_t *nunit, int sms, cudaStream_t s) {
   note_launch();
-  k_seg_plan<<<1, 1024, 0, s>>>(plan, nb1, bstart, big_list, big_of, nbig);
+  k_seg_plan<<<1, 1024, 0, s>>>(plan, nb1, bstart, big_list, big_cb, big_of, nbig);
   note_launch();
-  k_split_big<<<4 * sms, kSplitThreads, 0, s>>>(plan, bstart, big_list, nbig, keys, idx, keys_alt,
-                                                idx_alt, sub_off);
+  k_split_big<<<4 * sms, kSplitThreads, 0, s>>>(plan, bstart, big_list, big_cb, nbig, keys, idx,
+                                                keys_alt, idx_alt, sub_off);
   note_launch();
   k_units_small<<<1, 1024, 0, s>>>(nb1, bstart, big_of, u_lo, u_cnt, u_meta, nunit);
 }
@@ -678,7 +746,7 @@ __device__ __forceinline__ void seg_emit(const SegOut &o, bool valid, uint64_t g
     v = (start || (g & o.chunk_mask) == 0) ? rel : rel - (prev & o.rel_mask);
     o.s_rel[g] = (uint32_t)v;
     o.bflag[g] = start ? 1 : 0;
-    if (start) o.tmp_bid[g] = key >> o.rel_bits;
+    o.tmp_bid[g] = key >> o.rel_bits;  // every slot: full sectors
     my_max = v > my_max ? v : my_max;
     if (PERM) {
       o.perm[g] = ix;
@@ -696,12 +764,14 @@ __device__ __forceinline__ void seg_emit(const SegOut &o, bool valid, uint64_t g
 
 // ---------------------------------------------------------------------------
 // sub-bucket runs of the split buckets: one warp per run, sorted and
-// segmented in registers.  Warp tasks are (split bucket, 32 consecutive
-// sub-buckets); a run starts at the first non-empty sub-bucket of the task
+// segmented in registers.  Warp tasks are 32 consecutive sub-buckets of a
+// split bucket; a run starts at the first non-empty sub-bucket of the task
 // and wherever a sub-bucket's offset enters a new kSubSpan-slot span, so a
 // run holds fewer than kSubSpan particles plus its last sub-bucket.  A run
-// too large for a warp becomes a k_local unit.
+// of more than kRunCap particles becomes a k_local unit.
 // ---------------------------------------------------------------------------
+constexpr int kRunCap = 128;
+
 template <int R, int MODE, bool PERM>
 __device__ __forceinline__ void sub_run_r(const unsigned long long *ks, const uint32_t *is, int c,
                                           unsigned long long base, uint64_t g0, const SegOut &o,
@@ -730,29 +800,27 @@ __device__ __forceinline__ void sub_run_r(const unsigned long long *ks, const ui
 }
 
 template <int MODE, bool PERM>
-__device__ __noinline__ void sub_run(const unsigned long long *ks, const uint32_t *is, int c,
-                                     unsigned long long base, uint64_t g0, const SegOut &o,
-                                     uint32_t *s_hist, unsigned long long &my_max) {
+__device__ __forceinline__ void sub_run(const unsigned long long *ks, const uint32_t *is, int c,
+                                        unsigned long long base, uint64_t g0, const SegOut &o,
+                                        uint32_t *s_hist, unsigned long long &my_max) {
   if (c <= 32) sub_run_r<1, MODE, PERM>(ks, is, c, base, g0, o, s_hist, my_max);
   else if (c <= 64) sub_run_r<2, MODE, PERM>(ks, is, c, base, g0, o, s_hist, my_max);
-  else if (c <= 128) sub_run_r<4, MODE, PERM>(ks, is, c, base, g0, o, s_hist, my_max);
-  else if (c <= 256) sub_run_r<8, MODE, PERM>(ks, is, c, base, g0, o, s_hist, my_max);
-  else if constexpr (MODE != 3) sub_run_r<16, MODE, PERM>(ks, is, c, base, g0, o, s_hist, my_max);
+  else sub_run_r<4, MODE, PERM>(ks, is, c, base, g0, o, s_hist, my_max);
 }
 
 template <bool PERM>
 __global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
-  constexpr int kSub = 1 << kSubBits;
   __shared__ uint32_t s_hist[kAlpha];
   __shared__ unsigned long long s_max;
   __shared__ int s_status;
-  __shared__ uint32_t s_part, s_rel, s_d, s_nbig;
+  __shared__ uint32_t s_part, s_rel, s_d, s_nbig, s_nchunk;
   if (threadIdx.x == 0) {
     s_status = A.plan->status;
     s_part = A.plan->part_shift;
     s_rel = A.plan->rel_bits;
     s_d = A.plan->d;
     s_nbig = A.nbig[0];
+    s_nchunk = A.nbig[2];
     s_max = 0ull;
   }
   for (int b = threadIdx.x; b < kAlpha; b += kSubThreads) s_hist[b] = 0u;
@@ -760,9 +828,7 @@ __global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
   if (s_status != OK) return;
   const int lane = threadIdx.x & 31;
   const uint32_t part_shift = s_part, rel_bits = s_rel;
-  const int sub = min(kSubBits, (int)part_shift - (int)rel_bits);
-  const uint32_t nsub = 1u << sub;
-  const int shift2 = (int)part_shift - sub;
+  const int maxsub = (int)part_shift - (int)rel_bits;
   SegOut o;
   o.s_rel = A.s_rel;
   o.bflag = A.bflag;
@@ -776,15 +842,24 @@ __global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
   o.rel_mask = (1ull << rel_bits) - 1ull;
   o.chunk_mask = (1ull << A.log2_chunk) - 1ull;
   unsigned long long my_max = 0ull;
-  const uint32_t ntask = s_nbig * 32u;
+  const uint32_t nbig = s_nbig, ntask = s_nchunk;
   const uint32_t warps = gridDim.x * (kSubThreads / 32);
   for (uint32_t t = blockIdx.x * (kSubThreads / 32) + (threadIdx.x >> 5); t < ntask; t += warps) {
-    const uint32_t j = t >> 5, ch = t & 31u;
-    if (ch * 32u >= nsub) continue;
+    // the split bucket of chunk t: big_cb[j] <= t < big_cb[j + 1]
+    uint32_t jl = 0, jh = nbig;
+    while (jh - jl > 1) {
+      const uint32_t mid = (jl + jh) >> 1;
+      if (A.big_cb[mid] <= t) jl = mid;
+      else jh = mid;
+    }
+    const uint32_t j = jl, ch = t - A.big_cb[j];
     const uint32_t b = A.big_list[j];
     const uint64_t lo = A.bstart[b];
     const uint32_t cnt = (uint32_t)(A.bstart[b + 1] - lo);
-    const uint32_t *so = A.sub_off + (uint64_t)j * kSub;
+    const int sub = sub_bits_for(cnt, maxsub);
+    const uint32_t nsub = 1u << sub;
+    const int shift2 = (int)part_shift - sub;
+    const uint32_t *so = A.sub_off + (uint64_t)A.big_cb[j] * 32u;
     const uint32_t dg = ch * 32u + lane;
     const uint32_t off = dg < nsub ? so[dg] : cnt;
     uint32_t nx = __shfl_down_sync(0xffffffffu, off, 1);
@@ -808,13 +883,7 @@ __global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
       const uint32_t wend = __shfl_sync(0xffffffffu, off, l1 & 31);
       const uint32_t w1 = l1 == 32 ? chunk_end : wend;
       const int wc = (int)(w1 - w0);
-      // digits of the run: l0 .. last non-empty lane before l1
-      const uint32_t below = l1 == 32 ? ne : (ne & ((1u << l1) - 1u));
-      const uint32_t g0 = ch * 32u + (uint32_t)l0;
-      const uint32_t g1 = ch * 32u + (uint32_t)(32 - __clz(below));
-      const unsigned long long base = bucket_base | ((unsigned long long)g0 << shift2);
-      const int mode = window_mode((unsigned long long)(g1 - g0) << shift2, PERM);
-      if (wc > window_cap(mode)) {
+      if (wc > kRunCap) {
         if (lane == 0) {
           const uint32_t u = atomicAdd(A.nunit, 1u);
           A.u_lo[u] = (uint32_t)(lo + w0);
@@ -823,6 +892,12 @@ __global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
         }
         continue;
       }
+      // digits of the run: l0 .. last non-empty lane before l1
+      const uint32_t below = l1 == 32 ? ne : (ne & ((1u << l1) - 1u));
+      const uint32_t g0 = ch * 32u + (uint32_t)l0;
+      const uint32_t g1 = ch * 32u + (uint32_t)(32 - __clz(below));
+      const unsigned long long base = bucket_base | ((unsigned long long)g0 << shift2);
+      const int mode = window_mode((unsigned long long)(g1 - g0) << shift2, PERM);
       const uint64_t g = lo + w0;
       if (mode == 0) {
         sub_run<0, PERM>(ks + w0, PERM ? is + w0 : nullptr, wc, base, g, o, s_hist, my_max);
@@ -846,8 +921,8 @@ __global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
 
 void launch_subsort(const SubsortArgs &a, int sms, cudaStream_t s) {
   note_launch();
-  if (a.perm) k_subsort<true><<<4 * sms, kSubThreads, 0, s>>>(a);
-  else k_subsort<false><<<4 * sms, kSubThreads, 0, s>>>(a);
+  if (a.perm) k_subsort<true><<<8 * sms, kSubThreads, 0, s>>>(a);
+  else k_subsort<false><<<8 * sms, kSubThreads, 0, s>>>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -1163,23 +1238,22 @@ void launch_local(const LocalArgs &a, int ctas, cudaStream_t s) {
 // non-outlier slots), then delta code ids and counts (Sec. "Block coding")
 // ---------------------------------------------------------------------------
 constexpr int kFlagThreads = 256;
-constexpr int kFlagPer = 16;  // slots per thread (one 16-byte load)
+constexpr int kFlagPer = 8;  // slots per thread (one 8-byte load)
 constexpr int kFlagTile = kFlagThreads * kFlagPer;
 
-__device__ __forceinline__ uint32_t flag_count16(const uint8_t *flag, uint64_t g, uint64_t nbk,
-                                                 uint32_t &bits) {
-  // flags of slots g .. g+15 (g a multiple of 16) as a bit mask
-  bits = 0u;
+__device__ __forceinline__ uint32_t flag_bits8(const uint8_t *flag, uint64_t g, uint64_t nbk) {
+  // start flags of slots g .. g+7 (g a multiple of 8) as a bit mask
   if (g >= nbk) return 0u;
-  const uint4 w = *reinterpret_cast<const uint4 *>(flag + g);
-  const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+  const uint2 w = *reinterpret_cast<const uint2 *>(flag + g);
+  uint32_t bits = 0u;
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) bits |= ((ws[q] >> (8 * b)) & 1u) << (4 * q + b);
+  for (int b = 0; b < 4; ++b) {
+    bits |= ((w.x >> (8 * b)) & 1u) << b;
+    bits |= ((w.y >> (8 * b)) & 1u) << (4 + b);
+  }
   const uint64_t left = nbk - g;
-  if (left < 16) bits &= (1u << left) - 1u;
-  return __popc(bits);
+  if (left < 8) bits &= (1u << left) - 1u;
+  return bits;
 }
 
 __global__ void __launch_bounds__(kFlagThreads) k_flag_count(
@@ -1188,33 +1262,50 @@ __global__ void __launch_bounds__(kFlagThreads) k_flag_count(
   __shared__ unsigned long long s_warp[32];
   const uint64_t nbk = *nbkp;
   const uint64_t g = (uint64_t)blockIdx.x * kFlagTile + (uint64_t)threadIdx.x * kFlagPer;
-  uint32_t bits;
-  const uint32_t c = flag_count16(flag, g, nbk, bits);
+  const uint32_t c = __popc(flag_bits8(flag, g, nbk));
   unsigned long long tot;
   block_exscan<kFlagThreads>(c, s_warp, tot);
   if (threadIdx.x == 0) tile_cnt[blockIdx.x] = tot;
 }
 
 // bpos[B] = slot of block B's first particle, bidv[B] = its block id;
-// bpos[M] = nbk; mcount = M
+// bpos[M] = nbk; mcount = M.  A tile's blocks are gathered in shared memory
+// and written out contiguously.
 __global__ void __launch_bounds__(kFlagThreads) k_flag_apply(
     const uint8_t *__restrict__ flag, const unsigned long long *__restrict__ nbkp,
     const unsigned long long *__restrict__ tile_base, uint32_t ntiles,
     const unsigned long long *__restrict__ tmp_bid, uint32_t *__restrict__ bpos,
     unsigned long long *__restrict__ bidv, unsigned long long *__restrict__ mcount) {
   __shared__ unsigned long long s_warp[32];
+  __shared__ uint32_t s_pos[kFlagTile];
+  __shared__ unsigned long long s_bid[kFlagTile];
   const uint64_t nbk = *nbkp;
   const uint64_t g = (uint64_t)blockIdx.x * kFlagTile + (uint64_t)threadIdx.x * kFlagPer;
-  uint32_t bits;
-  const uint32_t c = flag_count16(flag, g, nbk, bits);
+  uint32_t bits = flag_bits8(flag, g, nbk);
   unsigned long long tot;
-  unsigned long long B = tile_base[blockIdx.x] + block_exscan<kFlagThreads>(c, s_warp, tot);
-  while (bits) {
-    const int b = __ffs(bits) - 1;
-    bits &= bits - 1u;
-    bpos[B] = (uint32_t)(g + b);
-    bidv[B] = tmp_bid[g + b];
-    ++B;
+  uint32_t t = (uint32_t)block_exscan<kFlagThreads>(__popc(bits), s_warp, tot);
+  if (bits) {
+    unsigned long long ids[kFlagPer];
+    const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(tmp_bid + g);
+#pragma unroll
+    for (int q = 0; q < kFlagPer / 2; ++q) {
+      const ulonglong2 v = src[q];
+      ids[2 * q] = v.x;
+      ids[2 * q + 1] = v.y;
+    }
+#pragma unroll
+    for (int b = 0; b < kFlagPer; ++b)
+      if ((bits >> b) & 1u) {
+        s_pos[t] = (uint32_t)(g + b);
+        s_bid[t] = ids[b];
+        ++t;
+      }
+  }
+  __syncthreads();
+  const unsigned long long B0 = tile_base[blockIdx.x];
+  for (uint32_t i = threadIdx.x; i < (uint32_t)tot; i += kFlagThreads) {
+    bpos[B0 + i] = s_pos[i];
+    bidv[B0 + i] = s_bid[i];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const unsigned long long M = tile_base[ntiles];

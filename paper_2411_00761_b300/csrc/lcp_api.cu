@@ -44,12 +44,12 @@ T *P(DevBuf &b) {
 }
 
 struct Workspace {
-  DevBuf big_list, big_of, nbig, sub_cnt, seg_lo, seg_cnt, seg_meta, nseg, bflag, ftile, fbase;
+  DevBuf big_list, big_cb, big_of, nbig, sub_cnt, seg_lo, seg_cnt, seg_meta, nseg, bflag, ftile, fbase;
   DevBuf mm, plan, keys, keys2, idx2, idx_alt, tile_hist, btot, bstart, s_rel, tmp_bid, tmp_pos,
       s_id, s_cnt, hist, maxv, nvals, mcount, kcount, desc, codes, lens,
       tables, chunk_bits, chunk_off, outl_idx, summary, q_in, q_slot, perm, sym, patch_s,
       patch_i, patch_x, patch_s2, patch_i2, patch_so, patch_io, dec_fields, hufft, err,
-      scan_tmp, scan_base, bid, counts, starts, cand, tq, fplan, fstatus;
+      scan_tmp, scan_base, bid, counts, starts, cand, tq, fplan, fstatus, cbwork;
 };
 
 __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
@@ -197,6 +197,7 @@ int ws_common(lcp_ctx *c, uint64_t n, uint32_t d) {
   TRY(grow(w.lens, 3ull * kAlpha));
   TRY(grow(w.tables, 3ull * (kAlpha + 32) * 2));
   TRY(grow(w.summary, sizeof(Summary)));
+  TRY(grow(w.cbwork, codebook_work_size(3)));
   const uint64_t nd = n * d;
   const uint64_t chunks = std::max<uint64_t>(nd, n) / 1024 + 2;
   TRY(grow(w.chunk_bits, chunks * 8));
@@ -239,12 +240,12 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   TRY(grow(w.fbase, (flag_tiles(nn) + 1) * 8));
   // split buckets (each above 256 keys) and the units: unsplit buckets
   // merged, the outlier bucket, runs of sub-buckets too large for a warp
-  const uint64_t nbig_max = n / 256 + 1;
-  const uint64_t segcap = nb1 + n / 256 + 2;
-  TRY(grow(w.big_list, (size_t)nb1 * 4));
+  const uint64_t segcap = nb1 + n / 128 + 2;
+  TRY(grow(w.big_list, (size_t)(nb1 + 1) * 4));
+  TRY(grow(w.big_cb, (size_t)(nb1 + 1) * 4));
   TRY(grow(w.big_of, (size_t)nb1 * 4));
   TRY(grow(w.nbig, 16));
-  TRY(grow(w.sub_cnt, (size_t)std::min<uint64_t>(nbig_max, nb1) * 1024 * 4));
+  TRY(grow(w.sub_cnt, (size_t)sub_off_size(n, nb1) * 4));
   TRY(grow(w.seg_lo, (size_t)segcap * 4));
   TRY(grow(w.seg_cnt, (size_t)segcap * 4));
   TRY(grow(w.seg_meta, (size_t)segcap * 4));
@@ -278,8 +279,9 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   launch_segments(P<Plan>(w.plan), nb1, P<unsigned long long>(w.bstart),
                   P<unsigned long long>(w.keys2), want_perm ? P<uint32_t>(w.idx2) : nullptr,
                   P<unsigned long long>(w.keys), want_perm ? P<uint32_t>(w.idx_alt) : nullptr,
-                  P<uint32_t>(w.big_list), P<int>(w.big_of), P<uint32_t>(w.nbig),
-                  P<uint32_t>(w.sub_cnt), P<uint32_t>(w.seg_lo), P<uint32_t>(w.seg_cnt),
+                  P<uint32_t>(w.big_list), P<uint32_t>(w.big_cb), P<int>(w.big_of),
+                  P<uint32_t>(w.nbig), P<uint32_t>(w.sub_cnt), P<uint32_t>(w.seg_lo),
+                  P<uint32_t>(w.seg_cnt),
                   P<uint32_t>(w.seg_meta), P<uint32_t>(w.nseg), sms, s);
   prof_end(c, s);
   CK(cudaMemsetAsync(w.hist.p, 0, 3ull * kAlpha * 4, s));
@@ -287,6 +289,7 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   SubsortArgs sa;
   sa.plan = P<Plan>(w.plan);
   sa.big_list = P<uint32_t>(w.big_list);
+  sa.big_cb = P<uint32_t>(w.big_cb);
   sa.nbig = P<uint32_t>(w.nbig);
   sa.bstart = P<unsigned long long>(w.bstart);
   sa.sub_off = P<uint32_t>(w.sub_cnt);
@@ -348,7 +351,8 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   // 8. codebooks and the container layout
   prof_begin(c, "s.codebook", s);
   launch_codebook(3, P<uint32_t>(w.hist), P<unsigned long long>(w.maxv),
-                  P<unsigned long long>(w.nvals), kLog2Chunk, P<StreamDesc>(w.desc),
+                  P<unsigned long long>(w.nvals), kLog2Chunk, P<uint8_t>(w.cbwork),
+                  P<StreamDesc>(w.desc),
                   P<uint32_t>(w.codes), P<uint8_t>(w.lens), P<uint16_t>(w.tables), s);
   LayoutArgs L;
   L.method = 0;
@@ -425,7 +429,8 @@ int compress_t_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   note_launch();
   k_set_u64<<<1, 1, 0, s>>>(P<unsigned long long>(w.nvals), (unsigned long long)(n * d));
   launch_codebook(1, P<uint32_t>(w.hist), P<unsigned long long>(w.maxv),
-                  P<unsigned long long>(w.nvals), kLog2Chunk, P<StreamDesc>(w.desc),
+                  P<unsigned long long>(w.nvals), kLog2Chunk, P<uint8_t>(w.cbwork),
+                  P<StreamDesc>(w.desc),
                   P<uint32_t>(w.codes), P<uint8_t>(w.lens), P<uint16_t>(w.tables), s);
   LayoutArgs L;
   L.method = 1;

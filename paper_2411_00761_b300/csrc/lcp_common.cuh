@@ -120,6 +120,27 @@ __host__ __device__ inline uint32_t bitlen64(unsigned long long v) {
 // ---------------------------------------------------------------------------
 // float helpers
 // ---------------------------------------------------------------------------
+// Runs of equal values held by consecutive lanes of a warp (a lane that is
+// not valid forms a run of its own): the run's first lane, this lane's rank
+// in the run and the run's length.  One shared-memory atomic per run then
+// serves clustered inputs, whose neighbouring lanes often hit one counter.
+// All 32 lanes must call it.
+__device__ __forceinline__ void lane_runs(uint32_t v, bool valid, int &leader, uint32_t &rank,
+                                          uint32_t &len) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t up = __shfl_up_sync(0xffffffffu, v, 1);
+  const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+  const bool prev_valid = lane > 0 && ((vmask >> (lane - 1)) & 1u);
+  const bool head = !valid || !prev_valid || up != v;
+  const uint32_t heads = __ballot_sync(0xffffffffu, head);
+  const uint32_t le = 0xffffffffu >> (31 - lane);  // lanes 0..lane
+  leader = 31 - __clz(heads & le);
+  const uint32_t above = heads & ~le;
+  const int next = above ? __ffs(above) - 1 : 32;
+  rank = (uint32_t)(lane - leader);
+  len = (uint32_t)(next - leader);
+}
+
 __device__ __forceinline__ uint32_t order_key(float f) {
   uint32_t b = __float_as_uint(f);
   return (b & 0x80000000u) ? ~b : (b | 0x80000000u);

@@ -62,11 +62,13 @@ void launch_scatter(const unsigned long long *keys, uint64_t n, const Plan *plan
 // level-2 split of the buckets above the split threshold (sub_off: per
 // split bucket, the offset of each sub-bucket) and the unit list of the
 // unsplit buckets and the outlier bucket
+// big_list, big_cb: nb1 + 1 entries; nbig: 4; sub_off: sub_off_size(n, nb1)
+uint64_t sub_off_size(uint64_t n, uint32_t nb1);
 void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *bstart,
                      unsigned long long *keys, uint32_t *idx, unsigned long long *keys_alt,
-                     uint32_t *idx_alt, uint32_t *big_list, int *big_of, uint32_t *nbig,
-                     uint32_t *sub_off, uint32_t *u_lo, uint32_t *u_cnt, uint32_t *u_meta,
-                     uint32_t *nunit, int sms, cudaStream_t s);
+                     uint32_t *idx_alt, uint32_t *big_list, uint32_t *big_cb, int *big_of,
+                     uint32_t *nbig, uint32_t *sub_off, uint32_t *u_lo, uint32_t *u_cnt,
+                     uint32_t *u_meta, uint32_t *nunit, int sms, cudaStream_t s);
 // sorting and segmentation outputs, per sorted slot g: s_rel[g] (relative
 // location deltas), bflag[g] (1 where a block starts), tmp_bid[g] (the block
 // id, at block starts only), perm[g] and q_slot (perm mode)
@@ -95,7 +97,7 @@ void launch_local(const LocalArgs &a, int ctas, cudaStream_t s);
 // runs too large for a warp are appended to the unit list
 struct SubsortArgs {
   const Plan *plan;
-  const uint32_t *big_list, *nbig;
+  const uint32_t *big_list, *big_cb, *nbig;
   const unsigned long long *bstart;
   const uint32_t *sub_off;
   const unsigned long long *keys_alt;      // split keys
@@ -133,9 +135,12 @@ void launch_sort_pairs(unsigned long long *keys, uint32_t *vals, unsigned long l
                        unsigned long long *keys_out, uint32_t *vals_out, cudaStream_t s);
 
 // --- coding (k_code.cu) --------------------------------------------------
+// work: codebook_work_size(ns) bytes
+size_t codebook_work_size(int ns);
 void launch_codebook(int ns, const uint32_t *hist, const unsigned long long *maxv,
-                     const unsigned long long *n_vals, uint32_t log2_chunk, StreamDesc *desc,
-                     uint32_t *codes, uint8_t *lens, uint16_t *tables, cudaStream_t s);
+                     const unsigned long long *n_vals, uint32_t log2_chunk, uint8_t *work,
+                     StreamDesc *desc, uint32_t *codes, uint8_t *lens, uint16_t *tables,
+                     cudaStream_t s);
 struct LayoutArgs {
   int method;  // 0 S, 1 T
   uint32_t d, log2_chunk, flags, p;
