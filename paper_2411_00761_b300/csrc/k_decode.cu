@@ -709,9 +709,12 @@ void launch_check_counts(const unsigned long long *counts, uint64_t m,
 }
 
 // ---------------------------------------------------------------------------
-// LCP-S expand + reconstruct: one CTA per chunk of particles
+// LCP-S expand + reconstruct: one CTA per tile of kExpTile particles, four
+// consecutive particles per thread
 // ---------------------------------------------------------------------------
-constexpr int kExpThreads = 1024;
+constexpr int kExpThreads = 256;
+constexpr int kExpPer = kExpTile / kExpThreads;
+static_assert(kExpPer == 4, "four particles per thread (one 16-byte load / store)");
 
 template <int D>
 __global__ void __launch_bounds__(kExpThreads) k_expand_s(
@@ -720,99 +723,164 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_s(
     uint64_t nb, uint64_t n, uint32_t log2_chunk, const uint32_t *__restrict__ tile_first,
     float *__restrict__ out, int32_t *__restrict__ qout, int *__restrict__ err) {
   __shared__ FieldPlan sF[D];
-  __shared__ uint32_t sb_f[kExpThreads][D];
-  __shared__ uint8_t s_flag[kExpThreads];
-  __shared__ uint32_t s_wv[32], s_wf[32], s_wb[32];
+  __shared__ uint32_t sb_f[kExpTile][D];  // per-axis block corner of the tile's blocks
+  __shared__ __align__(16) uint8_t s_flag[kExpTile];  // a block starts here (not the first)
+  __shared__ uint32_t s_wv[kExpThreads / 32], s_wf[kExpThreads / 32], s_wb[kExpThreads / 32];
   __shared__ uint32_t s_lp;
   if (threadIdx.x < D) sF[threadIdx.x] = plan->f[threadIdx.x];
   if (threadIdx.x == 0) s_lp = plan->lp;
-  // tiles of kExpThreads particles; the chunk size divides the tile, so every
+  // tiles of kExpTile particles; the chunk size divides the tile, so every
   // tile starts a chunk (relative locations restart there)
   const uint64_t cmask = (1ull << log2_chunk) - 1ull;
-  const uint64_t lo = (uint64_t)blockIdx.x * kExpThreads;
-  const uint64_t hi = min(nb, lo + kExpThreads);
+  const uint64_t lo = (uint64_t)blockIdx.x * kExpTile;
+  const uint64_t hi = min(nb, lo + kExpTile);
   const uint64_t first = tile_first[blockIdx.x];
-  s_flag[threadIdx.x] = 0;
+  reinterpret_cast<uint32_t *>(s_flag)[threadIdx.x] = 0u;
   __syncthreads();
   const uint32_t lp = s_lp;
-  // block first + t: its per-axis block indices (multiply-shift division,
-  // field 0 fastest) and, for t > 0, a start flag at its first particle
-  const uint64_t bi = first + threadIdx.x;
-  if (bi < M) {
-    const unsigned long long st = bstart[bi];
-    if (st < hi) {
-      if (threadIdx.x > 0 && st > lo) s_flag[st - lo] = 1;
-      unsigned long long r = bid[bi];
+  // blocks first + t (at most kExpTile overlap the tile): per-axis block
+  // indices (multiply-shift division, field 0 fastest) and, for t > 0, a
+  // start flag at the block's first particle
 #pragma unroll
-      for (int f = 0; f < D; ++f) {
-        const FieldPlan &F = sF[f];
-        unsigned long long qd = F.bshift == 255u ? r : (__umul64hi(r, F.bmagic) >> F.bshift);
-        unsigned long long bf = r - qd * F.bn;
-        sb_f[threadIdx.x][f] = (uint32_t)(bf << lp);
-        r = qd;
+  for (int j = 0; j < kExpPer; ++j) {
+    const uint32_t t = threadIdx.x + j * kExpThreads;
+    const uint64_t bi = first + t;
+    if (bi < M) {
+      const unsigned long long st = bstart[bi];
+      if (st < hi) {
+        if (t > 0 && st > lo) s_flag[st - lo] = 1;
+        unsigned long long r = bid[bi];
+#pragma unroll
+        for (int f = 0; f < D; ++f) {
+          const FieldPlan &F = sF[f];
+          const unsigned long long qd =
+              F.bshift == 255u ? r : (__umul64hi(r, F.bmagic) >> F.bshift);
+          const unsigned long long bf = r - qd * F.bn;
+          sb_f[t][f] = (uint32_t)(bf << lp);
+          r = qd;
+        }
       }
     }
   }
   __syncthreads();
-  // particle of this thread: block ordinal = inclusive count of start flags;
-  // relative code = segmented inclusive sum (segments at block and chunk starts)
-  const uint64_t k = lo + threadIdx.x;
-  const bool valid = k < hi;
-  const uint32_t flag = valid ? s_flag[threadIdx.x] : 0u;
-  const bool seg = (k == lo) || flag || ((k & cmask) == 0);
-  uint32_t x = valid ? s_rel[k] : 0u;
-  uint32_t fl = seg ? 1u : 0u;
-  uint32_t cb = flag;
+  // this thread's particles k0 .. k0+3: block ordinal = inclusive count of
+  // start flags; relative code = segmented inclusive sum (segments at block
+  // and chunk starts)
+  const uint64_t k0 = lo + (uint64_t)threadIdx.x * kExpPer;
+  uint32_t x[kExpPer], fl[kExpPer];
+  const uint32_t flags4 = reinterpret_cast<const uint32_t *>(s_flag)[threadIdx.x];
+  if (k0 + kExpPer <= hi) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(s_rel + k0);
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+    x[3] = v.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < kExpPer; ++j) x[j] = k0 + j < hi ? s_rel[k0 + j] : 0u;
+  }
+  uint32_t tv = 0u, tf = 0u, tb = 0u;  // thread aggregate: value, has-segment-start, flags
+#pragma unroll
+  for (int j = 0; j < kExpPer; ++j) {
+    const uint64_t k = k0 + j;
+    const uint32_t f = (flags4 >> (8 * j)) & 1u;
+    fl[j] = f;
+    const bool seg = (k == lo) || f || ((k & cmask) == 0);
+    if (seg) {
+      tv = x[j];
+      tf = 1u;
+    } else {
+      tv += x[j];
+    }
+    x[j] = tv;  // thread-local inclusive segmented sum
+    tb += f;
+  }
+  // exclusive carry from the threads before: (value, flag) segmented, counts plain
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t cv = tv, cf = tf, cc = tb;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    uint32_t g = __shfl_up_sync(0xffffffffu, fl, o);
-    uint32_t c = __shfl_up_sync(0xffffffffu, cb, o);
+    const uint32_t y = __shfl_up_sync(0xffffffffu, cv, o);
+    const uint32_t g = __shfl_up_sync(0xffffffffu, cf, o);
+    const uint32_t c = __shfl_up_sync(0xffffffffu, cc, o);
     if (lane >= o) {
-      if (!fl) x += y;
-      fl |= g;
-      cb += c;
+      if (!cf) cv += y;
+      cf |= g;
+      cc += c;
     }
   }
   if (lane == 31) {
-    s_wv[w] = x;
-    s_wf[w] = fl;
-    s_wb[w] = cb;
+    s_wv[w] = cv;
+    s_wf[w] = cf;
+    s_wb[w] = cc;
   }
   __syncthreads();
-  if (w == 0) {
-    uint32_t xv = s_wv[lane], xf = s_wf[lane], xb = s_wb[lane];
+  // carry-in of warp w: fold warps 0..w-1
+  uint32_t wv = 0u, wf = 0u, wb = 0u;
+  for (int u = 0; u < w; ++u) {
+    if (s_wf[u]) wv = s_wv[u];
+    else wv += s_wv[u];
+    wf |= s_wf[u];
+    wb += s_wb[u];
+  }
+  // exclusive within the warp
+  uint32_t ev = __shfl_up_sync(0xffffffffu, cv, 1);
+  uint32_t ef = __shfl_up_sync(0xffffffffu, cf, 1);
+  uint32_t ec = __shfl_up_sync(0xffffffffu, cc, 1);
+  if (lane == 0) {
+    ev = 0u;
+    ef = 0u;
+    ec = 0u;
+  }
+  const uint32_t inv = ef ? ev : ev + wv;  // carry value into this thread
+  const uint32_t inb = ec + wb;            // start flags before this thread
+  uint32_t blk[kExpPer], rel[kExpPer];
+  {
+    bool seen = false;  // a segment started within this thread so far
+    uint32_t bc = inb;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, xv, o);
-      uint32_t g = __shfl_up_sync(0xffffffffu, xf, o);
-      uint32_t c = __shfl_up_sync(0xffffffffu, xb, o);
-      if (lane >= o) {
-        if (!xf) xv += y;
-        xf |= g;
-        xb += c;
-      }
+    for (int j = 0; j < kExpPer; ++j) {
+      const uint64_t k = k0 + j;
+      const bool seg = (k == lo) || fl[j] || ((k & cmask) == 0);
+      seen |= seg;
+      rel[j] = seen ? x[j] : x[j] + inv;
+      bc += fl[j];
+      blk[j] = bc;
     }
-    s_wv[lane] = xv;  // inclusive carry-out of warps 0..lane
-    s_wb[lane] = xb;
   }
-  __syncthreads();
-  if (w > 0) {
-    if (!fl) x += s_wv[w - 1];
-    cb += s_wb[w - 1];
-  }
-  if (!valid) return;
-  const uint32_t rel = x;
-  const uint32_t blk = cb;
   const uint32_t pm = (1u << lp) - 1u;
+  const bool full = (k0 + kExpPer <= hi) && ((n & 3ull) == 0) &&
+                    ((((uintptr_t)out) | (uintptr_t)qout) & 15u) == 0;
 #pragma unroll
   for (int f = 0; f < D; ++f) {
-    const FieldPlan &F = sF[f];
-    const uint32_t q = sb_f[blk][f] + ((rel >> (f * lp)) & pm);
-    if (q > F.qmax) atomicExch(err, 1);
-    out[(uint64_t)f * n + k] = reconstruct((long long)q, F);
-    if (qout) qout[(uint64_t)f * n + k] = (int32_t)q;
+    const uint32_t c8 = sF[f].c8, sticky = sF[f].sticky, qmax = sF[f].qmax;
+    const long long mb = sF[f].mb;
+    const int32_t g1 = sF[f].g1;
+    float r[kExpPer];
+    int32_t q4[kExpPer];
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < kExpPer; ++j) {
+      const uint32_t q = sb_f[blk[j]][f] + ((rel[j] >> (f * lp)) & pm);
+      bad |= (k0 + j < hi) && q > qmax;
+      q4[j] = (int32_t)q;
+      r[j] = reconstruct_c((long long)q, c8, mb, sticky, g1, sF[f]);
+    }
+    if (bad) atomicExch(err, 1);
+    float *o = out + (uint64_t)f * n + k0;
+    if (full) {
+      *reinterpret_cast<float4 *>(o) = make_float4(r[0], r[1], r[2], r[3]);
+      if (qout)
+        *reinterpret_cast<int4 *>(qout + (uint64_t)f * n + k0) =
+            make_int4(q4[0], q4[1], q4[2], q4[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kExpPer; ++j)
+        if (k0 + j < hi) {
+          o[j] = r[j];
+          if (qout) qout[(uint64_t)f * n + k0 + j] = q4[j];
+        }
+    }
   }
 }
 
@@ -821,7 +889,7 @@ static void expand_t(const Plan *plan, const unsigned long long *bid, const unsi
                      uint64_t M, const uint32_t *s_rel, uint64_t nb, uint64_t n,
                      uint32_t log2_chunk, const uint32_t *tile_first, float *out, int32_t *qout,
                      int *err, cudaStream_t s) {
-  const uint64_t chunks = (nb + kExpThreads - 1) / kExpThreads;
+  const uint64_t chunks = (nb + kExpTile - 1) / kExpTile;
   if (chunks == 0) return;
   note_launch();
   k_expand_s<D><<<(unsigned)chunks, kExpThreads, 0, s>>>(plan, bid, bstart, M, s_rel, nb, n,

@@ -390,6 +390,21 @@ __device__ __forceinline__ float reconstruct(long long q, const FieldPlan &F) {
   return recon_wide(q, F);
 }
 
+// reconstruct() with the plan's constants already in registers; Fs (the
+// plan, e.g. in shared memory) serves the rare wide fallback
+__device__ __forceinline__ float reconstruct_c(long long q, uint32_t c8, long long mb,
+                                               uint32_t sticky, int32_t g1,
+                                               const FieldPlan &Fs) {
+  long long V = (2 * q + 1) * (long long)c8 + mb;
+  long long W = 2 * V + (long long)sticky;
+  float r = __ll2float_rn(W);
+  uint32_t b = __float_as_uint(r);
+  if ((b & 0x7fffffffu) == 0) return r;
+  int ne = (int)((b >> 23) & 0xffu) + g1;
+  if (ne >= 1 && ne <= 254) return __uint_as_float((uint32_t)((int)b + g1 * (1 << 23)));
+  return recon_wide(q, Fs);
+}
+
 // ---------------------------------------------------------------------------
 // Q3: |x - xr| > e exactly
 // ---------------------------------------------------------------------------
