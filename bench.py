@@ -80,10 +80,20 @@ def stage_bytes(stage: str, N, D, M, K, C):
         "s.quantize": raw + 8 * N,
         "s.bucket_offsets": 0,
         "s.scatter": 16 * N,
-        "s.local_sort": 8 * N + 4 * nb + 12 * M,
-        "s.blocks": 12 * M + 16 * M,
+        # level-2 split: keys read twice (histogram, scatter), written once
+        "s.split": 24 * nb,
+        # runs of sub-buckets (nearly all particles): keys in; deltas, start
+        # flags and block ids out
+        "s.subsort": 8 * nb + 4 * nb + nb + 8 * nb,
+        "s.local_sort": 0,
+        # flags read twice, dense block ids read once; slots and ids of M
+        # blocks written, read back, deltas written
+        "s.blocks": 2 * nb + 8 * nb + 12 * M + 12 * M + 16 * M,
         "s.codebook": 0,
-        "s.encode": 16 * M + 4 * nb + C,
+        "s.encode_ids": 16 * M,
+        "s.encode_counts": 16 * M,
+        "s.encode_rel": 4 * nb,
+        "s.outliers": 4 * K * D,
         "d.streams": C + 16 * M + 4 * nb,
         "d.block_scans": 48 * M,
         "d.expand": 16 * M + 4 * nb + raw,

@@ -233,9 +233,12 @@ struct BitReader4 {
 
 // All Huffman streams of a container in one launch.  CTA b serves stream s
 // with cta_base[s] <= b < cta_base[s+1]; inside it, a warp decodes 32
-// consecutive chunks, lane l the chunk c0 + l, 32 symbols per round into
-// shared memory, then writes each lane's 32 values with coalesced stores.
-constexpr int kDecWarps = 2;
+// consecutive chunks, lane l the chunk c0 + l, kDecR symbols per round into
+// a shared-memory stage; each store instruction then writes kDecR
+// consecutive values of 32 / kDecR chunks.
+constexpr int kDecWarps = 8;
+constexpr int kDecR = 16;
+constexpr size_t kDecStage = sizeof(unsigned long long) * kDecWarps * 32 * (kDecR + 1);
 
 struct HuffJob {
   const uint8_t *sec;
@@ -250,12 +253,61 @@ struct HuffJobs {
   int n;
 };
 
+// MSB-first bit window over one lane's payload words: w holds nb valid bits
+// (left aligned), kept above 32 after every refill; nx is the next word,
+// loaded one refill ahead.  Words past the payload read as zero.
+struct LaneBits {
+  unsigned long long w;
+  int nb;
+  uint32_t nx;
+  const uint32_t *p, *end;
+  __device__ __forceinline__ uint32_t ld(const uint32_t *q) const { return q < end ? __ldg(q) : 0u; }
+  __device__ __forceinline__ void init(const uint32_t *pl, unsigned long long nwords,
+                                       unsigned long long pos) {
+    end = pl + nwords;
+    const uint32_t *q = pl + (pos >> 5);
+    w = ((unsigned long long)ld(q) << 32) | ld(q + 1);
+    const int off = (int)(pos & 31);
+    w <<= off;
+    nb = 64 - off;
+    p = q + 2;
+    nx = ld(p);
+    refill();
+  }
+  __device__ __forceinline__ void refill() {
+    if (nb <= 32) {
+      w |= (unsigned long long)nx << (32 - nb);
+      nb += 32;
+      ++p;
+      nx = ld(p);
+    }
+  }
+  __device__ __forceinline__ void drop(int n) {  // n <= 32
+    w <<= n;
+    nb -= n;
+    refill();
+  }
+  __device__ __forceinline__ unsigned long long raw(int width) {  // 1 <= width <= 64
+    if (width <= 32) {
+      const unsigned long long v = w >> (64 - width);
+      drop(width);
+      return v;
+    }
+    const int h = width - 32;
+    const unsigned long long hi = w >> (64 - h);
+    drop(h);
+    const unsigned long long lo = w >> 32;
+    drop(32);
+    return (hi << 32) | lo;
+  }
+};
+
 __global__ void __launch_bounds__(32 * kDecWarps) k_huff_decode(HuffJobs jobs,
                                                                 int *__restrict__ err) {
   __shared__ uint32_t fast[1 << kFastBits];
   __shared__ uint32_t first[kLmax + 1], index[kLmax + 1], count[kLmax + 1];
   __shared__ uint16_t syms[kAlpha];
-  __shared__ unsigned long long stage[kDecWarps][32][33];
+  extern __shared__ unsigned long long dec_stage[];  // [warp][lane][kDecR + 1]
   int js = 0;
   while (js + 1 < jobs.n && blockIdx.x >= jobs.j[js + 1].cta_base) ++js;
   const HuffJob &J = jobs.j[js];
@@ -274,6 +326,8 @@ __global__ void __launch_bounds__(32 * kDecWarps) k_huff_decode(HuffJobs jobs,
     return;
   }
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  unsigned long long(*stage)[kDecR + 1] =
+      reinterpret_cast<unsigned long long(*)[kDecR + 1]>(dec_stage + (size_t)wl * 32 * (kDecR + 1));
   const unsigned long long cs = 1ull << info.log2_chunk;
   const uint8_t *ct = J.sec + pad16(80ull + 2ull * info.used);
   const uint32_t *pl = reinterpret_cast<const uint32_t *>(ct + pad16(8ull * info.n_chunks));
@@ -285,61 +339,66 @@ __global__ void __launch_bounds__(32 * kDecWarps) k_huff_decode(HuffJobs jobs,
   const bool act = c < info.n_chunks;
   const unsigned long long lo = c * cs;
   const unsigned long long hi = act ? min(info.n, lo + cs) : lo;
-  BitReader4 br;
+  LaneBits br;
   bool ok = true;
   if (act) {
     const unsigned long long pos = (unsigned long long)reinterpret_cast<const uint32_t *>(ct)[2 * c] |
                                    ((unsigned long long)reinterpret_cast<const uint32_t *>(ct)[2 * c + 1] << 32);
-    if (pos > info.payload_bits) {
-      atomicExch(err, 1);
-      ok = false;
-    }
+    if (pos > info.payload_bits) ok = false;
     br.init(pl, nwords, ok ? pos : 0ull);
   }
-  const unsigned long long mine = (act && ok) ? hi - lo : 0ull;
+  const uint32_t mine = (act && ok) ? (uint32_t)(hi - lo) : 0u;
+  const int width = (int)info.width;
+  bool bad = act && !ok;
   unsigned long long *o64 = reinterpret_cast<unsigned long long *>(J.out);
   uint32_t *o32 = reinterpret_cast<uint32_t *>(J.out);
-  for (unsigned long long r0 = 0; r0 < cs; r0 += 32) {
-    for (int k = 0; k < 32; ++k) {
-      if (r0 + k >= mine) break;
-      uint32_t e = fast[br.peek(kFastBits)];
+  constexpr int kChunksPerStore = 32 / kDecR;
+  const int wsub = lane % kDecR, wch = lane / kDecR;
+  for (uint32_t r0 = 0; r0 < (uint32_t)cs; r0 += kDecR) {
+    const uint32_t todo = mine > r0 ? min(mine - r0, (uint32_t)kDecR) : 0u;
+    for (uint32_t k = 0; k < todo; ++k) {
+      const uint32_t e = fast[(uint32_t)(br.w >> (64 - kFastBits))];
       uint32_t sym;
+      int len;
       if (e) {
         sym = e >> 5;
-        br.skip((int)(e & 31u));
+        len = (int)(e & 31u);
       } else {
         int L = kFastBits + 1;
         uint32_t code = 0;
         for (; L <= kLmax; ++L) {
-          code = br.peek(L);
+          code = (uint32_t)(br.w >> (64 - L));
           if (code - first[L] < count[L]) break;
         }
         if (L > kLmax) {
-          atomicExch(err, 1);
+          bad = true;
           sym = 0;
-          L = 1;
+          len = 1;
         } else {
           sym = syms[index[L] + (code - first[L])];
+          len = L;
         }
-        br.skip(L);
       }
+      br.drop(len);
       unsigned long long v = sym;
-      if (sym == (uint32_t)kEsc) v = br.read((int)info.width);
-      stage[wl][lane][k] = v;
+      if (sym == (uint32_t)kEsc && width > 0) v = br.raw(width);
+      stage[lane][k] = v;
     }
     __syncwarp();
-    for (int l = 0; l < 32; ++l) {
+#pragma unroll 4
+    for (int it = 0; it < 32 / kChunksPerStore; ++it) {
+      const int l = it * kChunksPerStore + wch;
       const unsigned long long cl = g * 32 + l;
-      if (cl >= info.n_chunks) break;
-      const unsigned long long base = cl * cs + r0;
-      const unsigned long long lim = min(info.n, cl * cs + cs);
-      if (base + lane < lim) {
-        if (J.wide) o64[base + lane] = stage[wl][l][lane];
-        else o32[base + lane] = (uint32_t)stage[wl][l][lane];
+      const unsigned long long base = cl * cs + r0 + wsub;
+      if (cl < info.n_chunks && base < min(info.n, cl * cs + cs)) {
+        if (J.wide) o64[base] = stage[l][wsub];
+        else o32[base] = (uint32_t)stage[l][wsub];
       }
     }
     __syncwarp();
+    if (__all_sync(0xffffffffu, r0 + kDecR >= mine)) break;
   }
+  if (bad) atomicExch(err, 1);
 }
 
 template <typename T>
@@ -407,8 +466,14 @@ void launch_decode_streams(int ns, const uint8_t *const *secs, const StreamInfo 
   }
   (void)sms;
   if (jobs.n) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_huff_decode, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kDecStage);
+      attr = true;
+    }
     note_launch();
-    k_huff_decode<<<ctas, 32 * kDecWarps, 0, s>>>(jobs, err);
+    k_huff_decode<<<ctas, 32 * kDecWarps, kDecStage, s>>>(jobs, err);
   }
 }
 

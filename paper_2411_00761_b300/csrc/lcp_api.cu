@@ -374,20 +374,26 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   CK(cudaGetLastError());
   if (!size_only) {
     // 9. payloads
-    prof_begin(c, "s.encode", s);
     StreamDesc *D = P<StreamDesc>(w.desc);
+    prof_begin(c, "s.encode_ids", s);
     launch_encode_u64(P<unsigned long long>(w.s_id), n, D + 0, P<uint32_t>(w.codes),
                       P<uint8_t>(w.lens), kLog2Chunk, out, P<Summary>(w.summary),
                       P<unsigned long long>(w.chunk_bits), P<unsigned long long>(w.chunk_off), sms,
                       s);
+    prof_end(c, s);
+    prof_begin(c, "s.encode_counts", s);
     launch_encode_u64(P<unsigned long long>(w.s_cnt), n, D + 1, P<uint32_t>(w.codes) + kAlpha,
                       P<uint8_t>(w.lens) + kAlpha, kLog2Chunk, out, P<Summary>(w.summary),
                       P<unsigned long long>(w.chunk_bits), P<unsigned long long>(w.chunk_off), sms,
                       s);
+    prof_end(c, s);
+    prof_begin(c, "s.encode_rel", s);
     launch_encode_u32(P<uint32_t>(w.s_rel), n, D + 2, P<uint32_t>(w.codes) + 2 * kAlpha,
                       P<uint8_t>(w.lens) + 2 * kAlpha, kLog2Chunk, out, P<Summary>(w.summary),
                       P<unsigned long long>(w.chunk_bits), P<unsigned long long>(w.chunk_off), sms,
                       s);
+    prof_end(c, s);
+    prof_begin(c, "s.outliers", s);
     launch_outliers_s(X, n, d, P<uint32_t>(w.outl_idx), D + 3, out, P<Summary>(w.summary), sms, s);
     prof_end(c, s);
     CK(cudaGetLastError());
