@@ -447,6 +447,7 @@ void launch_layout(const LayoutArgs &a, int sms, bool size_only, cudaStream_t s)
 // whole words) in shared memory and writes the w words out
 // ---------------------------------------------------------------------------
 constexpr int kFixWarps = 8;
+constexpr int kFixGroups = 4;  // groups per warp iteration (their loads issued together)
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kFixWarps) k_encode_fixed(
@@ -463,30 +464,40 @@ __global__ void __launch_bounds__(32 * kFixWarps) k_encode_fixed(
   const unsigned long long words = words_of(D.payload_bits);
   const unsigned long long groups = (D.n + 31) >> 5;
   const unsigned long long nw = (unsigned long long)gridDim.x * kFixWarps;
-  for (unsigned long long g = (unsigned long long)blockIdx.x * kFixWarps + wl; g < groups; g += nw) {
-    buf[lane] = 0u;
-    buf[lane + 32] = 0u;
-    __syncwarp();
-    const unsigned long long i = g * 32ull + lane;
-    if (i < D.n) {
-      const unsigned long long v = (unsigned long long)vals[i];
-      // bits [lane*w, lane*w + w) of the group, MSB first
-      const uint32_t b0 = (uint32_t)lane * w;
-      uint32_t left = w, pos = b0;
-      while (left) {
-        const uint32_t wi = pos >> 5, off = pos & 31u;
-        const uint32_t take = min(left, 32u - off);
-        const unsigned long long part = (v >> (left - take)) & ((1ull << take) - 1ull);
-        atomicOr(&buf[wi], (uint32_t)part << (32u - off - take));
-        pos += take;
-        left -= take;
-      }
+  for (unsigned long long g0 = ((unsigned long long)blockIdx.x * kFixWarps + wl) * kFixGroups;
+       g0 < groups; g0 += nw * kFixGroups) {
+    unsigned long long v[kFixGroups];
+#pragma unroll
+    for (int q = 0; q < kFixGroups; ++q) {
+      const unsigned long long i = (g0 + q) * 32ull + lane;
+      v[q] = i < D.n ? (unsigned long long)vals[i] : 0ull;
     }
-    __syncwarp();
-    const unsigned long long wbase = g * (unsigned long long)w;
-    for (uint32_t k = lane; k < w; k += 32)
-      if (wbase + k < words) pl[wbase + k] = buf[k];
-    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < kFixGroups; ++q) {
+      const unsigned long long g = g0 + q;
+      if (g >= groups) break;
+      buf[lane] = 0u;
+      buf[lane + 32] = 0u;
+      __syncwarp();
+      const unsigned long long i = g * 32ull + lane;
+      if (i < D.n) {
+        // bits [lane*w, lane*w + w) of the group, MSB first
+        uint32_t left = w, pos = (uint32_t)lane * w;
+        while (left) {
+          const uint32_t wi = pos >> 5, off = pos & 31u;
+          const uint32_t take = min(left, 32u - off);
+          const unsigned long long part = (v[q] >> (left - take)) & ((1ull << take) - 1ull);
+          atomicOr(&buf[wi], (uint32_t)part << (32u - off - take));
+          pos += take;
+          left -= take;
+        }
+      }
+      __syncwarp();
+      const unsigned long long wbase = g * (unsigned long long)w;
+      for (uint32_t k = lane; k < w; k += 32)
+        if (wbase + k < words) pl[wbase + k] = buf[k];
+      __syncwarp();
+    }
   }
 }
 
@@ -527,10 +538,19 @@ __global__ void __launch_bounds__(256) k_chunk_bits(const T *__restrict__ vals,
   for (unsigned long long c = warp; c < D.n_chunks; c += nw) {
     const unsigned long long lo = c * cs, hi = min(D.n, lo + cs);
     unsigned long long bits = 0;
-    for (unsigned long long i = lo + lane; i < hi; i += 32) {
-      const unsigned long long v = (unsigned long long)vals[i];
-      const uint32_t sym = v < (unsigned long long)kEsc ? (uint32_t)v : (uint32_t)kEsc;
-      bits += (tab[sym] & 31u) + (sym == kEsc ? D.width : 0u);
+    for (unsigned long long i0 = lo + lane; i0 < hi; i0 += 32 * 8) {
+      unsigned long long v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const unsigned long long i = i0 + 32ull * q;
+        v[q] = i < hi ? (unsigned long long)vals[i] : 0ull;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (i0 + 32ull * q >= hi) continue;
+        const uint32_t sym = v[q] < (unsigned long long)kEsc ? (uint32_t)v[q] : (uint32_t)kEsc;
+        bits += (tab[sym] & 31u) + (sym == kEsc ? D.width : 0u);
+      }
     }
     for (int o = 16; o; o >>= 1) bits += __shfl_down_sync(0xffffffffu, bits, o);
     if (lane == 0) chunk_bits[c] = bits;
@@ -593,28 +613,38 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_huff_encode(
     for (uint32_t i = lane; i < nwords; i += 32) buf[i] = 0u;
     __syncwarp();
     uint32_t base = (uint32_t)(start & 31ull);  // bit position relative to word w0
-    for (unsigned long long r0 = lo; r0 < hi; r0 += 32) {
-      const unsigned long long i = r0 + lane;
-      unsigned long long v = 0ull;
-      uint32_t sym = 0u, L = 0u, nb = 0u;
-      if (i < hi) {
-        v = (unsigned long long)vals[i];
-        sym = v < (unsigned long long)kEsc ? (uint32_t)v : (uint32_t)kEsc;
-        L = tab[sym] & 31u;
-        nb = L + (sym == kEsc ? D.width : 0u);
-      }
-      uint32_t x = nb;
+    for (unsigned long long b0 = lo; b0 < hi; b0 += 32 * 8) {
+      unsigned long long vv[8];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+      for (int q = 0; q < 8; ++q) {
+        const unsigned long long i = b0 + 32ull * q + lane;
+        vv[q] = i < hi ? (unsigned long long)vals[i] : 0ull;
       }
-      const uint32_t pos = base + x - nb;
-      if (nb) {
-        put_bits_smem(buf, pos, tab[sym] >> 5, L);
-        if (sym == kEsc) put_bits_smem(buf, pos + L, v, D.width);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const unsigned long long r0 = b0 + 32ull * q;
+        if (r0 >= hi) break;
+        const unsigned long long i = r0 + lane;
+        const unsigned long long v = vv[q];
+        uint32_t sym = 0u, L = 0u, nb = 0u;
+        if (i < hi) {
+          sym = v < (unsigned long long)kEsc ? (uint32_t)v : (uint32_t)kEsc;
+          L = tab[sym] & 31u;
+          nb = L + (sym == kEsc ? D.width : 0u);
+        }
+        uint32_t x = nb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        const uint32_t pos = base + x - nb;
+        if (nb) {
+          put_bits_smem(buf, pos, tab[sym] >> 5, L);
+          if (sym == kEsc) put_bits_smem(buf, pos + L, v, D.width);
+        }
+        base += __shfl_sync(0xffffffffu, x, 31);
       }
-      base += __shfl_sync(0xffffffffu, x, 31);
     }
     __syncwarp();
     for (uint32_t i = lane; i < nwords; i += 32) {
@@ -636,7 +666,8 @@ static void encode_stream(const T *vals, uint64_t n, const StreamDesc *desc, con
                           unsigned long long *chunk_off, int sms, cudaStream_t s) {
   // fixed-length (no-op unless chosen)
   const unsigned long long groups = (n + 31ull) / 32ull;
-  unsigned g = (unsigned)std::min<unsigned long long>((groups + kFixWarps - 1) / kFixWarps,
+  const unsigned long long units = (groups + kFixGroups - 1) / kFixGroups;
+  unsigned g = (unsigned)std::min<unsigned long long>((units + kFixWarps - 1) / kFixWarps,
                                                       8ull * sms);
   if (g == 0) g = 1;
   note_launch();
@@ -647,7 +678,7 @@ static void encode_stream(const T *vals, uint64_t n, const StreamDesc *desc, con
   unsigned gc = (unsigned)std::min<unsigned long long>((chunks * 32 + 255) / 256, 16ull * sms);
   note_launch();
   k_chunk_bits<T><<<gc, 256, 0, s>>>(vals, desc, codes, lens, log2_chunk, chunk_bits, summary);
-  launch_scan_small(chunk_bits, (uint32_t)chunks, chunk_off, s);
+  launch_scan_small(chunk_bits, (uint32_t)chunks, chunk_off, s, &desc->coder);
   unsigned gt = (unsigned)std::min<unsigned long long>((chunks + 255) / 256, 4ull * sms);
   note_launch();
   k_chunk_table<<<gt, 256, 0, s>>>(chunk_off, desc, out, summary);

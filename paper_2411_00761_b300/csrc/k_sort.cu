@@ -77,34 +77,80 @@ __global__ void k_bucket_colsum(const uint32_t *__restrict__ tile_hist, int tile
   totals[b] = s;
 }
 
-// exclusive scan of n values (one CTA); out[n] = total
+// exclusive scan of n values (one CTA); out[n] = total.  Tiles of
+// kScanTileS values: loaded coalesced (the next tile's loads issued before
+// the current one is scanned), four consecutive values per thread.
+constexpr int kScanTileS = 4096;
+
 __global__ void __launch_bounds__(1024) k_scan_small(const unsigned long long *__restrict__ in,
                                                      uint32_t n,
-                                                     unsigned long long *__restrict__ out) {
+                                                     unsigned long long *__restrict__ out,
+                                                     const uint32_t *__restrict__ gate) {
+  __shared__ unsigned long long t[kScanTileS];
   __shared__ unsigned long long s_warp[32];
-  const uint32_t per = (n + 1023) / 1024;
-  const uint32_t lo = threadIdx.x * per, hi = min(n, lo + per);
-  unsigned long long sum = 0;
-  for (uint32_t i = lo; i < hi; ++i) sum += in[i];
-  unsigned long long total;
-  unsigned long long run = block_exscan<1024>(sum, s_warp, total);
-  for (uint32_t i = lo; i < hi; ++i) {
-    unsigned long long v = in[i];
-    out[i] = run;
-    run += v;
+  if (gate && *gate != 1u) return;  // the stream this scan serves is not Huffman coded
+  constexpr int per = kScanTileS / 1024;
+  unsigned long long cur[per], nxt[per];
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    const uint32_t i = threadIdx.x + 1024u * k;
+    cur[k] = i < n ? in[i] : 0ull;
   }
-  if (threadIdx.x == 0) out[n] = total;
+  unsigned long long carry = 0;
+  for (uint32_t base = 0; base < n; base += kScanTileS) {
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+      const uint32_t i = base + kScanTileS + threadIdx.x + 1024u * k;
+      nxt[k] = i < n ? in[i] : 0ull;
+    }
+#pragma unroll
+    for (int k = 0; k < per; ++k) t[threadIdx.x + 1024 * k] = cur[k];
+    __syncthreads();
+    unsigned long long v[per], sum = 0;
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+      v[j] = t[per * threadIdx.x + j];
+      sum += v[j];
+    }
+    unsigned long long total;
+    unsigned long long run = carry + block_exscan<1024>(sum, s_warp, total);
+#pragma unroll
+    for (int j = 0; j < per; ++j) {
+      t[per * threadIdx.x + j] = run;
+      run += v[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+      const uint32_t i = base + threadIdx.x + 1024u * k;
+      if (i < n) out[i] = t[threadIdx.x + 1024 * k];
+    }
+    carry += total;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < per; ++k) cur[k] = nxt[k];
+  }
+  if (threadIdx.x == 0) out[n] = carry;
 }
 
+// per bucket, the running offset over the tiles (eight tiles' counts loaded
+// at a time)
 __global__ void k_bucket_tileoff(uint32_t *__restrict__ tile_hist, int tiles, uint32_t nb1,
                                  const unsigned long long *__restrict__ bucket_start) {
   uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nb1) return;
   uint32_t run = (uint32_t)bucket_start[b];
-  for (int t = 0; t < tiles; ++t) {
-    uint32_t v = tile_hist[(uint64_t)t * nb1 + b];
-    tile_hist[(uint64_t)t * nb1 + b] = run;
-    run += v;
+  for (int t0 = 0; t0 < tiles; t0 += 8) {
+    uint32_t v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      v[j] = t0 + j < tiles ? tile_hist[(uint64_t)(t0 + j) * nb1 + b] : 0u;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (t0 + j < tiles) {
+        tile_hist[(uint64_t)(t0 + j) * nb1 + b] = run;
+        run += v[j];
+      }
   }
 }
 
@@ -115,15 +161,15 @@ void launch_bucket_offsets(uint32_t *tile_hist, int tiles, uint32_t nb1,
   note_launch();
   k_bucket_colsum<<<g, 256, 0, s>>>(tile_hist, tiles, nb1, totals);
   note_launch();
-  k_scan_small<<<1, 1024, 0, s>>>(totals, nb1, bucket_start);
+  k_scan_small<<<1, 1024, 0, s>>>(totals, nb1, bucket_start, nullptr);
   note_launch();
   k_bucket_tileoff<<<g, 256, 0, s>>>(tile_hist, tiles, nb1, bucket_start);
 }
 
 void launch_scan_small(const unsigned long long *in, uint32_t n, unsigned long long *out,
-                       cudaStream_t s) {
+                       cudaStream_t s, const uint32_t *gate) {
   note_launch();
-  k_scan_small<<<1, 1024, 0, s>>>(in, n, out);
+  k_scan_small<<<1, 1024, 0, s>>>(in, n, out, gate);
 }
 
 // ---------------------------------------------------------------------------
