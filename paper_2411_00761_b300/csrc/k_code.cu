@@ -83,34 +83,39 @@ __global__ void __launch_bounds__(kCbThreads) k_cb_build(const uint32_t *__restr
   __syncthreads();
   if (threadIdx.x == 0) {
     // leaves nodew[0..U) ascending; internal node j (id U + j) has weight
-    // nodew[U + j], created in non-decreasing order.  The heads of both
-    // queues and the next entry of each are kept in registers.
+    // nodew[U + j], created in non-decreasing order.  Branch-free picks: the
+    // next four leaves and three internal nodes are kept in registers, the
+    // refills loaded unconditionally (clamped in range) and selected.  An
+    // internal entry not yet created is filled in when its node is made.
     const uint32_t *lw = nodew;
     uint32_t *iw = nodew + U;
     int nl = 0, ni = 0;
-    uint32_t L0 = lw[0], L1 = lw[1];
-    uint32_t I0 = 0u, I1 = 0u;
+    uint32_t L0 = lw[0], L1 = lw[1], L2 = lw[min(2, U - 1)], L3 = lw[min(3, U - 1)];
+    uint32_t I0 = 0u, I1 = 0u, I2 = 0u;
     for (int nn = 0; nn < U - 1; ++nn) {
       uint32_t sum = 0u;
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        int id;
-        if (nl < U && (ni == nn || L0 <= I0)) {
-          sum += L0;
-          id = nl++;
-          L0 = L1;
-          L1 = nl + 1 < U ? lw[nl + 1] : 0u;
-        } else {
-          sum += I0;
-          id = U + ni++;
-          I0 = I1;
-          I1 = ni + 1 < nn ? iw[ni + 1] : 0u;
-        }
-        parent[id] = (uint16_t)(U + nn);
+        const uint32_t nextL = lw[min(nl + 4, U - 1)];
+        const uint32_t nextI = iw[min(ni + 3, U - 2)];
+        const bool leaf = nl < U && (ni == nn || L0 <= I0);
+        sum += leaf ? L0 : I0;
+        parent[leaf ? nl : U + ni] = (uint16_t)(U + nn);
+        L0 = leaf ? L1 : L0;
+        L1 = leaf ? L2 : L1;
+        L2 = leaf ? L3 : L2;
+        L3 = leaf ? nextL : L3;
+        I0 = leaf ? I0 : I1;
+        I1 = leaf ? I1 : I2;
+        I2 = leaf ? I2 : nextI;
+        nl += leaf ? 1 : 0;
+        ni += leaf ? 0 : 1;
       }
       iw[nn] = sum;
-      if (ni == nn) I0 = sum;
-      else if (ni + 1 == nn) I1 = sum;
+      const int q = nn - ni;  // queue length before this node joins
+      I0 = q == 0 ? sum : I0;
+      I1 = q == 1 ? sum : I1;
+      I2 = q == 2 ? sum : I2;
     }
     parent[2 * U - 2] = (uint16_t)(2 * U - 2);
   }

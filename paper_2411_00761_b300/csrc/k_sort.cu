@@ -417,7 +417,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
     const uint32_t *__restrict__ big_list, const uint32_t *__restrict__ big_cb,
     uint32_t *__restrict__ nbig, const unsigned long long *__restrict__ keys,
     const uint32_t *__restrict__ idx, unsigned long long *__restrict__ keys_out,
-    uint32_t *__restrict__ idx_out, uint32_t *__restrict__ sub_off) {
+    uint32_t *__restrict__ idx_out, uint32_t *__restrict__ sub_off,
+    uint32_t *__restrict__ chunk_owner) {
   constexpr int per = kSubMax / kSplitThreads;
   __shared__ uint32_t h[kSubMax];
   __shared__ unsigned long long s_warp[32];
@@ -439,6 +440,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
     const uint32_t mask = (1u << sub) - 1u;
     const uint32_t nsub = 1u << sub;
     const unsigned long long *kb = keys + lo;
+    for (uint32_t q = threadIdx.x; q < sub_chunks(sub); q += kSplitThreads)
+      chunk_owner[big_cb[j] + q] = j;
     for (uint32_t t0 = 0; t0 < cnt; t0 += kSplitThreads * kSplitIlp) {
       unsigned long long k[kSplitIlp];
 #pragma unroll
@@ -599,13 +602,14 @@ uint64_t sub_off_size(uint64_t n, uint32_t nb1) {
 void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *bstart,
                      unsigned long long *keys, uint32_t *idx, unsigned long long *keys_alt,
                      uint32_t *idx_alt, uint32_t *big_list, uint32_t *big_cb, int *big_of,
-                     uint32_t *nbig, uint32_t *sub_off, uint32_t *u_lo, uint32_t *u_cnt,
-                     uint32_t *u_meta, uint32_t *nunit, int sms, cudaStream_t s) {
+                     uint32_t *nbig, uint32_t *sub_off, uint32_t *chunk_owner, uint32_t *u_lo,
+                     uint32_t *u_cnt, uint32_t *u_meta, uint32_t *nunit, int sms,
+                     cudaStream_t s) {
   note_launch();
   k_seg_plan<<<1, 1024, 0, s>>>(plan, nb1, bstart, big_list, big_cb, big_of, nbig);
   note_launch();
   k_split_big<<<4 * sms, kSplitThreads, 0, s>>>(plan, bstart, big_list, big_cb, nbig, keys, idx,
-                                                keys_alt, idx_alt, sub_off);
+                                                keys_alt, idx_alt, sub_off, chunk_owner);
   note_launch();
   k_units_small<<<1, 1024, 0, s>>>(nb1, bstart, big_of, u_lo, u_cnt, u_meta, nunit);
 }
@@ -636,11 +640,14 @@ __device__ __forceinline__ KeyIdx shfl_x(const KeyIdx &v, int m) {
   return KeyIdx{shfl_x(v.k, m), shfl_x(v.i, m)};
 }
 
+// kmax (a power of two, 2 <= kmax <= 32R): the elements that matter all lie
+// in [0, kmax) (the rest are padding); levels above kmax are skipped, and the
+// first kmax elements still end ascending.
 template <int R, typename T>
-__device__ __forceinline__ void warp_bitonic(T (&v)[R]) {
+__device__ __forceinline__ void warp_bitonic(T (&v)[R], uint32_t kmax = 32u * R) {
   const uint32_t lane = threadIdx.x & 31;
 #pragma unroll 1
-  for (uint32_t k = 2; k <= 32u * R; k <<= 1) {
+  for (uint32_t k = 2; k <= kmax; k <<= 1) {
     if (k > (uint32_t)R) {
       // element i = lane*R + r sorts up when bit k of i is clear; for k > R
       // that bit is bit k/R of the lane
@@ -830,7 +837,11 @@ __device__ __forceinline__ void sub_run_r(const unsigned long long *ks, const ui
     const int i = lane * R + r;
     v[r] = i < c ? win_make<MODE>(ks[i], PERM ? is[i] : 0u, base) : win_pad<MODE>();
   }
-  if (c > 1) warp_bitonic<R>(v);
+  if (c > 1) {
+    uint32_t kmax = 2u;
+    while (kmax < (uint32_t)c) kmax <<= 1;
+    warp_bitonic<R>(v, kmax);
+  }
   unsigned long long key[R];
   uint32_t ix[R];
 #pragma unroll
@@ -888,17 +899,10 @@ __global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
   o.rel_mask = (1ull << rel_bits) - 1ull;
   o.chunk_mask = (1ull << A.log2_chunk) - 1ull;
   unsigned long long my_max = 0ull;
-  const uint32_t nbig = s_nbig, ntask = s_nchunk;
+  const uint32_t ntask = s_nchunk;
   const uint32_t warps = gridDim.x * (kSubThreads / 32);
   for (uint32_t t = blockIdx.x * (kSubThreads / 32) + (threadIdx.x >> 5); t < ntask; t += warps) {
-    // the split bucket of chunk t: big_cb[j] <= t < big_cb[j + 1]
-    uint32_t jl = 0, jh = nbig;
-    while (jh - jl > 1) {
-      const uint32_t mid = (jl + jh) >> 1;
-      if (A.big_cb[mid] <= t) jl = mid;
-      else jh = mid;
-    }
-    const uint32_t j = jl, ch = t - A.big_cb[j];
+    const uint32_t j = A.chunk_owner[t], ch = t - A.big_cb[j];
     const uint32_t b = A.big_list[j];
     const uint64_t lo = A.bstart[b];
     const uint32_t cnt = (uint32_t)(A.bstart[b + 1] - lo);

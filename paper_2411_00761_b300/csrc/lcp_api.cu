@@ -44,7 +44,7 @@ T *P(DevBuf &b) {
 }
 
 struct Workspace {
-  DevBuf big_list, big_cb, big_of, nbig, sub_cnt, seg_lo, seg_cnt, seg_meta, nseg, bflag, ftile, fbase;
+  DevBuf big_list, big_cb, chunk_owner, big_of, nbig, sub_cnt, seg_lo, seg_cnt, seg_meta, nseg, bflag, ftile, fbase;
   DevBuf mm, plan, keys, keys2, idx2, idx_alt, tile_hist, btot, bstart, s_rel, tmp_bid, tmp_pos,
       s_id, s_cnt, hist, maxv, nvals, mcount, kcount, desc, codes, lens,
       tables, chunk_bits, chunk_off, outl_idx, summary, q_in, q_slot, perm, sym, patch_s,
@@ -246,6 +246,7 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   TRY(grow(w.big_of, (size_t)nb1 * 4));
   TRY(grow(w.nbig, 16));
   TRY(grow(w.sub_cnt, (size_t)sub_off_size(n, nb1) * 4));
+  TRY(grow(w.chunk_owner, (size_t)(sub_off_size(n, nb1) / 32 + 1) * 4));
   TRY(grow(w.seg_lo, (size_t)segcap * 4));
   TRY(grow(w.seg_cnt, (size_t)segcap * 4));
   TRY(grow(w.seg_meta, (size_t)segcap * 4));
@@ -280,7 +281,8 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
                   P<unsigned long long>(w.keys2), want_perm ? P<uint32_t>(w.idx2) : nullptr,
                   P<unsigned long long>(w.keys), want_perm ? P<uint32_t>(w.idx_alt) : nullptr,
                   P<uint32_t>(w.big_list), P<uint32_t>(w.big_cb), P<int>(w.big_of),
-                  P<uint32_t>(w.nbig), P<uint32_t>(w.sub_cnt), P<uint32_t>(w.seg_lo),
+                  P<uint32_t>(w.nbig), P<uint32_t>(w.sub_cnt), P<uint32_t>(w.chunk_owner),
+                  P<uint32_t>(w.seg_lo),
                   P<uint32_t>(w.seg_cnt),
                   P<uint32_t>(w.seg_meta), P<uint32_t>(w.nseg), sms, s);
   prof_end(c, s);
@@ -290,6 +292,7 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   sa.plan = P<Plan>(w.plan);
   sa.big_list = P<uint32_t>(w.big_list);
   sa.big_cb = P<uint32_t>(w.big_cb);
+  sa.chunk_owner = P<uint32_t>(w.chunk_owner);
   sa.nbig = P<uint32_t>(w.nbig);
   sa.bstart = P<unsigned long long>(w.bstart);
   sa.sub_off = P<uint32_t>(w.sub_cnt);

@@ -63,13 +63,15 @@ void launch_scatter(const unsigned long long *keys, uint64_t n, const Plan *plan
 // level-2 split of the buckets above the split threshold (sub_off: per
 // split bucket, the offset of each sub-bucket) and the unit list of the
 // unsplit buckets and the outlier bucket
-// big_list, big_cb: nb1 + 1 entries; nbig: 4; sub_off: sub_off_size(n, nb1)
+// big_list, big_cb: nb1 + 1 entries; nbig: 4; sub_off: sub_off_size(n, nb1);
+// chunk_owner (split bucket of each 32-digit chunk): sub_off_size / 32
 uint64_t sub_off_size(uint64_t n, uint32_t nb1);
 void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *bstart,
                      unsigned long long *keys, uint32_t *idx, unsigned long long *keys_alt,
                      uint32_t *idx_alt, uint32_t *big_list, uint32_t *big_cb, int *big_of,
-                     uint32_t *nbig, uint32_t *sub_off, uint32_t *u_lo, uint32_t *u_cnt,
-                     uint32_t *u_meta, uint32_t *nunit, int sms, cudaStream_t s);
+                     uint32_t *nbig, uint32_t *sub_off, uint32_t *chunk_owner, uint32_t *u_lo,
+                     uint32_t *u_cnt, uint32_t *u_meta, uint32_t *nunit, int sms,
+                     cudaStream_t s);
 // sorting and segmentation outputs, per sorted slot g: s_rel[g] (relative
 // location deltas), bflag[g] (1 where a block starts), tmp_bid[g] (the block
 // id, at block starts only), perm[g] and q_slot (perm mode)
@@ -98,7 +100,7 @@ void launch_local(const LocalArgs &a, int ctas, cudaStream_t s);
 // runs too large for a warp are appended to the unit list
 struct SubsortArgs {
   const Plan *plan;
-  const uint32_t *big_list, *big_cb, *nbig;
+  const uint32_t *big_list, *big_cb, *chunk_owner, *nbig;
   const unsigned long long *bstart;
   const uint32_t *sub_off;
   const unsigned long long *keys_alt;      // split keys
