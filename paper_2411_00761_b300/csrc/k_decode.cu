@@ -571,14 +571,15 @@ void launch_scan_u64(const unsigned long long *in, uint64_t n, int mode, bool in
 }
 
 // ---------------------------------------------------------------------------
-// block scans of an LCP-S frame, fused: block ids (inclusive scan of the id
-// deltas), counts (inclusive scan of the count deltas) and block starts
-// (exclusive scan of the counts), plus, per tile of kExpTile particles, the
-// block holding the tile's first particle.  Tile aggregates: id sum A, count
+// block scans of an LCP-S frame: block ids (inclusive scan of the id deltas),
+// counts (inclusive scan of the count deltas) and block starts (exclusive
+// scan of the counts).  Here only the bases of each tile of kBsTile blocks
+// are formed; k_expand_blocks applies them.  Tile aggregates: id sum A, count
 // delta sum B, and P = sum of the local inclusive count prefixes, so that the
 // counts of a tile with carry-in C sum to len * C + P.
 // ---------------------------------------------------------------------------
-constexpr int kBsTile = 4096;
+constexpr int kBsTile = 1024;   // blocks per aggregate tile = blocks per expand CTA
+constexpr int kBsThreads = 256;
 constexpr int kExpTile = 1024;
 
 struct BsAgg {
@@ -614,11 +615,11 @@ __device__ __forceinline__ unsigned long long blk_exscan(unsigned long long v,
   return base + x - v;
 }
 
-__global__ void __launch_bounds__(1024) k_bscan_sum(const unsigned long long *__restrict__ sid,
-                                                    const unsigned long long *__restrict__ scnt,
-                                                    uint64_t M, BsAgg *__restrict__ agg) {
+__global__ void __launch_bounds__(kBsThreads) k_bscan_sum(const unsigned long long *__restrict__ sid,
+                                                          const unsigned long long *__restrict__ scnt,
+                                                          uint64_t M, BsAgg *__restrict__ agg) {
   __shared__ unsigned long long s_warp[32];
-  constexpr int per = kBsTile / 1024;
+  constexpr int per = kBsTile / kBsThreads;
   const uint64_t lo = (uint64_t)blockIdx.x * kBsTile + (uint64_t)threadIdx.x * per;
   unsigned long long a = 0, b = 0, d[per];
 #pragma unroll
@@ -632,8 +633,8 @@ __global__ void __launch_bounds__(1024) k_bscan_sum(const unsigned long long *__
     b += d[k];
   }
   unsigned long long ta, tb;
-  blk_exscan<1024>(a, s_warp, ta);
-  unsigned long long run = blk_exscan<1024>(b, s_warp, tb);  // prefix of deltas before me
+  blk_exscan<kBsThreads>(a, s_warp, ta);
+  unsigned long long run = blk_exscan<kBsThreads>(b, s_warp, tb);  // prefix of deltas before me
   unsigned long long p = 0;
 #pragma unroll
   for (int k = 0; k < per; ++k) {
@@ -641,7 +642,7 @@ __global__ void __launch_bounds__(1024) k_bscan_sum(const unsigned long long *__
     if (lo + k < M) p += run;
   }
   unsigned long long tp;
-  blk_exscan<1024>(p, s_warp, tp);
+  blk_exscan<kBsThreads>(p, s_warp, tp);
   if (threadIdx.x == 0) {
     const uint64_t t0 = (uint64_t)blockIdx.x * kBsTile;
     agg[blockIdx.x] = BsAgg{ta, tb, tp, (M - t0) < (uint64_t)kBsTile ? M - t0 : (uint64_t)kBsTile};
@@ -680,79 +681,6 @@ __global__ void __launch_bounds__(1024) k_bscan_top(BsAgg *__restrict__ agg, uin
   }
 }
 
-__global__ void __launch_bounds__(1024) k_bscan_apply(const unsigned long long *__restrict__ sid,
-                                                      const unsigned long long *__restrict__ scnt,
-                                                      uint64_t M, const BsAgg *__restrict__ agg,
-                                                      unsigned long long *__restrict__ bid,
-                                                      unsigned long long *__restrict__ bstart,
-                                                      uint32_t *__restrict__ tile_first,
-                                                      uint64_t nb, int *__restrict__ err) {
-  __shared__ unsigned long long s_warp[32];
-  constexpr int per = kBsTile / 1024;
-  const BsAgg base = agg[blockIdx.x];
-  const uint64_t lo = (uint64_t)blockIdx.x * kBsTile + (uint64_t)threadIdx.x * per;
-  unsigned long long a[per], d[per];
-  unsigned long long sa = 0, sb = 0;
-#pragma unroll
-  for (int k = 0; k < per; ++k) {
-    const uint64_t i = lo + k;
-    a[k] = 0;
-    d[k] = 0;
-    if (i < M) {
-      a[k] = sid[i];
-      d[k] = (unsigned long long)unzigzag(scnt[i]);
-    }
-    sa += a[k];
-    sb += d[k];
-  }
-  unsigned long long tot;
-  unsigned long long ra = base.a + blk_exscan<1024>(sa, s_warp, tot);
-  unsigned long long rd = blk_exscan<1024>(sb, s_warp, tot);  // local count-delta prefix
-  // local counts c_i = carry + local inclusive delta prefix; starts need their
-  // exclusive prefix within the tile
-  unsigned long long cs = 0, lp = rd;
-#pragma unroll
-  for (int k = 0; k < per; ++k) {
-    lp += d[k];
-    if (lo + k < M) cs += base.b + lp;
-  }
-  unsigned long long rs = base.p + blk_exscan<1024>(cs, s_warp, tot);
-  lp = rd;
-#pragma unroll
-  for (int k = 0; k < per; ++k) {
-    const uint64_t i = lo + k;
-    lp += d[k];
-    ra += a[k];
-    if (i < M) {
-      const long long c = (long long)(base.b + lp);
-      bid[i] = ra;
-      bstart[i] = rs;
-      if (c < 1 || (unsigned long long)c > nb || rs + (unsigned long long)c > nb) atomicExch(err, 1);
-      // tiles whose first particle lies in this block
-      const unsigned long long e = rs + (unsigned long long)(c > 0 ? c : 0);
-      if (e <= nb) {
-        for (unsigned long long t = (rs + kExpTile - 1) / kExpTile; t * kExpTile < e; ++t)
-          tile_first[t] = (uint32_t)i;
-      }
-      if (i == M - 1 && e != nb) atomicExch(err, 1);
-      rs += (unsigned long long)(c > 0 ? c : 0);
-    }
-  }
-}
-
-void launch_block_scans(const unsigned long long *sid, const unsigned long long *scnt, uint64_t M,
-                        void *agg, unsigned long long *bid, unsigned long long *bstart,
-                        uint32_t *tile_first, uint64_t nb, int *err, cudaStream_t s) {
-  if (M == 0) return;
-  const uint64_t tiles = (M + kBsTile - 1) / kBsTile;
-  BsAgg *g = reinterpret_cast<BsAgg *>(agg);
-  note_launch();
-  k_bscan_sum<<<(unsigned)tiles, 1024, 0, s>>>(sid, scnt, M, g);
-  note_launch();
-  k_bscan_top<<<1, 1024, 0, s>>>(g, (uint32_t)tiles);
-  note_launch();
-  k_bscan_apply<<<(unsigned)tiles, 1024, 0, s>>>(sid, scnt, M, g, bid, bstart, tile_first, nb, err);
-}
 
 // counts (inclusive scan of count deltas) must be >= 1 and sum to nb
 __global__ void k_check_counts(const unsigned long long *__restrict__ counts, uint64_t m,
@@ -774,207 +702,270 @@ void launch_check_counts(const unsigned long long *counts, uint64_t m,
 }
 
 // ---------------------------------------------------------------------------
-// LCP-S expand + reconstruct: one CTA per tile of kExpTile particles, four
-// consecutive particles per thread
+// LCP-S expand by block tiles (the block scans' last pass fused in): CTA t
+// takes blocks [1024 t, 1024 t + 1024) and the particles they hold, a
+// contiguous slot range [P0, P1).  From the decoded id and count deltas and
+// the tile bases it forms the blocks' ids, counts and starts in shared memory
+// (per-axis block corners by multiply-shift division), then expands the
+// particles in windows of 1024 slots, four consecutive slots per thread:
+// block ordinal by counting start flags, relative codes by a segmented scan
+// (segments at block and chunk starts) carried across windows, values by Q2.
 // ---------------------------------------------------------------------------
-constexpr int kExpThreads = 256;
-constexpr int kExpPer = kExpTile / kExpThreads;
-static_assert(kExpPer == 4, "four particles per thread (one 16-byte load / store)");
+constexpr int kXThreads = 256;
+constexpr int kXPer = kBsTile / kXThreads;  // blocks, then slots, per thread
+static_assert(kXPer == 4 && kExpTile == kXThreads * 4, "four blocks / slots per thread");
 
 template <int D>
-__global__ void __launch_bounds__(kExpThreads) k_expand_s(
-    const Plan *__restrict__ plan, const unsigned long long *__restrict__ bid,
-    const unsigned long long *__restrict__ bstart, uint64_t M, const uint32_t *__restrict__ s_rel,
-    uint64_t nb, uint64_t n, uint32_t log2_chunk, const uint32_t *__restrict__ tile_first,
+__global__ void __launch_bounds__(kXThreads) k_expand_blocks(
+    const Plan *__restrict__ plan, const unsigned long long *__restrict__ sid,
+    const unsigned long long *__restrict__ scnt, uint64_t M, const BsAgg *__restrict__ agg,
+    const uint32_t *__restrict__ s_rel, uint64_t nb, uint64_t n, uint32_t log2_chunk,
     float *__restrict__ out, int32_t *__restrict__ qout, int *__restrict__ err) {
   __shared__ FieldPlan sF[D];
-  __shared__ uint32_t sb_f[kExpTile][D];  // per-axis block corner of the tile's blocks
-  __shared__ __align__(16) uint8_t s_flag[kExpTile];  // a block starts here (not the first)
-  __shared__ uint32_t s_wv[kExpThreads / 32], s_wf[kExpThreads / 32], s_wb[kExpThreads / 32];
-  __shared__ uint32_t s_lp;
+  __shared__ uint32_t sb_f[kBsTile][D];  // per-axis block corners
+  __shared__ unsigned long long s_st[kBsTile];  // absolute block starts
+  __shared__ __align__(16) uint8_t s_flag[kExpTile];
+  __shared__ unsigned long long s_warp[32];
+  __shared__ uint32_t s_wv[kXThreads / 32], s_wf[kXThreads / 32], s_wb[kXThreads / 32];
+  __shared__ uint32_t s_lp, s_cv, s_cb;
   if (threadIdx.x < D) sF[threadIdx.x] = plan->f[threadIdx.x];
   if (threadIdx.x == 0) s_lp = plan->lp;
-  // tiles of kExpTile particles; the chunk size divides the tile, so every
-  // tile starts a chunk (relative locations restart there)
-  const uint64_t cmask = (1ull << log2_chunk) - 1ull;
-  const uint64_t lo = (uint64_t)blockIdx.x * kExpTile;
-  const uint64_t hi = min(nb, lo + kExpTile);
-  const uint64_t first = tile_first[blockIdx.x];
-  reinterpret_cast<uint32_t *>(s_flag)[threadIdx.x] = 0u;
-  __syncthreads();
+  const BsAgg base = agg[blockIdx.x];  // a: id base, b: count carry-in, p: first start
+  const uint64_t b0 = (uint64_t)blockIdx.x * kBsTile + (uint64_t)threadIdx.x * kXPer;
+  // ---- blocks: ids, counts, starts ----
+  unsigned long long a[kXPer], dl[kXPer];
+  unsigned long long sa = 0, sd = 0;
+#pragma unroll
+  for (int j = 0; j < kXPer; ++j) {
+    a[j] = 0ull;
+    dl[j] = 0ull;
+    if (b0 + j < M) {
+      a[j] = sid[b0 + j];
+      dl[j] = (unsigned long long)unzigzag(scnt[b0 + j]);
+    }
+    sa += a[j];
+    sd += dl[j];
+  }
+  unsigned long long tot;
+  unsigned long long ra = base.a + blk_exscan<kXThreads>(sa, s_warp, tot);
+  unsigned long long rd = blk_exscan<kXThreads>(sd, s_warp, tot);
+  unsigned long long cnt[kXPer], cs = 0;
+  {
+    unsigned long long lp = rd;
+#pragma unroll
+    for (int j = 0; j < kXPer; ++j) {
+      lp += dl[j];
+      cnt[j] = base.b + lp;  // the count: carry-in plus the deltas so far
+      if (b0 + j < M) cs += cnt[j];
+    }
+  }
+  unsigned long long L;
+  unsigned long long rs = base.p + blk_exscan<kXThreads>(cs, s_warp, L);
   const uint32_t lp = s_lp;
-  // blocks first + t (at most kExpTile overlap the tile): per-axis block
-  // indices (multiply-shift division, field 0 fastest) and, for t > 0, a
-  // start flag at the block's first particle
+  bool bad = false;
 #pragma unroll
-  for (int j = 0; j < kExpPer; ++j) {
-    const uint32_t t = threadIdx.x + j * kExpThreads;
-    const uint64_t bi = first + t;
-    if (bi < M) {
-      const unsigned long long st = bstart[bi];
-      if (st < hi) {
-        if (t > 0 && st > lo) s_flag[st - lo] = 1;
-        unsigned long long r = bid[bi];
+  for (int j = 0; j < kXPer; ++j) {
+    const uint64_t i = b0 + j;
+    if (i >= M) continue;
+    ra += a[j];
+    const long long c = (long long)cnt[j];
+    if (c < 1 || (unsigned long long)c > nb || rs + (unsigned long long)c > nb) bad = true;
+    if (i == M - 1 && rs + (unsigned long long)(c > 0 ? c : 0) != nb) bad = true;
+    s_st[threadIdx.x * kXPer + j] = rs;
+    unsigned long long r = ra;
 #pragma unroll
-        for (int f = 0; f < D; ++f) {
-          const FieldPlan &F = sF[f];
-          const unsigned long long qd =
-              F.bshift == 255u ? r : (__umul64hi(r, F.bmagic) >> F.bshift);
-          const unsigned long long bf = r - qd * F.bn;
-          sb_f[t][f] = (uint32_t)(bf << lp);
-          r = qd;
-        }
+    for (int f = 0; f < D; ++f) {
+      const FieldPlan &F = sF[f];
+      const unsigned long long qd = F.bshift == 255u ? r : (__umul64hi(r, F.bmagic) >> F.bshift);
+      const unsigned long long bf = r - qd * F.bn;
+      sb_f[threadIdx.x * kXPer + j][f] = (uint32_t)(bf << lp);
+      r = qd;
+    }
+    rs += (unsigned long long)(c > 0 ? c : 0);
+  }
+  if (bad) atomicExch(err, 1);
+  if (threadIdx.x == 0) {
+    s_cv = 0u;
+    s_cb = 0u;
+  }
+  // ---- particles of the tile's blocks: slots [P0, P1) ----
+  const uint64_t P0 = base.p < nb ? base.p : nb;
+  const uint64_t P1 = base.p + L < nb ? base.p + L : nb;
+  const uint64_t cmask = (1ull << log2_chunk) - 1ull;
+  const uint32_t pm = (1u << lp) - 1u;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const bool aligned = (n & 3ull) == 0 && ((((uintptr_t)out) | (uintptr_t)qout) & 15u) == 0;
+  for (uint64_t R0 = P0 & ~3ull; R0 < P1; R0 += kExpTile) {
+    reinterpret_cast<uint32_t *>(s_flag)[threadIdx.x] = 0u;
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kXPer; ++j) {
+      if (b0 + j >= M) continue;
+      const unsigned long long st = s_st[threadIdx.x * kXPer + j];
+      if (st >= R0 && st < R0 + kExpTile) s_flag[st - R0] = 1;
+    }
+    __syncthreads();
+    const uint32_t cv_in = s_cv, cb_in = s_cb;
+    const uint64_t k0 = R0 + (uint64_t)threadIdx.x * 4;
+    const uint32_t flags4 = reinterpret_cast<const uint32_t *>(s_flag)[threadIdx.x];
+    uint32_t x[4], fl[4];
+    const bool full = k0 >= P0 && k0 + 4 <= P1;
+    if (full) {
+      const uint4 v = *reinterpret_cast<const uint4 *>(s_rel + k0);
+      x[0] = v.x;
+      x[1] = v.y;
+      x[2] = v.z;
+      x[3] = v.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) x[j] = (k0 + j >= P0 && k0 + j < P1) ? s_rel[k0 + j] : 0u;
+    }
+    uint32_t tv = 0u, tf = 0u, tb = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint64_t k = k0 + j;
+      const uint32_t f = (flags4 >> (8 * j)) & 1u;
+      fl[j] = f;
+      const bool seg = f || ((k & cmask) == 0);
+      if (seg) {
+        tv = x[j];
+        tf = 1u;
+      } else {
+        tv += x[j];
+      }
+      x[j] = tv;
+      tb += f;
+    }
+    uint32_t cvv = tv, cff = tf, ccc = tb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, cvv, o);
+      const uint32_t g = __shfl_up_sync(0xffffffffu, cff, o);
+      const uint32_t c = __shfl_up_sync(0xffffffffu, ccc, o);
+      if (lane >= o) {
+        if (!cff) cvv += y;
+        cff |= g;
+        ccc += c;
       }
     }
-  }
-  __syncthreads();
-  // this thread's particles k0 .. k0+3: block ordinal = inclusive count of
-  // start flags; relative code = segmented inclusive sum (segments at block
-  // and chunk starts)
-  const uint64_t k0 = lo + (uint64_t)threadIdx.x * kExpPer;
-  uint32_t x[kExpPer], fl[kExpPer];
-  const uint32_t flags4 = reinterpret_cast<const uint32_t *>(s_flag)[threadIdx.x];
-  if (k0 + kExpPer <= hi) {
-    const uint4 v = *reinterpret_cast<const uint4 *>(s_rel + k0);
-    x[0] = v.x;
-    x[1] = v.y;
-    x[2] = v.z;
-    x[3] = v.w;
-  } else {
-#pragma unroll
-    for (int j = 0; j < kExpPer; ++j) x[j] = k0 + j < hi ? s_rel[k0 + j] : 0u;
-  }
-  uint32_t tv = 0u, tf = 0u, tb = 0u;  // thread aggregate: value, has-segment-start, flags
-#pragma unroll
-  for (int j = 0; j < kExpPer; ++j) {
-    const uint64_t k = k0 + j;
-    const uint32_t f = (flags4 >> (8 * j)) & 1u;
-    fl[j] = f;
-    const bool seg = (k == lo) || f || ((k & cmask) == 0);
-    if (seg) {
-      tv = x[j];
-      tf = 1u;
-    } else {
-      tv += x[j];
+    if (lane == 31) {
+      s_wv[w] = cvv;
+      s_wf[w] = cff;
+      s_wb[w] = ccc;
     }
-    x[j] = tv;  // thread-local inclusive segmented sum
-    tb += f;
-  }
-  // exclusive carry from the threads before: (value, flag) segmented, counts plain
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t cv = tv, cf = tf, cc = tb;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, cv, o);
-    const uint32_t g = __shfl_up_sync(0xffffffffu, cf, o);
-    const uint32_t c = __shfl_up_sync(0xffffffffu, cc, o);
-    if (lane >= o) {
-      if (!cf) cv += y;
-      cf |= g;
-      cc += c;
+    __syncthreads();
+    // carry into this warp: the previous window, then warps 0..w-1
+    uint32_t wv = cv_in, wb = cb_in;
+    for (int u = 0; u < w; ++u) {
+      if (s_wf[u]) wv = s_wv[u];
+      else wv += s_wv[u];
+      wb += s_wb[u];
     }
-  }
-  if (lane == 31) {
-    s_wv[w] = cv;
-    s_wf[w] = cf;
-    s_wb[w] = cc;
-  }
-  __syncthreads();
-  // carry-in of warp w: fold warps 0..w-1
-  uint32_t wv = 0u, wf = 0u, wb = 0u;
-  for (int u = 0; u < w; ++u) {
-    if (s_wf[u]) wv = s_wv[u];
-    else wv += s_wv[u];
-    wf |= s_wf[u];
-    wb += s_wb[u];
-  }
-  // exclusive within the warp
-  uint32_t ev = __shfl_up_sync(0xffffffffu, cv, 1);
-  uint32_t ef = __shfl_up_sync(0xffffffffu, cf, 1);
-  uint32_t ec = __shfl_up_sync(0xffffffffu, cc, 1);
-  if (lane == 0) {
-    ev = 0u;
-    ef = 0u;
-    ec = 0u;
-  }
-  const uint32_t inv = ef ? ev : ev + wv;  // carry value into this thread
-  const uint32_t inb = ec + wb;            // start flags before this thread
-  uint32_t blk[kExpPer], rel[kExpPer];
-  {
-    bool seen = false;  // a segment started within this thread so far
-    uint32_t bc = inb;
-#pragma unroll
-    for (int j = 0; j < kExpPer; ++j) {
-      const uint64_t k = k0 + j;
-      const bool seg = (k == lo) || fl[j] || ((k & cmask) == 0);
-      seen |= seg;
-      rel[j] = seen ? x[j] : x[j] + inv;
-      bc += fl[j];
-      blk[j] = bc;
+    uint32_t ev = __shfl_up_sync(0xffffffffu, cvv, 1);
+    uint32_t ef = __shfl_up_sync(0xffffffffu, cff, 1);
+    uint32_t ec = __shfl_up_sync(0xffffffffu, ccc, 1);
+    if (lane == 0) {
+      ev = 0u;
+      ef = 0u;
+      ec = 0u;
     }
-  }
-  const uint32_t pm = (1u << lp) - 1u;
-  const bool full = (k0 + kExpPer <= hi) && ((n & 3ull) == 0) &&
-                    ((((uintptr_t)out) | (uintptr_t)qout) & 15u) == 0;
+    const uint32_t inv = ef ? ev : ev + wv;
+    uint32_t blk[4], rel[4];
+    {
+      bool seen = false;
+      uint32_t bc = ec + wb;
 #pragma unroll
-  for (int f = 0; f < D; ++f) {
-    const uint32_t c8 = sF[f].c8, sticky = sF[f].sticky, qmax = sF[f].qmax;
-    const long long mb = sF[f].mb;
-    const int32_t g1 = sF[f].g1;
-    float r[kExpPer];
-    int32_t q4[kExpPer];
-    bool bad = false;
-#pragma unroll
-    for (int j = 0; j < kExpPer; ++j) {
-      const uint32_t q = sb_f[blk[j]][f] + ((rel[j] >> (f * lp)) & pm);
-      bad |= (k0 + j < hi) && q > qmax;
-      q4[j] = (int32_t)q;
-      r[j] = reconstruct_c((long long)q, c8, mb, sticky, g1, sF[f]);
+      for (int j = 0; j < 4; ++j) {
+        const uint64_t k = k0 + j;
+        seen |= fl[j] || ((k & cmask) == 0);
+        rel[j] = seen ? x[j] : x[j] + inv;
+        bc += fl[j];
+        blk[j] = bc - 1u;  // ordinal of the block holding slot k within the tile
+      }
     }
-    if (bad) atomicExch(err, 1);
-    float *o = out + (uint64_t)f * n + k0;
-    if (full) {
-      *reinterpret_cast<float4 *>(o) = make_float4(r[0], r[1], r[2], r[3]);
-      if (qout)
-        *reinterpret_cast<int4 *>(qout + (uint64_t)f * n + k0) =
-            make_int4(q4[0], q4[1], q4[2], q4[3]);
-    } else {
 #pragma unroll
-      for (int j = 0; j < kExpPer; ++j)
-        if (k0 + j < hi) {
-          o[j] = r[j];
-          if (qout) qout[(uint64_t)f * n + k0 + j] = q4[j];
-        }
+    for (int f = 0; f < D; ++f) {
+      const uint32_t c8 = sF[f].c8, sticky = sF[f].sticky, qmax = sF[f].qmax;
+      const long long mb = sF[f].mb;
+      const int32_t g1 = sF[f].g1;
+      float r[4];
+      int32_t q4[4];
+      bool over = false;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool valid = k0 + j >= P0 && k0 + j < P1;
+        const uint32_t bj = valid ? blk[j] : 0u;
+        const uint32_t q = sb_f[bj < (uint32_t)kBsTile ? bj : 0u][f] + ((rel[j] >> (f * lp)) & pm);
+        over |= valid && (bj >= (uint32_t)kBsTile || q > qmax);
+        q4[j] = (int32_t)q;
+        r[j] = reconstruct_c((long long)q, c8, mb, sticky, g1, sF[f]);
+      }
+      if (over) atomicExch(err, 1);
+      float *o = out + (uint64_t)f * n + k0;
+      if (full && aligned) {
+        *reinterpret_cast<float4 *>(o) = make_float4(r[0], r[1], r[2], r[3]);
+        if (qout)
+          *reinterpret_cast<int4 *>(qout + (uint64_t)f * n + k0) =
+              make_int4(q4[0], q4[1], q4[2], q4[3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (k0 + j >= P0 && k0 + j < P1) {
+            o[j] = r[j];
+            if (qout) qout[(uint64_t)f * n + k0 + j] = q4[j];
+          }
+      }
     }
+    // carries for the next window: the last slot's segmented value and
+    // the start flags seen so far
+    __syncthreads();
+    if (threadIdx.x == kXThreads - 1) {
+      s_cv = rel[3];
+      s_cb = blk[3] + 1u;
+    }
+    __syncthreads();
   }
 }
 
 template <int D>
-static void expand_t(const Plan *plan, const unsigned long long *bid, const unsigned long long *bstart,
-                     uint64_t M, const uint32_t *s_rel, uint64_t nb, uint64_t n,
-                     uint32_t log2_chunk, const uint32_t *tile_first, float *out, int32_t *qout,
-                     int *err, cudaStream_t s) {
-  const uint64_t chunks = (nb + kExpTile - 1) / kExpTile;
-  if (chunks == 0) return;
+static void expand_blocks_t(const Plan *plan, const unsigned long long *sid,
+                            const unsigned long long *scnt, uint64_t M, const BsAgg *agg,
+                            const uint32_t *s_rel, uint64_t nb, uint64_t n, uint32_t log2_chunk,
+                            float *out, int32_t *qout, int *err, cudaStream_t s) {
+  const uint64_t tiles = (M + kBsTile - 1) / kBsTile;
+  if (tiles == 0) return;
   note_launch();
-  k_expand_s<D><<<(unsigned)chunks, kExpThreads, 0, s>>>(plan, bid, bstart, M, s_rel, nb, n,
-                                                        log2_chunk, tile_first, out, qout, err);
+  k_expand_blocks<D><<<(unsigned)tiles, kXThreads, 0, s>>>(plan, sid, scnt, M, agg, s_rel, nb, n,
+                                                          log2_chunk, out, qout, err);
 }
 
-void launch_expand_s(uint32_t d, const Plan *plan, const unsigned long long *bid,
-                     const unsigned long long *bstart, uint64_t M, const uint32_t *s_rel,
-                     uint64_t nb, uint64_t n, uint32_t log2_chunk, const uint32_t *tile_first,
-                     float *out, int32_t *qout, int *err, cudaStream_t s) {
+void launch_expand_blocks(uint32_t d, const Plan *plan, const unsigned long long *sid,
+                          const unsigned long long *scnt, uint64_t M, const void *agg,
+                          const uint32_t *s_rel, uint64_t nb, uint64_t n, uint32_t log2_chunk,
+                          float *out, int32_t *qout, int *err, cudaStream_t s) {
+  const BsAgg *g = reinterpret_cast<const BsAgg *>(agg);
   switch (d) {
-    case 1: expand_t<1>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
-    case 2: expand_t<2>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
-    case 3: expand_t<3>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
-    case 4: expand_t<4>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
-    case 5: expand_t<5>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
-    case 6: expand_t<6>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
-    case 7: expand_t<7>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
-    default: expand_t<8>(plan, bid, bstart, M, s_rel, nb, n, log2_chunk, tile_first, out, qout, err, s); break;
+    case 1: expand_blocks_t<1>(plan, sid, scnt, M, g, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 2: expand_blocks_t<2>(plan, sid, scnt, M, g, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 3: expand_blocks_t<3>(plan, sid, scnt, M, g, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 4: expand_blocks_t<4>(plan, sid, scnt, M, g, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 5: expand_blocks_t<5>(plan, sid, scnt, M, g, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 6: expand_blocks_t<6>(plan, sid, scnt, M, g, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    case 7: expand_blocks_t<7>(plan, sid, scnt, M, g, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
+    default: expand_blocks_t<8>(plan, sid, scnt, M, g, s_rel, nb, n, log2_chunk, out, qout, err, s); break;
   }
+}
+
+// block-tile aggregates and their bases only (the expand applies them)
+void launch_block_bases(const unsigned long long *sid, const unsigned long long *scnt, uint64_t M,
+                        void *agg, cudaStream_t s) {
+  if (M == 0) return;
+  const uint64_t tiles = (M + kBsTile - 1) / kBsTile;
+  BsAgg *g = reinterpret_cast<BsAgg *>(agg);
+  note_launch();
+  k_bscan_sum<<<(unsigned)tiles, kBsThreads, 0, s>>>(sid, scnt, M, g);
+  note_launch();
+  k_bscan_top<<<1, 1024, 0, s>>>(g, (uint32_t)tiles);
 }
 
 // raw outliers of an LCP-S frame go to the last K slots; their codes (for a

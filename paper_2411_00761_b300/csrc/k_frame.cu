@@ -186,7 +186,7 @@ __device__ __forceinline__ void quant_particle(const float *xs, const Plan &P, u
 }
 
 template <int D>
-__global__ void __launch_bounds__(512) k_quantize_s(const float *__restrict__ fields, uint64_t n,
+__global__ void __launch_bounds__(512, 2) k_quantize_s(const float *__restrict__ fields, uint64_t n,
                                                     const Plan *__restrict__ plan, uint32_t nb1,
                                                     uint64_t span,
                                                     unsigned long long *__restrict__ keys,
@@ -202,73 +202,31 @@ __global__ void __launch_bounds__(512) k_quantize_s(const float *__restrict__ fi
   const uint64_t hi = min(n, lo + span);
   const uint32_t shift = sP.part_shift;
   const uint32_t nb = nb1 - 1;
-  const bool vec = ((n & 3ull) == 0) && ((((uintptr_t)fields) & 15u) == 0) && ((lo & 3ull) == 0);
-  if (vec) {
-    // uniform trip count: the bucket counts are aggregated across lanes
-    for (uint64_t b0 = lo; b0 < hi; b0 += 4ull * blockDim.x) {
-      const uint64_t i0 = b0 + 4ull * threadIdx.x;
-      const bool valid = i0 < hi;
-      uint32_t bq[4] = {0u, 0u, 0u, 0u};
-      if (valid) {
-        float xs[4][D];
-#pragma unroll
-        for (int f = 0; f < D; ++f) {
-          float4 v = __ldcs(reinterpret_cast<const float4 *>(fields + (uint64_t)f * n + i0));
-          xs[0][f] = v.x;
-          xs[1][f] = v.y;
-          xs[2][f] = v.z;
-          xs[3][f] = v.w;
-        }
-        unsigned long long k4[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          int32_t qs[D];
-          quant_particle<D>(xs[j], sP, i0 + j, k4[j], qs);
-          bq[j] = (k4[j] & kOutlierBit) ? nb : (uint32_t)(k4[j] >> shift);
-          if (qout) {
-#pragma unroll
-            for (int f = 0; f < D; ++f) qout[(uint64_t)f * n + i0 + j] = qs[f];
-          }
-        }
-        ulonglong2 *kp = reinterpret_cast<ulonglong2 *>(keys + i0);
-        kp[0] = make_ulonglong2(k4[0], k4[1]);
-        kp[1] = make_ulonglong2(k4[2], k4[3]);
-      }
-      // bucket histogram: this thread's particles in bucket bq[0] summed over
-      // the run of lanes sharing it; the others one atomic each
-      uint32_t own = 0u;
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        if (valid && j > 0 && bq[j] != bq[0]) atomicAdd(&s_hist[bq[j]], 1u);
-        own += (valid && bq[j] == bq[0]) ? 1u : 0u;
-      }
-      int leader;
-      uint32_t rank, len;
-      lane_runs(bq[0], valid, leader, rank, len);
-      uint32_t sum = own;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_down_sync(0xffffffffu, sum, o);
-        if ((uint32_t)o < len - rank) sum += y;
-      }
-      if (valid && rank == 0u) atomicAdd(&s_hist[bq[0]], sum);
-    }
-  } else {
-    for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+  // one particle per thread per round (loads coalesced across the warp);
+  // the trip count is uniform so that bucket counts can be aggregated
+  // across lanes: one atomic per run of lanes with the same bucket
+  for (uint64_t b0 = lo; b0 < hi; b0 += blockDim.x) {
+    const uint64_t i = b0 + threadIdx.x;
+    const bool valid = i < hi;
+    uint32_t b = 0u;
+    if (valid) {
       float xs[D];
 #pragma unroll
-      for (int f = 0; f < D; ++f) xs[f] = fields[(uint64_t)f * n + i];
+      for (int f = 0; f < D; ++f) xs[f] = __ldcs(fields + (uint64_t)f * n + i);
       unsigned long long k;
       int32_t qs[D];
       quant_particle<D>(xs, sP, i, k, qs);
-      uint32_t b = (k & kOutlierBit) ? nb : (uint32_t)(k >> shift);
-      atomicAdd(&s_hist[b], 1u);
+      b = (k & kOutlierBit) ? nb : (uint32_t)(k >> shift);
       keys[i] = k;
       if (qout) {
 #pragma unroll
         for (int f = 0; f < D; ++f) qout[(uint64_t)f * n + i] = qs[f];
       }
     }
+    int leader;
+    uint32_t rank, len;
+    lane_runs(b, valid, leader, rank, len);
+    if (valid && rank == 0u) atomicAdd(&s_hist[b], len);
   }
   __syncthreads();
   uint32_t *th = tile_hist + (uint64_t)blockIdx.x * nb1;

@@ -26,7 +26,7 @@ constexpr int kLocalWarps = kLocalThreads / 32;
 constexpr int kCap = kUnitCap;  // keys of a unit sorted in shared memory
 constexpr int kSplitMin = 256;  // buckets above this many keys are split again
 constexpr int kSubMinBits = 5;  // level-2 digit width: about 8 keys per sub-bucket,
-constexpr int kSubMaxBits = 12; // within these bounds
+constexpr int kSubMaxBits = 13; // within these bounds
 constexpr int kSubMax = 1 << kSubMaxBits;
 constexpr int kSplitThreads = 512;
 constexpr int kSplitIlp = 4;    // keys in flight per thread in the split passes

@@ -96,7 +96,7 @@ void note_cuda_error(cudaError_t e, const char *what, int line) {
 
 uint32_t bits_target(uint64_t n) {
   uint32_t b = 0;
-  while (b < 15 && ((2048ull << b) < n)) ++b;
+  while (b < 14 && ((2048ull << b) < n)) ++b;
   return b;
 }
 
@@ -1007,18 +1007,16 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
     }
     prof_end(c, s);
     if (M > 0) {
-      TRY(grow(w.scan_tmp, (M / 4096 + 2) * 32));
-      TRY(grow(w.tmp_pos, (nb / 1024 + 2) * 4));
+      TRY(grow(w.scan_tmp, (M / 1024 + 2) * 32));
       prof_begin(c, "d.block_scans", s);
-      launch_block_scans(P<unsigned long long>(w.s_id), P<unsigned long long>(w.s_cnt), M,
-                         w.scan_tmp.p, P<unsigned long long>(w.bid),
-                         P<unsigned long long>(w.starts), P<uint32_t>(w.tmp_pos), nb, err, s);
+      launch_block_bases(P<unsigned long long>(w.s_id), P<unsigned long long>(w.s_cnt), M,
+                         w.scan_tmp.p, s);
       CK(cudaGetLastError());
       prof_end(c, s);
       prof_begin(c, "d.expand", s);
-      launch_expand_s(h.d, P<Plan>(w.plan), P<unsigned long long>(w.bid),
-                      P<unsigned long long>(w.starts), M, P<uint32_t>(w.s_rel), nb, n,
-                      h.log2_chunk, P<uint32_t>(w.tmp_pos), out, qout, err, s);
+      launch_expand_blocks(h.d, P<Plan>(w.plan), P<unsigned long long>(w.s_id),
+                           P<unsigned long long>(w.s_cnt), M, w.scan_tmp.p,
+                           P<uint32_t>(w.s_rel), nb, n, h.log2_chunk, out, qout, err, s);
       prof_end(c, s);
     }
     launch_outliers_decode(P<Plan>(w.plan), reinterpret_cast<const float *>(in + h.off[3]), h.K,

@@ -200,13 +200,14 @@ void launch_scan_u64(const unsigned long long *in, uint64_t n, int mode, bool in
 void launch_check_counts(const unsigned long long *counts, uint64_t m,
                          const unsigned long long *starts_total, uint64_t nb, int *err, int sms,
                          cudaStream_t s);
-void launch_block_scans(const unsigned long long *sid, const unsigned long long *scnt, uint64_t M,
-                        void *agg, unsigned long long *bid, unsigned long long *bstart,
-                        uint32_t *tile_first, uint64_t nb, int *err, cudaStream_t s);
-void launch_expand_s(uint32_t d, const Plan *plan, const unsigned long long *bid,
-                     const unsigned long long *bstart, uint64_t M, const uint32_t *s_rel,
-                     uint64_t nb, uint64_t n, uint32_t log2_chunk, const uint32_t *tile_first,
-                     float *out, int32_t *qout, int *err, cudaStream_t s);
+// block-tile bases (agg: 32 bytes per 1024 blocks + 32) and the fused
+// expand over block tiles
+void launch_block_bases(const unsigned long long *sid, const unsigned long long *scnt, uint64_t M,
+                        void *agg, cudaStream_t s);
+void launch_expand_blocks(uint32_t d, const Plan *plan, const unsigned long long *sid,
+                          const unsigned long long *scnt, uint64_t M, const void *agg,
+                          const uint32_t *s_rel, uint64_t nb, uint64_t n, uint32_t log2_chunk,
+                          float *out, int32_t *qout, int *err, cudaStream_t s);
 void launch_outliers_decode(const Plan *plan, const float *raw, uint64_t K, uint64_t n, uint32_t d,
                             float *out, int32_t *qout, int sms, cudaStream_t s);
 
