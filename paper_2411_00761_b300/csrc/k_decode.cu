@@ -649,35 +649,28 @@ __global__ void __launch_bounds__(kBsThreads) k_bscan_sum(const unsigned long lo
   }
 }
 
-// tile bases: id base, count carry-in, start base (one CTA)
+// tile bases: id base, count carry-in, start base (one CTA).  Rounds of 1024
+// tiles, one per thread (coalesced; the next round's aggregates loaded
+// before the current one is scanned), with the three running carries.
 __global__ void __launch_bounds__(1024) k_bscan_top(BsAgg *__restrict__ agg, uint32_t tiles) {
   __shared__ unsigned long long s_warp[32];
-  const uint32_t per = (tiles + 1023) / 1024;
-  const uint32_t lo = threadIdx.x * per, hi = min(tiles, lo + per);
-  unsigned long long sa = 0, sb = 0;
-  for (uint32_t t = lo; t < hi; ++t) {
-    sa += agg[t].a;
-    sb += agg[t].b;
-  }
-  unsigned long long tot;
-  unsigned long long ra = blk_exscan<1024>(sa, s_warp, tot);
-  unsigned long long rb = blk_exscan<1024>(sb, s_warp, tot);
-  // totals of counts per tile need the carry-in of each tile
-  unsigned long long st = 0;
-  {
-    unsigned long long cb = rb;
-    for (uint32_t t = lo; t < hi; ++t) {
-      st += agg[t].len * cb + agg[t].p;
-      cb += agg[t].b;
-    }
-  }
-  unsigned long long rs = blk_exscan<1024>(st, s_warp, tot);
-  for (uint32_t t = lo; t < hi; ++t) {
-    const BsAgg g = agg[t];
-    agg[t] = BsAgg{ra, rb, rs, g.len};
-    ra += g.a;
-    rs += g.len * rb + g.p;
-    rb += g.b;
+  unsigned long long ca = 0, cb = 0, cs = 0;  // carries into the round
+  BsAgg cur = threadIdx.x < tiles ? agg[threadIdx.x] : BsAgg{0, 0, 0, 0};
+  for (uint32_t r0 = 0; r0 < tiles; r0 += 1024) {
+    const uint32_t t = r0 + threadIdx.x;
+    const uint32_t tn = t + 1024;
+    const BsAgg nxt = tn < tiles ? agg[tn] : BsAgg{0, 0, 0, 0};
+    unsigned long long ta, tb, ts;
+    const unsigned long long ra = ca + blk_exscan<1024>(cur.a, s_warp, ta);
+    const unsigned long long rb = cb + blk_exscan<1024>(cur.b, s_warp, tb);
+    // the counts of this tile sum to len * (its count carry-in) + p
+    const unsigned long long mine = cur.len * rb + cur.p;
+    const unsigned long long rs = cs + blk_exscan<1024>(mine, s_warp, ts);
+    if (t < tiles) agg[t] = BsAgg{ra, rb, rs, cur.len};
+    ca += ta;
+    cb += tb;
+    cs += ts;
+    cur = nxt;
   }
 }
 
