@@ -48,6 +48,11 @@ WORKLOADS = {
     "md": dict(desc="MD-like frame: 16M particles of a 252^3-cell FCC lattice + N(0, 0.05^2), "
                     "eb = 1e-4 of each field's range, p = 2", n=1 << 24, d=3, eb=1e-4, mode="rel",
                p=2, seed=1),
+    "batched": dict(desc="hybrid batched: 64 Brownian trajectories (FCC start, N log-uniform on "
+                         "[1e4, 4e6], steps N(0, 0.02^2)), eb = 1e-3 absolute, batch 10, LCP-FSM; "
+                         "one time step = all 64 frames compressed then decompressed",
+                    n=0, d=3, eb=1e-3, mode="abs", p=8, seed=3, trajectories=64, frames=50,
+                    batch=10, lanes=8),
     "plain": dict(desc="plain LCP-S frame: 2^20 particles, uniform + 64 Gaussian clusters, "
                        "eb = 1e-3 absolute, p = 8", n=1 << 20, d=3, eb=1e-3, mode="abs", p=8,
                   seed=0),
@@ -205,12 +210,52 @@ def cpu_baseline(name: str, X: np.ndarray, p: int, n_sample: int):
     return S.nbytes, t1 - t0, t2 - t1, len(r["bytes"])
 
 
+def run_reference_batched(args):
+    """The oracle's Algorithm 1 (encode + decode) per step on a bounded sample
+    of the multi-frame workload: the next frame of the smallest trajectory."""
+    from oracle import hybrid
+    from paper_2411_00761_b300 import synth
+    w = WORKLOADS["batched"]
+    sizes = synth.trajectory_sizes(w["trajectories"], 1e4, 4e6, w["seed"])
+    k = int(np.argmin(sizes))
+    steps = args.warmup + args.steps
+    frames = list(synth.brownian_trajectory(sizes[k], steps, w["seed"] + k))
+    rates = []
+    for t in range(steps):
+        pair = frames[max(0, t - 1): t + 1]  # an S frame, then the FSM's choice
+        t0 = time.perf_counter()
+        enc = hybrid.encode_trajectory(pair, w["eb"], w["mode"], w["p"], batch=w["batch"])
+        hybrid.decode_trajectory([b for b, _ in enc])
+        dt = time.perf_counter() - t0
+        if t >= args.warmup:
+            rates.append((sum(x.nbytes for x in pair), dt))
+    t = sum(dt for _, dt in rates) / len(rates)
+    val = sum(b for b, _ in rates) / sum(dt for _, dt in rates) / 1e9
+    line = {
+        "impl": "reference",
+        "metric": "compress/decompress GB/s vs HBM peak at fixed eb + ratio; batched p50/p99 ms",
+        "value": val, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 in, integer codes",
+        "data": "synthetic",
+        "config": {"workload": "batched", "desc": w["desc"], "p": w["p"],
+                   "sample": f"two consecutive frames of the smallest trajectory (n = {sizes[k]})"},
+        "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": "two consecutive frames of the smallest trajectory per step"},
+        "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     name = args.workload
     w = WORKLOADS[name]
+    if name == "batched":
+        return run_reference_batched(args)
     X = make_frame(name, w["seed"])
     n_sample = args.sample or (1 << 18 if w["d"] == 6 else 1 << 19)
     p = w["p"]
@@ -239,6 +284,145 @@ def run_reference(args):
     return 0
 
 
+def batched_start(sizes, seed):
+    """Initial positions of the multi-frame workload (the FCC start of
+    synth.brownian_trajectory, storage order permuted)."""
+    from paper_2411_00761_b300 import synth
+    out = []
+    for k, n in enumerate(sizes):
+        rng = np.random.default_rng(seed + k)
+        order = rng.permutation(n)
+        out.append(synth.fcc_block_start(n, 1.0)[:, order])
+    return out
+
+
+def run_batched(args):
+    """Config 4: per time step, every trajectory's frame in one batched
+    compress call and one batched decompress call (lanes = contexts with their
+    own streams), against one frame per call."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2411_00761_b300 import lcp, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    w = WORKLOADS["batched"]
+    T = w["trajectories"]
+    sizes = synth.trajectory_sizes(T, 1e4, 4e6, w["seed"])
+    steps_total = args.warmup + args.steps
+    if steps_total > w["frames"]:
+        raise SystemExit(f"at most {w['frames']} time steps")
+    # positions on the device (f64), Brownian steps drawn there (seeded)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w["seed"] * 1000 + rank)
+    pos = [torch.from_numpy(p0).to(dev) for p0 in batched_start(sizes, w["seed"] * 100 + rank)]
+    raw = sum(3 * n * 4 for n in sizes)
+    lanes = lcp.Lanes(w["lanes"], local)
+    enc = [lcp.Trajectory(lanes.ctxs[0], batch=w["batch"], p=w["p"]) for _ in sizes]
+    decs = [lcp.Trajectory(lanes.ctxs[0], batch=w["batch"], p=w["p"]) for _ in sizes]
+    outs = [torch.empty(lcp.max_compressed_size(n, 3), dtype=torch.uint8, device=dev)
+            for n in sizes]
+    Ys = [torch.empty((3, n), dtype=torch.float32, device=dev) for n in sizes]
+
+    def frames():
+        return [p.float().contiguous() for p in pos]
+
+    def advance():
+        for p in pos:
+            p.add_(torch.randn(p.shape, generator=gen, device=dev, dtype=torch.float64) * 0.02)
+
+    launches0 = lcp.kernel_launches()
+    t_step, t_c, t_d, csize, nT = [], [], [], 0, 0
+    with ClockSampler(local) as clk:
+        for step in range(steps_total):
+            Xs = frames()
+            torch.cuda.synchronize(dev)
+            if world > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
+            res = lanes.compress([dict(X=Xs[k], eb=w["eb"], mode=w["mode"], p=w["p"],
+                                       method="auto", traj=enc[k], out=outs[k])
+                                  for k in range(T)])
+            t1 = time.perf_counter()
+            lanes.decompress([dict(buf=outs[k], size=res[k]["size"], traj=decs[k], out=Ys[k])
+                              for k in range(T)])
+            torch.cuda.synchronize(dev)
+            t2 = time.perf_counter()
+            if step >= args.warmup:
+                t_step.append((t2 - t0) * 1e3)
+                t_c.append((t1 - t0) * 1e3)
+                t_d.append((t2 - t1) * 1e3)
+                csize += sum(r["size"] for r in res)
+                nT += sum(1 for r in res if r["method"] == "temporal")
+            advance()
+    launches = lcp.kernel_launches() - launches0
+    # the same frames one per call on one context (fresh trajectories, a few steps)
+    seq_ctx = lcp.Context(local)
+    seq_tr = [lcp.Trajectory(seq_ctx, batch=w["batch"], p=w["p"]) for _ in sizes]
+    seq_ms = []
+    for step in range(min(5, args.steps)):
+        Xs = frames()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for k in range(T):
+            seq_ctx.compress(Xs[k], w["eb"], w["mode"], w["p"], method="auto", traj=seq_tr[k],
+                             out=outs[k])
+        torch.cuda.synchronize(dev)
+        seq_ms.append((time.perf_counter() - t0) * 1e3)
+        advance()
+    ms = statistics.mean(t_step)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * raw / (ms * 1e-3) / 1e9
+    pct = lambda v, q: float(np.percentile(np.array(v), q))
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        from oracle import hybrid
+        k_small = int(np.argmin(sizes))
+        Xs = list(synth.brownian_trajectory(sizes[k_small], 10, w["seed"] + k_small))
+        t0 = time.perf_counter()
+        enc_o = hybrid.encode_trajectory(Xs, w["eb"], w["mode"], w["p"], batch=w["batch"])
+        hybrid.decode_trajectory([b for b, _ in enc_o])
+        tcpu = time.perf_counter() - t0
+        cpu = {"value": sum(x.nbytes for x in Xs) / tcpu / 1e9, "unit": "GB/s", "cores": 1,
+               "kind": "oracle",
+               "sample": f"10 frames of the smallest trajectory (n = {sizes[k_small]}), "
+                         "Algorithm 1 encode + decode"}
+    if rank == 0:
+        line = {
+            "metric": "compress/decompress GB/s vs HBM peak at fixed eb + ratio; batched p50/p99 ms",
+            "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 in, integer codes",
+            "data": "synthetic",
+            "config": {"workload": "batched", "desc": w["desc"], "trajectories": T,
+                       "particles_per_step": int(sum(sizes)), "lanes": w["lanes"],
+                       "eb": w["eb"], "eb_mode": w["mode"], "p": w["p"], "batch": w["batch"],
+                       "parallelism": "single GPU, lanes overlap frames",
+                       "l2": f"{raw / 1e9:.2f} GB per step > 126 MB L2 (no flush)"},
+            "p50_ms": pct(t_step, 50), "p99_ms": pct(t_step, 99),
+            "compress_p50_ms": pct(t_c, 50), "compress_p99_ms": pct(t_c, 99),
+            "decompress_p50_ms": pct(t_d, 50), "decompress_p99_ms": pct(t_d, 99),
+            "one_frame_per_call_compress_ms": statistics.mean(seq_ms),
+            "ratio": raw * len(t_step) / max(csize, 1),
+            "temporal_frames_fraction": nT / (T * len(t_step)),
+            "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -255,6 +439,8 @@ def main():
         WORKLOADS[args.workload]["n"] = args.n
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
 
     import torch
     import torch.distributed as dist

@@ -160,6 +160,54 @@ LCP_API lcp_status lcp_traj_create(lcp_ctx *ctx, uint32_t batch_size, uint32_t p
 LCP_API lcp_status lcp_traj_destroy(lcp_traj *traj);
 
 /*
+ * Batched frames (the multi-frame layer around Algorithm 1: all frames of one
+ * time step of many trajectories at once).  lcp_compress_batch runs the jobs
+ * on `lanes` host threads; lane k uses ctxs[k] and streams[k] (streams may be
+ * NULL: every lane then uses the legacy default stream), so
+ * frames of different lanes overlap on the GPU.  Jobs are taken largest first
+ * (n * d) from a shared counter.  Each job is exactly one lcp_compress call:
+ * its bytes equal those of the same call made alone.  Two jobs of one batch
+ * must not share a trajectory.  Per job, status, out_size, chosen and ms
+ * (host wall time of the call) are filled in.  Returns LCP_OK when every job
+ * succeeded, else the status of the first failed job in job order.  The paper
+ * batches frames per trajectory (Sec. "Batch compression"); running many
+ * trajectories' frames concurrently is this library's.
+ */
+typedef struct {
+  lcp_traj *traj;         /* NULL: stateless LCP-S */
+  const float *d_fields;  /* [d][n], device */
+  uint64_t n;
+  uint32_t d;
+  double eb;
+  lcp_eb_mode mode;
+  uint32_t p;
+  lcp_method method;
+  void *d_out;            /* container buffer, out_cap bytes, device */
+  size_t out_cap;
+  size_t out_size;        /* out */
+  lcp_method chosen;      /* out */
+  lcp_status status;      /* out */
+  float ms;               /* out */
+} lcp_compress_job;
+
+typedef struct {
+  lcp_traj *traj;         /* decoder-side trajectory, or NULL for LCP-S frames */
+  const void *d_in;       /* container, device */
+  size_t in_size;
+  float *d_out;           /* [d][n_cap], device */
+  uint64_t n_cap;
+  uint64_t n_out;         /* out */
+  uint32_t d_fields;      /* out */
+  lcp_status status;      /* out */
+  float ms;               /* out */
+} lcp_decompress_job;
+
+LCP_API lcp_status lcp_compress_batch(lcp_ctx *const *ctxs, void *const *streams, int lanes,
+                                      lcp_compress_job *jobs, int njobs);
+LCP_API lcp_status lcp_decompress_batch(lcp_ctx *const *ctxs, void *const *streams, int lanes,
+                                        lcp_decompress_job *jobs, int njobs);
+
+/*
  * Per-kernel timing (tracing).  With profiling on, every entry point records
  * a CUDA event pair on its stream around each major kernel (stage names such
  * as "s.quantize", "s.local_sort", "d.expand").  lcp_ctx_profile_read returns

@@ -318,11 +318,11 @@ void launch_codebook(int ns, const uint32_t *hist, const unsigned long long *max
                      cudaStream_t s) {
   // sort keys, node weights, distances, parents
   const size_t smem = 8ull * kAlpha + 4ull * 2 * kAlpha + 4ull * 2 * kAlpha + 2ull * 2 * kAlpha;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_cb_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  // once per process; thread-safe (function-local static initialization)
+  static const bool attr =
+      cudaFuncSetAttribute(k_cb_build, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+      cudaSuccess;
+  (void)attr;
   uint8_t *lens_k = work;
   uint32_t *maxlen_k = reinterpret_cast<uint32_t *>(work + (size_t)ns * kHalvings * kAlpha);
   note_launch();
@@ -688,12 +688,10 @@ static void encode_stream(const T *vals, uint64_t n, const StreamDesc *desc, con
   note_launch();
   k_chunk_table<<<gt, 256, 0, s>>>(chunk_off, desc, out, summary);
   unsigned ge = (unsigned)std::min<unsigned long long>((chunks + kEncWarps - 1) / kEncWarps, 2ull * sms);
-  static bool attr = false;  // per instantiation
-  if (!attr) {
-    cudaFuncSetAttribute(k_huff_encode<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kEncSmem);
-    attr = true;
-  }
+  static const bool attr =  // once per instantiation, thread-safe
+      cudaFuncSetAttribute(k_huff_encode<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kEncSmem) == cudaSuccess;
+  (void)attr;
   note_launch();
   k_huff_encode<T><<<ge, 32 * kEncWarps, kEncSmem, s>>>(vals, desc, codes, lens, log2_chunk,
                                                          chunk_off, out, summary);

@@ -466,12 +466,10 @@ void launch_decode_streams(int ns, const uint8_t *const *secs, const StreamInfo 
   }
   (void)sms;
   if (jobs.n) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_huff_decode, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kDecStage);
-      attr = true;
-    }
+    static const bool attr =  // once per process, thread-safe
+        cudaFuncSetAttribute(k_huff_decode, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kDecStage) == cudaSuccess;
+    (void)attr;
     note_launch();
     k_huff_decode<<<ctas, 32 * kDecWarps, kDecStage, s>>>(jobs, err);
   }

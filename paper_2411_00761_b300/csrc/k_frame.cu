@@ -239,11 +239,10 @@ static void launch_q(const float *fields, uint64_t n, const Plan *plan, uint32_t
   uint64_t span = (n + tiles - 1) / tiles;
   span = (span + 3) & ~3ull;
   size_t smem = sizeof(uint32_t) * nb1;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_quantize_s<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+  static const bool attr =  // once per instantiation, thread-safe
+      cudaFuncSetAttribute(k_quantize_s<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           200 * 1024) == cudaSuccess;
+  (void)attr;
   note_launch();
   k_quantize_s<D><<<tiles, 512, smem, s>>>(fields, n, plan, nb1, span, keys, tile_hist, q);
 }

@@ -227,11 +227,10 @@ void launch_scatter(const unsigned long long *keys, uint64_t n, const Plan *plan
                     uint32_t *idx_out, cudaStream_t s) {
   uint64_t span = (n + tiles - 1) / tiles;
   span = (span + 3) & ~3ull;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  static const bool attr =  // once per process, thread-safe
+      cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+      cudaSuccess;
+  (void)attr;
   note_launch();
   k_scatter<<<tiles, 512, sizeof(uint32_t) * nb1, s>>>(keys, n, plan, nb1, span, tile_off,
                                                       keys_out, idx_out);
@@ -1271,13 +1270,12 @@ void launch_local(const LocalArgs &a, int ctas, cudaStream_t s) {
   // unit keys, fallback radix counters, stream histogram; unit indices in perm mode
   const size_t base = (size_t)kCap * 8 + 4ull * 256 * kLocalWarps + 4ull * kAlpha;
   const size_t smem = base + (a.perm ? (size_t)kCap * 4 : 0);
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_local<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base);
-    cudaFuncSetAttribute(k_local<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(base + (size_t)kCap * 4));
-    attr = true;
-  }
+  static const bool attr =  // once per process, thread-safe
+      cudaFuncSetAttribute(k_local<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)base) == cudaSuccess &&
+      cudaFuncSetAttribute(k_local<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(base + (size_t)kCap * 4)) == cudaSuccess;
+  (void)attr;
   note_launch();
   if (a.perm) k_local<true><<<ctas, kLocalThreads, smem, s>>>(a);
   else k_local<false><<<ctas, kLocalThreads, smem, s>>>(a);

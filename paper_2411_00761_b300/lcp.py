@@ -47,7 +47,23 @@ SIGNATURES = {
     "lcp_quantize_noalloc": (C.c_int, [_vp, _u64, C.c_float, C.c_float, C.c_float, _vp, _vp, _vp,
                                        C.POINTER(_u64), _vp]),
     "lcp_ctx_profile_read": (C.c_int, [_vp, C.c_char_p, C.POINTER(C.c_float), C.c_int]),
+    "lcp_compress_batch": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp, C.c_int]),
+    "lcp_decompress_batch": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp, C.c_int]),
 }
+
+
+class CompressJob(C.Structure):
+    """lcp_compress_job (include/lcp.h)."""
+    _fields_ = [("traj", _vp), ("d_fields", _vp), ("n", _u64), ("d", _u32), ("eb", C.c_double),
+                ("mode", C.c_int), ("p", _u32), ("method", C.c_int), ("d_out", _vp),
+                ("out_cap", _sz), ("out_size", _sz), ("chosen", C.c_int), ("status", C.c_int),
+                ("ms", C.c_float)]
+
+
+class DecompressJob(C.Structure):
+    """lcp_decompress_job (include/lcp.h)."""
+    _fields_ = [("traj", _vp), ("d_in", _vp), ("in_size", _sz), ("d_out", _vp), ("n_cap", _u64),
+                ("n_out", _u64), ("d_fields", _u32), ("status", C.c_int), ("ms", C.c_float)]
 
 
 class LcpError(RuntimeError):
@@ -231,6 +247,64 @@ class Trajectory:
             self.close()
         except Exception:
             pass
+
+
+class Lanes:
+    """Contexts and CUDA streams for the batch calls: lane k runs its jobs on
+    its own context and stream, so frames of different lanes overlap."""
+
+    def __init__(self, lanes: int, device: int = 0):
+        self.ctxs = [Context(device) for _ in range(lanes)]
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(lanes)]
+        self._c = (_vp * lanes)(*[c.h.value for c in self.ctxs])
+        self._s = (_vp * lanes)(*[st.cuda_stream for st in self.streams])
+
+    def __len__(self):
+        return len(self.ctxs)
+
+    def compress(self, jobs: list[dict]) -> list[dict]:
+        """jobs: dicts with X [d, n] (CUDA float32), eb, mode, p, method, traj
+        (Trajectory or None) and out (uint8 CUDA buffer).  Returns per job the
+        container view, its size, the method used and the call's ms."""
+        arr = (CompressJob * len(jobs))()
+        for j, J in zip(arr, jobs):
+            X = J["X"]
+            assert X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.is_contiguous()
+            j.traj = J["traj"].h.value if J.get("traj") is not None else None
+            j.d_fields = X.data_ptr()
+            j.d, j.n = X.shape
+            j.eb = float(J["eb"])
+            j.mode = _mode(J.get("mode", "abs"))
+            j.p = int(J.get("p", 8))
+            j.method = _method(J.get("method", "spatial"))
+            j.d_out = J["out"].data_ptr()
+            j.out_cap = J["out"].numel()
+        torch.cuda.synchronize()  # inputs written on other streams are complete
+        st = _lib.lcp_compress_batch(self._c, self._s, len(self), arr, len(jobs))
+        res = []
+        for j, J in zip(arr, jobs):
+            res.append(dict(bytes=J["out"][: j.out_size], size=int(j.out_size),
+                            method="temporal" if j.chosen == TEMPORAL else "spatial",
+                            status=int(j.status), ms=float(j.ms)))
+        _check(st, "lcp_compress_batch")
+        return res
+
+    def decompress(self, jobs: list[dict]) -> list[dict]:
+        """jobs: dicts with buf (uint8 CUDA), size, traj (decoder Trajectory or
+        None) and out (float32 CUDA [d, n_cap]).  Returns per job n, d and ms."""
+        arr = (DecompressJob * len(jobs))()
+        for j, J in zip(arr, jobs):
+            j.traj = J["traj"].h.value if J.get("traj") is not None else None
+            j.d_in = J["buf"].data_ptr()
+            j.in_size = int(J["size"])
+            j.d_out = J["out"].data_ptr()
+            j.n_cap = J["out"].shape[-1]
+        torch.cuda.synchronize()
+        st = _lib.lcp_decompress_batch(self._c, self._s, len(self), arr, len(jobs))
+        res = [dict(n=int(j.n_out), d=int(j.d_fields), status=int(j.status), ms=float(j.ms))
+               for j in arr]
+        _check(st, "lcp_decompress_batch")
+        return res
 
 
 def quantize(x: torch.Tensor, m: float, e: float, max_abs: float | None = None, stream=None):
