@@ -53,6 +53,13 @@ WORKLOADS = {
                          "one time step = all 64 frames compressed then decompressed",
                     n=0, d=3, eb=1e-3, mode="abs", p=8, seed=3, trajectories=64, frames=50,
                     batch=10, lanes=8),
+    "serving": dict(desc="serving: 64 producers, Poisson arrivals at 2000 req/s, 50/50 compress / "
+                         "decompress (a decompress replays a retained earlier frame of the same "
+                         "producer); per producer N log-uniform on [1e4, 8e6], xyz of the plain / "
+                         "MD / cosmology generators, eb log-uniform on [1e-5, 1e-2] of the range; "
+                         "frames are the producer's base frame plus a Brownian step",
+                    n=0, d=3, eb=0.0, mode="rel", p=8, seed=4, producers=64, rate=2000.0,
+                    seconds=60.0, warm_seconds=5.0, lanes=8, batch=10, budget_gb=120),
     "plain": dict(desc="plain LCP-S frame: 2^20 particles, uniform + 64 Gaussian clusters, "
                        "eb = 1e-3 absolute, p = 8", n=1 << 20, d=3, eb=1e-3, mode="abs", p=8,
                   seed=0),
@@ -254,7 +261,7 @@ def run_reference(args):
         return 0
     name = args.workload
     w = WORKLOADS[name]
-    if name == "batched":
+    if name in ("batched", "serving"):  # the oracle's Algorithm 1 on a bounded sample
         return run_reference_batched(args)
     X = make_frame(name, w["seed"])
     n_sample = args.sample or (1 << 18 if w["d"] == 6 else 1 << 19)
@@ -423,6 +430,158 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Config 5: the request loop under an open Poisson load; latency is
+    enqueue -> result in device memory (the server's own clock)."""
+    import math
+    import threading
+
+    import torch
+
+    from paper_2411_00761_b300 import lcp, synth
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = WORKLOADS["serving"]
+    seconds = w["seconds"] if args.seconds <= 0 else args.seconds
+    rate = w["rate"] if args.rate <= 0 else args.rate
+    max_pending = 1024  # producers shed load beyond this many unanswered requests
+    rng = np.random.default_rng(w["seed"] + rank)
+    NP = w["producers"]
+    prods = []
+    for k in range(NP):
+        n = int(round(math.exp(rng.uniform(math.log(1e4), math.log(8e6)))))
+        eb = float(math.exp(rng.uniform(math.log(1e-5), math.log(1e-2))))
+        kind = int(rng.integers(0, 3))
+        base = torch.from_numpy(synth.frame_for_request(kind, n, int(rng.integers(0, 2 ** 31)))).to(dev)
+        rngf = base.amax(dim=1) - base.amin(dim=1)
+        sigma = (0.5 * eb * rngf).view(3, 1)  # a step of about half a bin
+        prods.append(dict(n=n, eb=eb, kind=kind, base=base, sigma=sigma))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(w["seed"])
+    srv = lcp.Server(lanes=w["lanes"], batch=w["batch"], hbm_budget=w["budget_gb"] << 30,
+                     device=local)
+    total = w["warm_seconds"] + seconds
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * total * 1.2) + 16))
+    arrivals = arrivals[arrivals < total]
+    who = rng.integers(0, NP, size=arrivals.size)
+    ops = rng.random(arrivals.size) < 0.5  # True: compress
+    pending = []  # (ticket, op, raw bytes, submit wall time, keep-alive tensors)
+    lock = threading.Condition()
+    done_list = []
+    stop = [False]
+
+    def waiter():
+        while True:
+            with lock:
+                while not pending and not stop[0]:
+                    lock.wait()
+                if not pending and stop[0]:
+                    return
+                item = pending.pop(0)
+            r = srv.wait(item[0])
+            done_list.append((item[:4], r))  # the request's tensors are released here
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    gen_stream = torch.cuda.Stream(device=dev)
+    rejected = 0
+    shed = 0
+    launches0 = lcp.kernel_launches()
+    t_start = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for a, k, is_c in zip(arrivals, who, ops):
+            now = time.perf_counter() - t_start
+            if a > now:
+                time.sleep(a - now)
+            P = prods[int(k)]
+            with lock:
+                backlog = len(pending)
+            if backlog >= max_pending:
+                shed += 1
+                continue
+            first, nxt = srv.frames(int(k))
+            if not is_c and nxt > first:
+                f = int(rng.integers(first, nxt))
+                Y = torch.empty((3, P["n"]), dtype=torch.float32, device=dev)
+                tk = srv.submit_decompress(int(k), f, Y)
+                keep = (Y,)
+                op = "decompress"
+            else:
+                with torch.cuda.stream(gen_stream):
+                    P["base"].add_(torch.randn(P["base"].shape, generator=gen, device=dev) *
+                                   P["sigma"])
+                    X = P["base"].contiguous().clone()
+                gen_stream.synchronize()
+                tk = srv.submit_compress(int(k), X, P["eb"], "rel", w["p"])
+                keep = (X,)
+                op = "compress"
+            if tk is None:
+                rejected += 1
+                continue
+            with lock:
+                pending.append((tk, op, 12 * P["n"], a, keep))
+                lock.notify()
+        with lock:
+            stop[0] = True
+            lock.notify()
+        th.join()
+        wall = time.perf_counter() - t_start
+    launches = lcp.kernel_launches() - launches0
+    mem = srv.device_bytes()
+    srv.close()
+    # statistics over requests that arrived after the warm-up
+    warm_ms = w["warm_seconds"] * 1e3
+    lat = {"compress": [], "decompress": []}
+    raw_done, comp_raw, comp_bytes, failed = 0, 0, 0, {}
+    first_t, last_t = None, None
+    for (tk, op, rb, a), r in done_list:
+        if r["status"] != lcp.OK:
+            key = f'{op}:{r["status"]}'
+            failed[key] = failed.get(key, 0) + 1
+            continue
+        if r["enqueue_ms"] < warm_ms:
+            continue
+        lat[op].append(r["done_ms"] - r["enqueue_ms"])
+        raw_done += rb
+        first_t = r["enqueue_ms"] if first_t is None else min(first_t, r["enqueue_ms"])
+        last_t = r["done_ms"] if last_t is None else max(last_t, r["done_ms"])
+        if op == "compress":
+            comp_raw += rb
+            comp_bytes += r["size"]
+    span_s = (last_t - first_t) * 1e-3 if first_t is not None else 1.0
+    allv = lat["compress"] + lat["decompress"]
+    pct = lambda v, q: float(np.percentile(np.array(v), q)) if v else None
+    line = {
+        "metric": "compress/decompress GB/s vs HBM peak at fixed eb + ratio; batched p50/p99 ms",
+        "value": raw_done / span_s / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": len(allv),
+        "warmup": int(sum(1 for _, r in done_list if r["enqueue_ms"] < warm_ms)),
+        "ms_per_step": span_s * 1e3 / max(len(allv), 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 in, integer codes",
+        "data": "synthetic",
+        "config": {"workload": "serving", "desc": w["desc"], "producers": NP,
+                   "offered_rate_req_s": rate, "seconds": seconds, "lanes": w["lanes"],
+                   "max_pending": max_pending,
+                   "batch": w["batch"], "hbm_budget_gb": w["budget_gb"],
+                   "parallelism": "single GPU, lanes overlap requests"},
+        "p50_ms": pct(allv, 50), "p99_ms": pct(allv, 99),
+        "compress_p50_ms": pct(lat["compress"], 50), "compress_p99_ms": pct(lat["compress"], 99),
+        "decompress_p50_ms": pct(lat["decompress"], 50),
+        "decompress_p99_ms": pct(lat["decompress"], 99),
+        "achieved_rate_req_s": len(allv) / span_s, "requests_done": len(allv),
+        "offered": int(arrivals.size), "rejected_by_budget": rejected, "shed": shed,
+        "failed_by_status": failed,
+        "ratio": comp_raw / max(comp_bytes, 1), "server_device_gb": mem / 1e9,
+        "wall_s": wall, "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
+        "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,6 +593,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="override the particle count (small cases)")
+    ap.add_argument("--seconds", type=float, default=0.0, help="serving: measured seconds")
+    ap.add_argument("--rate", type=float, default=0.0, help="serving: offered requests/s")
     args = ap.parse_args()
     if args.n:
         WORKLOADS[args.workload]["n"] = args.n
@@ -441,6 +602,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
 
     import torch
     import torch.distributed as dist

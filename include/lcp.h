@@ -159,6 +159,10 @@ LCP_API lcp_status lcp_select(lcp_ctx *ctx, lcp_traj *traj, const float *d_field
 LCP_API lcp_status lcp_traj_create(lcp_ctx *ctx, uint32_t batch_size, uint32_t p, lcp_traj **out);
 LCP_API lcp_status lcp_traj_destroy(lcp_traj *traj);
 
+/* Device memory a context's workspace / a trajectory's state holds (bytes). */
+LCP_API uint64_t lcp_ctx_device_bytes(const lcp_ctx *ctx);
+LCP_API uint64_t lcp_traj_device_bytes(const lcp_traj *traj);
+
 /*
  * Batched frames (the multi-frame layer around Algorithm 1: all frames of one
  * time step of many trajectories at once).  lcp_compress_batch runs the jobs
@@ -206,6 +210,65 @@ LCP_API lcp_status lcp_compress_batch(lcp_ctx *const *ctxs, void *const *streams
                                       lcp_compress_job *jobs, int njobs);
 LCP_API lcp_status lcp_decompress_batch(lcp_ctx *const *ctxs, void *const *streams, int lanes,
                                         lcp_decompress_job *jobs, int njobs);
+
+/*
+ * Serving: a request loop around the codec.  Producers submit requests as
+ * they arrive; the server runs them on `lanes` host threads, each with its own
+ * context and CUDA stream, so requests of different producers overlap on the
+ * GPU, while one producer's requests run one at a time in submission order.
+ *   - LCP_REQ_COMPRESS codes the producer's next frame (d_fields [d][n],
+ *     device, valid until the request completes) through the producer's
+ *     trajectory: LCP-FSM and Algorithm 1 with batch `batch`, block multiplier
+ *     p (0: 8).  The container is kept on the device (and copied to d_bytes
+ *     when given); the response gives its frame index, size and method.  A
+ *     producer's frames all have one shape.
+ *   - LCP_REQ_DECOMPRESS decodes the producer's frame `frame` into d_out
+ *     [d][n_cap] (device): its batch from the batch's first frame, preceded
+ *     by the batch's anchor when that first frame is LCP-T.  Containers older
+ *     than the last 2 * batch frames are freed (anchors still needed are
+ *     kept); lcp_server_frames gives the decodable range [first, next).
+ *   - Admission: lcp_server_submit returns LCP_ERR_NOMEM when the device
+ *     memory the server holds (workspaces, reference states, containers, and
+ *     what admitted requests may still add) plus this request's worst case
+ *     would exceed hbm_budget (0: no budget).
+ *   - lcp_server_wait blocks until the ticket's request is done and returns
+ *     its response once; times are ms since lcp_server_create (enqueue: at
+ *     submission, start: a lane took it, done: its result is in device memory).
+ * The paper has no serving layer; this is the library's.
+ */
+typedef struct lcp_server lcp_server;
+typedef enum { LCP_REQ_COMPRESS = 0, LCP_REQ_DECOMPRESS = 1 } lcp_req_op;
+typedef struct {
+  lcp_req_op op;
+  uint32_t producer;
+  const float *d_fields;  /* compress */
+  uint64_t n;
+  uint32_t d;
+  double eb;
+  lcp_eb_mode mode;
+  uint32_t p;
+  uint64_t frame;         /* decompress */
+  float *d_out;
+  uint64_t n_cap;
+  void *d_bytes;          /* compress, optional: a copy of the container */
+  size_t bytes_cap;       /* (ERR_CAPACITY in the response when too small) */
+} lcp_request;
+typedef struct {
+  lcp_status status;
+  uint64_t frame;
+  size_t size;
+  lcp_method method;
+  double enqueue_ms, start_ms, done_ms;
+} lcp_response;
+
+LCP_API lcp_status lcp_server_create(int device, int lanes, uint32_t batch, uint64_t hbm_budget,
+                                     lcp_server **out);
+LCP_API lcp_status lcp_server_submit(lcp_server *srv, const lcp_request *req, uint64_t *ticket);
+LCP_API lcp_status lcp_server_wait(lcp_server *srv, uint64_t ticket, lcp_response *out);
+LCP_API lcp_status lcp_server_frames(lcp_server *srv, uint32_t producer, uint64_t *first,
+                                     uint64_t *next);
+LCP_API uint64_t lcp_server_device_bytes(lcp_server *srv);
+LCP_API lcp_status lcp_server_destroy(lcp_server *srv);
 
 /*
  * Per-kernel timing (tracing).  With profiling on, every entry point records

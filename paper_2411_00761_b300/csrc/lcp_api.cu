@@ -576,6 +576,22 @@ lcp_status lcp_ctx_create(int device, lcp_ctx **out) {
   return LCP_OK;
 }
 
+uint64_t lcp_ctx_device_bytes(const lcp_ctx *c) {
+  if (!c) return 0;
+  const DevBuf *bufs = reinterpret_cast<const DevBuf *>(&c->ws);
+  uint64_t b = 0;
+  for (size_t i = 0; i < sizeof(Workspace) / sizeof(DevBuf); ++i) b += bufs[i].cap;
+  return b;
+}
+
+uint64_t lcp_traj_device_bytes(const lcp_traj *t) {
+  if (!t) return 0;
+  const DevBuf *bufs[] = {&t->prev_q, &t->prev_pi, &t->anc_q, &t->anc_pi, &t->new_q, &t->new_pi};
+  uint64_t b = 0;
+  for (const DevBuf *x : bufs) b += x->cap;
+  return b;
+}
+
 lcp_status lcp_ctx_destroy(lcp_ctx *c) {
   if (!c) return LCP_ERR_ARG;
   DeviceGuard g(c->device);

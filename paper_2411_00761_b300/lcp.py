@@ -47,6 +47,14 @@ SIGNATURES = {
     "lcp_quantize_noalloc": (C.c_int, [_vp, _u64, C.c_float, C.c_float, C.c_float, _vp, _vp, _vp,
                                        C.POINTER(_u64), _vp]),
     "lcp_ctx_profile_read": (C.c_int, [_vp, C.c_char_p, C.POINTER(C.c_float), C.c_int]),
+    "lcp_ctx_device_bytes": (_u64, [_vp]),
+    "lcp_traj_device_bytes": (_u64, [_vp]),
+    "lcp_server_create": (C.c_int, [C.c_int, C.c_int, _u32, _u64, C.POINTER(C.c_void_p)]),
+    "lcp_server_submit": (C.c_int, [_vp, _vp, C.POINTER(_u64)]),
+    "lcp_server_wait": (C.c_int, [_vp, _u64, _vp]),
+    "lcp_server_frames": (C.c_int, [_vp, _u32, C.POINTER(_u64), C.POINTER(_u64)]),
+    "lcp_server_device_bytes": (_u64, [_vp]),
+    "lcp_server_destroy": (C.c_int, [_vp]),
     "lcp_compress_batch": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp, C.c_int]),
     "lcp_decompress_batch": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp, C.c_int]),
 }
@@ -58,6 +66,22 @@ class CompressJob(C.Structure):
                 ("mode", C.c_int), ("p", _u32), ("method", C.c_int), ("d_out", _vp),
                 ("out_cap", _sz), ("out_size", _sz), ("chosen", C.c_int), ("status", C.c_int),
                 ("ms", C.c_float)]
+
+
+class Request(C.Structure):
+    """lcp_request (include/lcp.h)."""
+    _fields_ = [("op", C.c_int), ("producer", _u32), ("d_fields", _vp), ("n", _u64), ("d", _u32),
+                ("eb", C.c_double), ("mode", C.c_int), ("p", _u32), ("frame", _u64),
+                ("d_out", _vp), ("n_cap", _u64), ("d_bytes", _vp), ("bytes_cap", _sz)]
+
+
+class Response(C.Structure):
+    """lcp_response (include/lcp.h)."""
+    _fields_ = [("status", C.c_int), ("frame", _u64), ("size", _sz), ("method", C.c_int),
+                ("enqueue_ms", C.c_double), ("start_ms", C.c_double), ("done_ms", C.c_double)]
+
+
+REQ_COMPRESS, REQ_DECOMPRESS = 0, 1
 
 
 class DecompressJob(C.Structure):
@@ -305,6 +329,77 @@ class Lanes:
                for j in arr]
         _check(st, "lcp_decompress_batch")
         return res
+
+
+class Server:
+    """The request loop (lcp_server): producers submit compress / decompress
+    requests, lanes run them; see include/lcp.h."""
+
+    def __init__(self, lanes: int = 8, batch: int = 10, hbm_budget: int = 0, device: int = 0):
+        load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("the LCP library needs a CUDA GPU")
+        h = C.c_void_p()
+        _check(_lib.lcp_server_create(device, lanes, batch, hbm_budget, C.byref(h)),
+               "lcp_server_create")
+        self.h = h
+
+    def submit_compress(self, producer: int, X: torch.Tensor, eb: float, mode="rel",
+                        p: int = 8, out: torch.Tensor | None = None) -> int | None:
+        """Queues the producer's next frame; returns a ticket, or None when the
+        memory budget does not admit it.  X (and out, a uint8 buffer that
+        receives a copy of the container) must stay alive until it is done."""
+        assert X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.is_contiguous()
+        r = Request(op=REQ_COMPRESS, producer=producer, d_fields=X.data_ptr(), n=X.shape[1],
+                    d=X.shape[0], eb=float(eb), mode=_mode(mode), p=p)
+        if out is not None:
+            r.d_bytes = out.data_ptr()
+            r.bytes_cap = out.numel()
+        return self._submit(r)
+
+    def submit_decompress(self, producer: int, frame: int, out: torch.Tensor) -> int | None:
+        """Queues decoding of the producer's frame `frame` into out [d, n]."""
+        assert out.is_cuda and out.dtype == torch.float32 and out.dim() == 2
+        r = Request(op=REQ_DECOMPRESS, producer=producer, frame=frame, d_out=out.data_ptr(),
+                    n_cap=out.shape[1])
+        return self._submit(r)
+
+    def _submit(self, r: Request) -> int | None:
+        t = C.c_uint64(0)
+        st = _lib.lcp_server_submit(self.h, C.byref(r), C.byref(t))
+        if st == ERR_NOMEM:
+            return None
+        _check(st, "lcp_server_submit")
+        return t.value
+
+    def wait(self, ticket: int) -> dict:
+        """Blocks until the request is done; returns its response."""
+        r = Response()
+        _check(_lib.lcp_server_wait(self.h, ticket, C.byref(r)), "lcp_server_wait")
+        return dict(status=r.status, frame=r.frame, size=r.size,
+                    method="temporal" if r.method == TEMPORAL else "spatial",
+                    enqueue_ms=r.enqueue_ms, start_ms=r.start_ms, done_ms=r.done_ms)
+
+    def frames(self, producer: int) -> tuple[int, int]:
+        """Decodable frame range [first, next) of a producer."""
+        a, b = C.c_uint64(0), C.c_uint64(0)
+        _check(_lib.lcp_server_frames(self.h, producer, C.byref(a), C.byref(b)),
+               "lcp_server_frames")
+        return a.value, b.value
+
+    def device_bytes(self) -> int:
+        return int(_lib.lcp_server_device_bytes(self.h))
+
+    def close(self):
+        if self.h:
+            _lib.lcp_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def quantize(x: torch.Tensor, m: float, e: float, max_abs: float | None = None, stream=None):

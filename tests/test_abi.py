@@ -47,16 +47,16 @@ def test_binding_fails_loudly_without_gpu():
         lcp.Context(0)
 
 
-def test_batch_job_structs_match_the_header(tmp_path):
-    """The binding's ctypes job structs have the C layout (sizes and field
-    offsets from the header compiled by gcc)."""
+def test_job_and_request_structs_match_the_header(tmp_path):
+    """The binding's ctypes structs (batch jobs, server requests and
+    responses) have the C layout: sizes and field offsets from the header
+    compiled by gcc."""
     import subprocess
     from paper_2411_00761_b300 import lcp
     probe = tmp_path / "probe.c"
-    fields = {
-        "lcp_compress_job": [f for f, _ in lcp.CompressJob._fields_],
-        "lcp_decompress_job": [f for f, _ in lcp.DecompressJob._fields_],
-    }
+    structs = (("lcp_compress_job", lcp.CompressJob), ("lcp_decompress_job", lcp.DecompressJob),
+               ("lcp_request", lcp.Request), ("lcp_response", lcp.Response))
+    fields = {st: [f for f, _ in cls._fields_] for st, cls in structs}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lcp.h"', "int main(void) {"]
     for st, fs in fields.items():
         lines.append(f'  printf("{st} %zu\\n", sizeof({st}));')
@@ -69,8 +69,7 @@ def test_batch_job_structs_match_the_header(tmp_path):
                    check=True)
     got = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
                                                   check=True).stdout.splitlines())
-    for st, cls in (("lcp_compress_job", lcp.CompressJob),
-                    ("lcp_decompress_job", lcp.DecompressJob)):
+    for st, cls in structs:
         assert int(got[st]) == ctypes.sizeof(cls), st
         for f, _ in cls._fields_:
             assert int(got[f"{st}.{f}"]) == getattr(cls, f).offset, (st, f)
