@@ -30,6 +30,7 @@ constexpr int kSubMaxBits = 13; // within these bounds
 constexpr int kSubMax = 1 << kSubMaxBits;
 constexpr int kSplitThreads = 512;
 constexpr int kSplitIlp = 4;    // keys in flight per thread in the split passes
+constexpr uint32_t kSplitChunk = 32768;  // keys per task when a bucket is split by several CTAs
 constexpr int kSubThreads = 256;
 constexpr int kSubSpan = 16;    // sub-bucket runs: a new run where the offset enters a new span
 
@@ -364,74 +365,207 @@ __device__ __forceinline__ int sub_bits_for(uint64_t cnt, int maxsub) {
 __device__ __forceinline__ uint32_t sub_chunks(int sub) {
   return sub > 5 ? (1u << (sub - 5)) : 1u;  // 32-digit chunks
 }
+// tasks of a split bucket of cnt keys: one up to kSplitChunk keys, else one
+// per kSplitChunk keys
+__device__ __host__ __forceinline__ uint32_t split_tasks(uint32_t cnt) {
+  return cnt > kSplitChunk ? (cnt + kSplitChunk - 1) / kSplitChunk : 1u;
+}
 
 // split buckets: big_list[j] = bucket, big_cb[j] = first 32-digit chunk of
-// its sub-bucket offsets (big_cb[nbig] = all chunks); nbig[0] = split
-// buckets, nbig[1] = work counter, nbig[2] = chunks
+// its sub-bucket offsets (big_cb[nbig] = all chunks), big_tb[j] = its first
+// task (big_tb[nbig] = all tasks), big_hs[j] = first histogram slot of a
+// bucket of several tasks; task_owner[t] and slot_owner[h] = the bucket of
+// task t and of slot h; multi[m] = the m-th bucket of several tasks.
+// nbig: [0] split buckets, [1] work counter, [2] chunks, [3] tasks,
+// [4] buckets of several tasks, [5] histogram slots
 __global__ void __launch_bounds__(1024) k_seg_plan(const Plan *__restrict__ plan, uint32_t nb1,
                                                    const unsigned long long *__restrict__ bstart,
-                                                   uint32_t *__restrict__ big_list,
-                                                   uint32_t *__restrict__ big_cb,
-                                                   int *__restrict__ big_of,
-                                                   uint32_t *__restrict__ nbig) {
+                                                   SegBufs g) {
   __shared__ unsigned long long s_warp[32];
   const Plan &P = *plan;
   const uint32_t nb = nb1 - 1;
   const int maxsub = (int)P.part_shift - (int)P.rel_bits;
   const uint32_t per = (nb1 + 1023) / 1024;
   const uint32_t lo = threadIdx.x * per, hi = min(nb1, lo + per);
-  // (chunks << 32) | buckets
-  unsigned long long c = 0;
+  // c = (chunks << 32) | buckets; e = (tasks << 40) | (slots << 20) | multi
+  unsigned long long c = 0, e = 0;
   for (uint32_t b = lo; b < hi; ++b) {
     const uint64_t cnt = bstart[b + 1] - bstart[b];
-    if (maxsub > 0 && b < nb && cnt > (uint64_t)kSplitMin)
+    if (maxsub > 0 && b < nb && cnt > (uint64_t)kSplitMin) {
       c += ((unsigned long long)sub_chunks(sub_bits_for(cnt, maxsub)) << 32) | 1ull;
+      const unsigned long long T = split_tasks((uint32_t)cnt);
+      e += (T << 40) | (T > 1 ? (T << 20) | 1ull : 0ull);
+    }
   }
-  unsigned long long tot;
+  unsigned long long tot, tote;
   unsigned long long run = block_exscan<1024>(c, s_warp, tot);
+  unsigned long long rune = block_exscan<1024>(e, s_warp, tote);
   for (uint32_t b = lo; b < hi; ++b) {
     const uint64_t cnt = bstart[b + 1] - bstart[b];
     const bool big = maxsub > 0 && b < nb && cnt > (uint64_t)kSplitMin;
     const uint32_t j = (uint32_t)run;
-    big_of[b] = big ? (int)j : -1;
+    g.big_of[b] = big ? (int)j : -1;
     if (big) {
-      big_list[j] = b;
-      big_cb[j] = (uint32_t)(run >> 32);
+      g.big_list[j] = b;
+      g.big_cb[j] = (uint32_t)(run >> 32);
       run += ((unsigned long long)sub_chunks(sub_bits_for(cnt, maxsub)) << 32) | 1ull;
+      const uint32_t T = split_tasks((uint32_t)cnt);
+      const uint32_t tb = (uint32_t)(rune >> 40), hs = (uint32_t)(rune >> 20) & 0xFFFFFu;
+      g.big_tb[j] = tb;
+      g.big_hs[j] = hs;
+      for (uint32_t k = 0; k < T; ++k) g.task_owner[tb + k] = j;
+      if (T > 1) {
+        g.multi[(uint32_t)rune & 0xFFFFFu] = j;
+        for (uint32_t k = 0; k < T; ++k) g.slot_owner[hs + k] = j;
+      }
+      rune += ((unsigned long long)T << 40) | (T > 1 ? ((unsigned long long)T << 20) | 1ull : 0ull);
     }
   }
   if (threadIdx.x == 0) {
-    nbig[0] = (uint32_t)tot;
-    nbig[1] = 0u;  // work counter of k_split_big
-    nbig[2] = (uint32_t)(tot >> 32);
-    big_cb[(uint32_t)tot] = (uint32_t)(tot >> 32);
+    g.nbig[0] = (uint32_t)tot;
+    g.nbig[1] = 0u;  // work counter of k_split_big
+    g.nbig[2] = (uint32_t)(tot >> 32);
+    g.nbig[3] = (uint32_t)(tote >> 40);
+    g.nbig[4] = (uint32_t)tote & 0xFFFFFu;
+    g.nbig[5] = (uint32_t)(tote >> 20) & 0xFFFFFu;
+    g.big_cb[(uint32_t)tot] = (uint32_t)(tot >> 32);
+    g.big_tb[(uint32_t)tot] = (uint32_t)(tote >> 40);
   }
 }
 
-// One CTA per split bucket (fetched from a work counter): sub-bucket
-// histogram, offsets (sub_off[32 * big_cb[j] + digit], within the bucket),
-// scatter.  Loads are issued kSplitIlp at a time.
+// sub-bucket histogram of key range [c0, c1) of a split bucket into h
+// (zeroed by the caller), kSplitIlp loads in flight per thread
+__device__ __forceinline__ void split_count(const unsigned long long *__restrict__ kb,
+                                            uint32_t c0, uint32_t c1, int shift2, uint32_t mask,
+                                            uint32_t *h) {
+  for (uint32_t t0 = c0; t0 < c1; t0 += kSplitThreads * kSplitIlp) {
+    unsigned long long k[kSplitIlp];
+#pragma unroll
+    for (int r = 0; r < kSplitIlp; ++r) {
+      const uint32_t t = t0 + r * kSplitThreads + threadIdx.x;
+      k[r] = t < c1 ? kb[t] : 0ull;
+    }
+#pragma unroll
+    for (int r = 0; r < kSplitIlp; ++r) {
+      const uint32_t t = t0 + r * kSplitThreads + threadIdx.x;
+      const uint32_t dg = (uint32_t)(k[r] >> shift2) & mask;
+      int leader;
+      uint32_t rank, len;
+      lane_runs(dg, t < c1, leader, rank, len);
+      if (t < c1 && rank == 0u) atomicAdd(&h[dg], len);
+    }
+  }
+}
+
+// Buckets of several tasks, pass 1: one kSplitChunk-key task per slot, its
+// sub-bucket histogram stored densely at shist[slot * kSubMax + digit].
+__global__ void __launch_bounds__(kSplitThreads) k_split_hist(
+    const Plan *__restrict__ plan, const unsigned long long *__restrict__ bstart, SegBufs g,
+    const unsigned long long *__restrict__ keys) {
+  __shared__ uint32_t h[kSubMax];
+  const Plan &P = *plan;
+  const int maxsub = (int)P.part_shift - (int)P.rel_bits;
+  const uint32_t nslot = g.nbig[5];
+  for (uint32_t sl = blockIdx.x; sl < nslot; sl += gridDim.x) {
+    for (int d = threadIdx.x; d < kSubMax; d += kSplitThreads) h[d] = 0u;
+    __syncthreads();
+    const uint32_t j = g.slot_owner[sl];
+    const uint64_t lo = bstart[g.big_list[j]];
+    const uint32_t cnt = (uint32_t)(bstart[g.big_list[j] + 1] - lo);
+    const int sub = sub_bits_for(cnt, maxsub);
+    const uint32_t c0 = (sl - g.big_hs[j]) * kSplitChunk;
+    const uint32_t c1 = min(cnt, c0 + kSplitChunk);
+    split_count(keys + lo, c0, c1, (int)P.part_shift - sub, (1u << sub) - 1u, h);
+    __syncthreads();
+    uint32_t *out = g.shist + (uint64_t)sl * kSubMax;
+    for (uint32_t d = threadIdx.x; d < (1u << sub); d += kSplitThreads) out[d] = h[d];
+    __syncthreads();
+  }
+}
+
+// Buckets of several tasks, pass 2 (one CTA per bucket): sub-bucket offsets
+// from the summed task histograms; each task's slot is replaced by its
+// starting position per sub-bucket (the offset plus the earlier tasks'
+// counts).
+__global__ void __launch_bounds__(kSplitThreads) k_split_scan(
+    const Plan *__restrict__ plan, const unsigned long long *__restrict__ bstart, SegBufs g) {
+  constexpr int per = kSubMax / kSplitThreads;
+  __shared__ uint32_t tot[kSubMax];
+  __shared__ unsigned long long s_warp[32];
+  const Plan &P = *plan;
+  const int maxsub = (int)P.part_shift - (int)P.rel_bits;
+  const uint32_t nmulti = g.nbig[4];
+  for (uint32_t m = blockIdx.x; m < nmulti; m += gridDim.x) {
+    const uint32_t j = g.multi[m];
+    const uint32_t b = g.big_list[j];
+    const uint32_t cnt = (uint32_t)(bstart[b + 1] - bstart[b]);
+    const int sub = sub_bits_for(cnt, maxsub);
+    const uint32_t nsub = 1u << sub;
+    const uint32_t T = split_tasks(cnt);
+    uint32_t *hj = g.shist + (uint64_t)g.big_hs[j] * kSubMax;
+    for (uint32_t d = threadIdx.x; d < nsub; d += kSplitThreads) {
+      uint32_t x = 0;
+      for (uint32_t k = 0; k < T; ++k) x += hj[(uint64_t)k * kSubMax + d];
+      tot[d] = x;
+    }
+    __syncthreads();
+    uint32_t c[per];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+      const uint32_t dg = threadIdx.x * per + q;
+      c[q] = dg < nsub ? tot[dg] : 0u;
+      sum += c[q];
+    }
+    unsigned long long all;
+    uint32_t run = (uint32_t)block_exscan<kSplitThreads>(sum, s_warp, all);
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+      const uint32_t dg = threadIdx.x * per + q;
+      if (dg < nsub) tot[dg] = run;
+      run += c[q];
+    }
+    __syncthreads();
+    uint32_t *so = g.sub_off + (uint64_t)g.big_cb[j] * 32u;
+    for (uint32_t d = threadIdx.x; d < nsub; d += kSplitThreads) {
+      uint32_t base = tot[d];
+      so[d] = base;
+      for (uint32_t k = 0; k < T; ++k) {
+        const uint32_t x = hj[(uint64_t)k * kSubMax + d];
+        hj[(uint64_t)k * kSubMax + d] = base;
+        base += x;
+      }
+    }
+    for (uint32_t q = threadIdx.x; q < sub_chunks(sub); q += kSplitThreads)
+      g.chunk_owner[g.big_cb[j] + q] = j;
+    __syncthreads();
+  }
+}
+
+// Split tasks (fetched from a work counter).  A bucket of one task: one CTA
+// builds the sub-bucket histogram and offsets (sub_off[32 * big_cb[j] +
+// digit], within the bucket) and scatters.  A task of a bucket of several:
+// its starting positions come from pass 2, and it scatters its key range.
+// Loads are issued kSplitIlp at a time.
 __global__ void __launch_bounds__(kSplitThreads) k_split_big(
-    const Plan *__restrict__ plan, const unsigned long long *__restrict__ bstart,
-    const uint32_t *__restrict__ big_list, const uint32_t *__restrict__ big_cb,
-    uint32_t *__restrict__ nbig, const unsigned long long *__restrict__ keys,
-    const uint32_t *__restrict__ idx, unsigned long long *__restrict__ keys_out,
-    uint32_t *__restrict__ idx_out, uint32_t *__restrict__ sub_off,
-    uint32_t *__restrict__ chunk_owner) {
+    const Plan *__restrict__ plan, const unsigned long long *__restrict__ bstart, SegBufs g,
+    const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ idx,
+    unsigned long long *__restrict__ keys_out, uint32_t *__restrict__ idx_out) {
   constexpr int per = kSubMax / kSplitThreads;
   __shared__ uint32_t h[kSubMax];
   __shared__ unsigned long long s_warp[32];
-  __shared__ uint32_t s_j;
+  __shared__ uint32_t s_t;
   const Plan &P = *plan;
   const int maxsub = (int)P.part_shift - (int)P.rel_bits;
-  const uint32_t total_big = nbig[0];
+  const uint32_t total = g.nbig[3];
   for (;;) {
-    if (threadIdx.x == 0) s_j = atomicAdd(&nbig[1], 1u);
+    if (threadIdx.x == 0) s_t = atomicAdd(&g.nbig[1], 1u);
     for (int d = threadIdx.x; d < kSubMax; d += kSplitThreads) h[d] = 0u;
     __syncthreads();
-    const uint32_t j = s_j;
-    if (j >= total_big) break;
-    const uint32_t b = big_list[j];
+    const uint32_t t = s_t;
+    if (t >= total) break;
+    const uint32_t j = g.task_owner[t];
+    const uint32_t b = g.big_list[j];
     const uint64_t lo = bstart[b];
     const uint32_t cnt = (uint32_t)(bstart[b + 1] - lo);
     const int sub = sub_bits_for(cnt, maxsub);
@@ -439,73 +573,66 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
     const uint32_t mask = (1u << sub) - 1u;
     const uint32_t nsub = 1u << sub;
     const unsigned long long *kb = keys + lo;
-    for (uint32_t q = threadIdx.x; q < sub_chunks(sub); q += kSplitThreads)
-      chunk_owner[big_cb[j] + q] = j;
-    for (uint32_t t0 = 0; t0 < cnt; t0 += kSplitThreads * kSplitIlp) {
-      unsigned long long k[kSplitIlp];
+    uint32_t c0 = 0, c1 = cnt;
+    if (split_tasks(cnt) == 1u) {
+      for (uint32_t q = threadIdx.x; q < sub_chunks(sub); q += kSplitThreads)
+        g.chunk_owner[g.big_cb[j] + q] = j;
+      split_count(kb, 0u, cnt, shift2, mask, h);
+      __syncthreads();
+      // offsets; thread t owns sub-buckets t*per .. t*per+per-1
+      uint32_t c[per];
+      unsigned long long sum = 0;
 #pragma unroll
-      for (int r = 0; r < kSplitIlp; ++r) {
-        const uint32_t t = t0 + r * kSplitThreads + threadIdx.x;
-        k[r] = t < cnt ? kb[t] : 0ull;
+      for (int q = 0; q < per; ++q) {
+        const uint32_t dg = threadIdx.x * per + q;
+        c[q] = dg < nsub ? h[dg] : 0u;
+        sum += c[q];
       }
+      unsigned long long tot;
+      uint32_t run = (uint32_t)block_exscan<kSplitThreads>(sum, s_warp, tot);
+      uint32_t *so = g.sub_off + (uint64_t)g.big_cb[j] * 32u;
 #pragma unroll
-      for (int r = 0; r < kSplitIlp; ++r) {
-        const uint32_t t = t0 + r * kSplitThreads + threadIdx.x;
-        const uint32_t dg = (uint32_t)(k[r] >> shift2) & mask;
-        int leader;
-        uint32_t rank, len;
-        lane_runs(dg, t < cnt, leader, rank, len);
-        if (t < cnt && rank == 0u) atomicAdd(&h[dg], len);
+      for (int q = 0; q < per; ++q) {
+        const uint32_t dg = threadIdx.x * per + q;
+        if (dg < nsub) {
+          so[dg] = run;
+          h[dg] = run;
+        }
+        run += c[q];
       }
+    } else {
+      const uint32_t k = t - g.big_tb[j];
+      c0 = k * kSplitChunk;
+      c1 = min(cnt, c0 + kSplitChunk);
+      const uint32_t *base = g.shist + ((uint64_t)g.big_hs[j] + k) * kSubMax;
+      for (uint32_t d = threadIdx.x; d < nsub; d += kSplitThreads) h[d] = base[d];
     }
     __syncthreads();
-    // offsets; thread t owns sub-buckets t*per .. t*per+per-1
-    uint32_t c[per];
-    unsigned long long sum = 0;
-#pragma unroll
-    for (int q = 0; q < per; ++q) {
-      const uint32_t dg = threadIdx.x * per + q;
-      c[q] = dg < nsub ? h[dg] : 0u;
-      sum += c[q];
-    }
-    unsigned long long tot;
-    uint32_t run = (uint32_t)block_exscan<kSplitThreads>(sum, s_warp, tot);
-    uint32_t *so = sub_off + (uint64_t)big_cb[j] * 32u;
-#pragma unroll
-    for (int q = 0; q < per; ++q) {
-      const uint32_t dg = threadIdx.x * per + q;
-      if (dg < nsub) {
-        so[dg] = run;
-        h[dg] = run;
-      }
-      run += c[q];
-    }
-    __syncthreads();
-    for (uint32_t t0 = 0; t0 < cnt; t0 += kSplitThreads * kSplitIlp) {
+    for (uint32_t t0 = c0; t0 < c1; t0 += kSplitThreads * kSplitIlp) {
       unsigned long long k[kSplitIlp];
       uint32_t ix[kSplitIlp];
 #pragma unroll
       for (int r = 0; r < kSplitIlp; ++r) {
-        const uint32_t t = t0 + r * kSplitThreads + threadIdx.x;
-        k[r] = t < cnt ? kb[t] : 0ull;
-        ix[r] = (idx_out && t < cnt) ? idx[lo + t] : 0u;
+        const uint32_t u = t0 + r * kSplitThreads + threadIdx.x;
+        k[r] = u < c1 ? kb[u] : 0ull;
+        ix[r] = (idx_out && u < c1) ? idx[lo + u] : 0u;
       }
       uint32_t pos[kSplitIlp];
 #pragma unroll
       for (int r = 0; r < kSplitIlp; ++r) {
-        const uint32_t t = t0 + r * kSplitThreads + threadIdx.x;
+        const uint32_t u = t0 + r * kSplitThreads + threadIdx.x;
         const uint32_t dg = (uint32_t)(k[r] >> shift2) & mask;
         int leader;
         uint32_t rank, len;
-        lane_runs(dg, t < cnt, leader, rank, len);
-        uint32_t base = 0u;
-        if (t < cnt && rank == 0u) base = atomicAdd(&h[dg], len);
-        pos[r] = __shfl_sync(0xffffffffu, base, leader) + rank;
+        lane_runs(dg, u < c1, leader, rank, len);
+        uint32_t bs = 0u;
+        if (u < c1 && rank == 0u) bs = atomicAdd(&h[dg], len);
+        pos[r] = __shfl_sync(0xffffffffu, bs, leader) + rank;
       }
 #pragma unroll
       for (int r = 0; r < kSplitIlp; ++r) {
-        const uint32_t t = t0 + r * kSplitThreads + threadIdx.x;
-        if (t < cnt) {
+        const uint32_t u = t0 + r * kSplitThreads + threadIdx.x;
+        if (u < c1) {
           keys_out[lo + pos[r]] = k[r];
           if (idx_out) idx_out[lo + pos[r]] = ix[r];
         }
@@ -598,19 +725,33 @@ uint64_t sub_off_size(uint64_t n, uint32_t nb1) {
   return nbig * 32 + n / 4 + 64;
 }
 
+// tasks: every split bucket, plus one per kSplitChunk keys
+uint64_t split_tasks_max(uint64_t n, uint32_t nb1) {
+  return std::min<uint64_t>(nb1, n / (kSplitMin + 1) + 1) + n / kSplitChunk + 1;
+}
+// histogram slots: the tasks of the buckets of several tasks (each above
+// kSplitChunk keys), fewer than 2 n / kSplitChunk
+uint64_t split_slots_max(uint64_t n) { return 2 * (n / kSplitChunk) + 2; }
+
 void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *bstart,
                      unsigned long long *keys, uint32_t *idx, unsigned long long *keys_alt,
-                     uint32_t *idx_alt, uint32_t *big_list, uint32_t *big_cb, int *big_of,
-                     uint32_t *nbig, uint32_t *sub_off, uint32_t *chunk_owner, uint32_t *u_lo,
-                     uint32_t *u_cnt, uint32_t *u_meta, uint32_t *nunit, int sms,
-                     cudaStream_t s) {
+                     uint32_t *idx_alt, const SegBufs &g, uint32_t *u_lo, uint32_t *u_cnt,
+                     uint32_t *u_meta, uint32_t *nunit, uint64_t n, int sms, cudaStream_t s) {
   note_launch();
-  k_seg_plan<<<1, 1024, 0, s>>>(plan, nb1, bstart, big_list, big_cb, big_of, nbig);
+  k_seg_plan<<<1, 1024, 0, s>>>(plan, nb1, bstart, g);
+  if (n > kSplitChunk) {  // a bucket may need several tasks
+    const uint64_t mmax = std::min<uint64_t>(nb1, n / (kSplitChunk + 1) + 1);
+    note_launch();
+    k_split_hist<<<(unsigned)std::min<uint64_t>(split_slots_max(n), 4 * sms), kSplitThreads, 0,
+                   s>>>(plan, bstart, g, keys);
+    note_launch();
+    k_split_scan<<<(unsigned)std::min<uint64_t>(mmax, 2 * sms), kSplitThreads, 0, s>>>(plan,
+                                                                                      bstart, g);
+  }
   note_launch();
-  k_split_big<<<4 * sms, kSplitThreads, 0, s>>>(plan, bstart, big_list, big_cb, nbig, keys, idx,
-                                                keys_alt, idx_alt, sub_off, chunk_owner);
+  k_split_big<<<4 * sms, kSplitThreads, 0, s>>>(plan, bstart, g, keys, idx, keys_alt, idx_alt);
   note_launch();
-  k_units_small<<<1, 1024, 0, s>>>(nb1, bstart, big_of, u_lo, u_cnt, u_meta, nunit);
+  k_units_small<<<1, 1024, 0, s>>>(nb1, bstart, g.big_of, u_lo, u_cnt, u_meta, nunit);
 }
 
 // ---------------------------------------------------------------------------

@@ -44,7 +44,7 @@ T *P(DevBuf &b) {
 }
 
 struct Workspace {
-  DevBuf big_list, big_cb, chunk_owner, big_of, nbig, sub_cnt, seg_lo, seg_cnt, seg_meta, nseg, bflag, ftile, fbase;
+  DevBuf big_list, big_cb, big_tb, big_hs, task_owner, slot_owner, multi, shist, chunk_owner, big_of, nbig, sub_cnt, seg_lo, seg_cnt, seg_meta, nseg, bflag, ftile, fbase;
   DevBuf mm, plan, keys, keys2, idx2, idx_alt, tile_hist, btot, bstart, s_rel, tmp_bid, tmp_pos,
       s_id, s_cnt, hist, maxv, nvals, mcount, kcount, desc, codes, lens,
       tables, chunk_bits, chunk_off, outl_idx, summary, q_in, q_slot, perm, sym, patch_s,
@@ -243,8 +243,14 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   const uint64_t segcap = nb1 + n / 128 + 2;
   TRY(grow(w.big_list, (size_t)(nb1 + 1) * 4));
   TRY(grow(w.big_cb, (size_t)(nb1 + 1) * 4));
+  TRY(grow(w.big_tb, (size_t)(nb1 + 1) * 4));
+  TRY(grow(w.big_hs, (size_t)(nb1 + 1) * 4));
+  TRY(grow(w.task_owner, (size_t)split_tasks_max(n, nb1) * 4));
+  TRY(grow(w.slot_owner, (size_t)split_slots_max(n) * 4));
+  TRY(grow(w.multi, (size_t)nb1 * 4));
+  TRY(grow(w.shist, (size_t)split_slots_max(n) * 8192 * 4));
   TRY(grow(w.big_of, (size_t)nb1 * 4));
-  TRY(grow(w.nbig, 16));
+  TRY(grow(w.nbig, 32));
   TRY(grow(w.sub_cnt, (size_t)sub_off_size(n, nb1) * 4));
   TRY(grow(w.chunk_owner, (size_t)(sub_off_size(n, nb1) / 32 + 1) * 4));
   TRY(grow(w.seg_lo, (size_t)segcap * 4));
@@ -277,14 +283,24 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   CK(cudaGetLastError());
   // 6. level-2 split of the large buckets, sorting + segmentation
   prof_begin(c, "s.split", s);
+  SegBufs sg;
+  sg.big_list = P<uint32_t>(w.big_list);
+  sg.big_cb = P<uint32_t>(w.big_cb);
+  sg.big_tb = P<uint32_t>(w.big_tb);
+  sg.big_hs = P<uint32_t>(w.big_hs);
+  sg.task_owner = P<uint32_t>(w.task_owner);
+  sg.slot_owner = P<uint32_t>(w.slot_owner);
+  sg.multi = P<uint32_t>(w.multi);
+  sg.big_of = P<int>(w.big_of);
+  sg.nbig = P<uint32_t>(w.nbig);
+  sg.sub_off = P<uint32_t>(w.sub_cnt);
+  sg.chunk_owner = P<uint32_t>(w.chunk_owner);
+  sg.shist = P<uint32_t>(w.shist);
   launch_segments(P<Plan>(w.plan), nb1, P<unsigned long long>(w.bstart),
                   P<unsigned long long>(w.keys2), want_perm ? P<uint32_t>(w.idx2) : nullptr,
-                  P<unsigned long long>(w.keys), want_perm ? P<uint32_t>(w.idx_alt) : nullptr,
-                  P<uint32_t>(w.big_list), P<uint32_t>(w.big_cb), P<int>(w.big_of),
-                  P<uint32_t>(w.nbig), P<uint32_t>(w.sub_cnt), P<uint32_t>(w.chunk_owner),
-                  P<uint32_t>(w.seg_lo),
-                  P<uint32_t>(w.seg_cnt),
-                  P<uint32_t>(w.seg_meta), P<uint32_t>(w.nseg), sms, s);
+                  P<unsigned long long>(w.keys), want_perm ? P<uint32_t>(w.idx_alt) : nullptr, sg,
+                  P<uint32_t>(w.seg_lo), P<uint32_t>(w.seg_cnt), P<uint32_t>(w.seg_meta),
+                  P<uint32_t>(w.nseg), n, sms, s);
   prof_end(c, s);
   CK(cudaMemsetAsync(w.hist.p, 0, 3ull * kAlpha * 4, s));
   CK(cudaMemsetAsync(w.maxv.p, 0, 4 * 8, s));

@@ -63,15 +63,22 @@ void launch_scatter(const unsigned long long *keys, uint64_t n, const Plan *plan
 // level-2 split of the buckets above the split threshold (sub_off: per
 // split bucket, the offset of each sub-bucket) and the unit list of the
 // unsplit buckets and the outlier bucket
-// big_list, big_cb: nb1 + 1 entries; nbig: 4; sub_off: sub_off_size(n, nb1);
-// chunk_owner (split bucket of each 32-digit chunk): sub_off_size / 32
+// Buffers (device): big_list, big_cb, big_tb, big_hs, big_of: nb1 + 1
+// entries; task_owner: split_tasks_max; slot_owner: split_slots_max; multi:
+// nb1; nbig: 8; sub_off: sub_off_size; chunk_owner (split bucket of each
+// 32-digit chunk): sub_off_size / 32 + 1; shist: split_slots_max * 8192.
+struct SegBufs {
+  uint32_t *big_list, *big_cb, *big_tb, *big_hs, *task_owner, *slot_owner, *multi;
+  int *big_of;
+  uint32_t *nbig, *sub_off, *chunk_owner, *shist;
+};
 uint64_t sub_off_size(uint64_t n, uint32_t nb1);
+uint64_t split_tasks_max(uint64_t n, uint32_t nb1);
+uint64_t split_slots_max(uint64_t n);
 void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *bstart,
                      unsigned long long *keys, uint32_t *idx, unsigned long long *keys_alt,
-                     uint32_t *idx_alt, uint32_t *big_list, uint32_t *big_cb, int *big_of,
-                     uint32_t *nbig, uint32_t *sub_off, uint32_t *chunk_owner, uint32_t *u_lo,
-                     uint32_t *u_cnt, uint32_t *u_meta, uint32_t *nunit, int sms,
-                     cudaStream_t s);
+                     uint32_t *idx_alt, const SegBufs &g, uint32_t *u_lo, uint32_t *u_cnt,
+                     uint32_t *u_meta, uint32_t *nunit, uint64_t n, int sms, cudaStream_t s);
 // sorting and segmentation outputs, per sorted slot g: s_rel[g] (relative
 // location deltas), bflag[g] (1 where a block starts), tmp_bid[g] (the block
 // id, at block starts only), perm[g] and q_slot (perm mode)
