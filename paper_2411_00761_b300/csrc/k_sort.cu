@@ -32,7 +32,8 @@ constexpr int kSplitThreads = 512;
 constexpr int kSplitIlp = 4;    // keys in flight per thread in the split passes
 constexpr uint32_t kSplitChunk = 32768;  // keys per task when a bucket is split by several CTAs
 constexpr int kSubThreads = 256;
-constexpr int kSubSpan = 16;    // sub-bucket runs: a new run where the offset enters a new span
+constexpr int kSubCtas = 5;     // resident k_subsort CTAs per SM (48 registers)
+
 
 // ---------------------------------------------------------------------------
 // block-wide exclusive scan of u64 values held one per thread
@@ -377,7 +378,8 @@ __device__ __host__ __forceinline__ uint32_t split_tasks(uint32_t cnt) {
 // bucket of several tasks; task_owner[t] and slot_owner[h] = the bucket of
 // task t and of slot h; multi[m] = the m-th bucket of several tasks.
 // nbig: [0] split buckets, [1] work counter, [2] chunks, [3] tasks,
-// [4] buckets of several tasks, [5] histogram slots
+// [4] buckets of several tasks, [5] histogram slots, [6] k_subsort's work
+// counter
 __global__ void __launch_bounds__(1024) k_seg_plan(const Plan *__restrict__ plan, uint32_t nb1,
                                                    const unsigned long long *__restrict__ bstart,
                                                    SegBufs g) {
@@ -424,6 +426,7 @@ __global__ void __launch_bounds__(1024) k_seg_plan(const Plan *__restrict__ plan
   if (threadIdx.x == 0) {
     g.nbig[0] = (uint32_t)tot;
     g.nbig[1] = 0u;  // work counter of k_split_big
+    g.nbig[6] = 0u;  // work counter of k_subsort
     g.nbig[2] = (uint32_t)(tot >> 32);
     g.nbig[3] = (uint32_t)(tote >> 40);
     g.nbig[4] = (uint32_t)tote & 0xFFFFFu;
@@ -486,15 +489,17 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_hist(
 // Buckets of several tasks, pass 2 (one CTA per bucket): sub-bucket offsets
 // from the summed task histograms; each task's slot is replaced by its
 // starting position per sub-bucket (the offset plus the earlier tasks'
-// counts).
-__global__ void __launch_bounds__(kSplitThreads) k_split_scan(
+// counts).  Thread t owns digits 8t .. 8t+7, read and written as vectors.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_split_scan(
     const Plan *__restrict__ plan, const unsigned long long *__restrict__ bstart, SegBufs g) {
-  constexpr int per = kSubMax / kSplitThreads;
-  __shared__ uint32_t tot[kSubMax];
+  constexpr int per = kSubMax / kScanThreads;
+  static_assert(per == 8, "two 16-byte vectors per thread");
   __shared__ unsigned long long s_warp[32];
   const Plan &P = *plan;
   const int maxsub = (int)P.part_shift - (int)P.rel_bits;
   const uint32_t nmulti = g.nbig[4];
+  const uint32_t d0 = threadIdx.x * per;
   for (uint32_t m = blockIdx.x; m < nmulti; m += gridDim.x) {
     const uint32_t j = g.multi[m];
     const uint32_t b = g.big_list[j];
@@ -502,43 +507,66 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_scan(
     const int sub = sub_bits_for(cnt, maxsub);
     const uint32_t nsub = 1u << sub;
     const uint32_t T = split_tasks(cnt);
-    uint32_t *hj = g.shist + (uint64_t)g.big_hs[j] * kSubMax;
-    for (uint32_t d = threadIdx.x; d < nsub; d += kSplitThreads) {
-      uint32_t x = 0;
-      for (uint32_t k = 0; k < T; ++k) x += hj[(uint64_t)k * kSubMax + d];
-      tot[d] = x;
-    }
-    __syncthreads();
+    uint32_t *hj = g.shist + (uint64_t)g.big_hs[j] * kSubMax + d0;
+    const bool full = d0 + per <= nsub;  // else only digits below nsub count
     uint32_t c[per];
-    unsigned long long sum = 0;
 #pragma unroll
-    for (int q = 0; q < per; ++q) {
-      const uint32_t dg = threadIdx.x * per + q;
-      c[q] = dg < nsub ? tot[dg] : 0u;
-      sum += c[q];
-    }
-    unsigned long long all;
-    uint32_t run = (uint32_t)block_exscan<kSplitThreads>(sum, s_warp, all);
-#pragma unroll
-    for (int q = 0; q < per; ++q) {
-      const uint32_t dg = threadIdx.x * per + q;
-      if (dg < nsub) tot[dg] = run;
-      run += c[q];
-    }
-    __syncthreads();
-    uint32_t *so = g.sub_off + (uint64_t)g.big_cb[j] * 32u;
-    for (uint32_t d = threadIdx.x; d < nsub; d += kSplitThreads) {
-      uint32_t base = tot[d];
-      so[d] = base;
+    for (int q = 0; q < per; ++q) c[q] = 0u;
+    if (d0 < nsub) {
+#pragma unroll 4
       for (uint32_t k = 0; k < T; ++k) {
-        const uint32_t x = hj[(uint64_t)k * kSubMax + d];
-        hj[(uint64_t)k * kSubMax + d] = base;
-        base += x;
+        const uint32_t *p = hj + (uint64_t)k * kSubMax;
+        if (full) {
+          const uint4 x = reinterpret_cast<const uint4 *>(p)[0];
+          const uint4 y = reinterpret_cast<const uint4 *>(p)[1];
+          c[0] += x.x, c[1] += x.y, c[2] += x.z, c[3] += x.w;
+          c[4] += y.x, c[5] += y.y, c[6] += y.z, c[7] += y.w;
+        } else {
+#pragma unroll
+          for (int q = 0; q < per; ++q)
+            if (d0 + q < nsub) c[q] += p[q];
+        }
       }
     }
-    for (uint32_t q = threadIdx.x; q < sub_chunks(sub); q += kSplitThreads)
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int q = 0; q < per; ++q) sum += c[q];
+    unsigned long long all;
+    uint32_t run = (uint32_t)block_exscan<kScanThreads>(sum, s_warp, all);
+    uint32_t o[per];
+#pragma unroll
+    for (int q = 0; q < per; ++q) {
+      o[q] = run;
+      run += c[q];
+    }
+    if (d0 < nsub) {
+      uint32_t *so = g.sub_off + (uint64_t)g.big_cb[j] * 32u + d0;
+#pragma unroll
+      for (int q = 0; q < per; ++q)
+        if (full || d0 + q < nsub) so[q] = o[q];
+#pragma unroll 4
+      for (uint32_t k = 0; k < T; ++k) {
+        uint32_t *p = hj + (uint64_t)k * kSubMax;
+        if (full) {
+          const uint4 x = reinterpret_cast<const uint4 *>(p)[0];
+          const uint4 y = reinterpret_cast<const uint4 *>(p)[1];
+          reinterpret_cast<uint4 *>(p)[0] = make_uint4(o[0], o[1], o[2], o[3]);
+          reinterpret_cast<uint4 *>(p)[1] = make_uint4(o[4], o[5], o[6], o[7]);
+          o[0] += x.x, o[1] += x.y, o[2] += x.z, o[3] += x.w;
+          o[4] += y.x, o[5] += y.y, o[6] += y.z, o[7] += y.w;
+        } else {
+#pragma unroll
+          for (int q = 0; q < per; ++q)
+            if (d0 + q < nsub) {
+              const uint32_t x = p[q];
+              p[q] = o[q];
+              o[q] += x;
+            }
+        }
+      }
+    }
+    for (uint32_t q = threadIdx.x; q < sub_chunks(sub); q += kScanThreads)
       g.chunk_owner[g.big_cb[j] + q] = j;
-    __syncthreads();
   }
 }
 
@@ -745,8 +773,8 @@ void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *b
     k_split_hist<<<(unsigned)std::min<uint64_t>(split_slots_max(n), 4 * sms), kSplitThreads, 0,
                    s>>>(plan, bstart, g, keys);
     note_launch();
-    k_split_scan<<<(unsigned)std::min<uint64_t>(mmax, 2 * sms), kSplitThreads, 0, s>>>(plan,
-                                                                                      bstart, g);
+    k_split_scan<<<(unsigned)std::min<uint64_t>(mmax, sms), kScanThreads, 0, s>>>(plan, bstart,
+                                                                                 g);
   }
   note_launch();
   k_split_big<<<4 * sms, kSplitThreads, 0, s>>>(plan, bstart, g, keys, idx, keys_alt, idx_alt);
@@ -818,6 +846,22 @@ __device__ __forceinline__ void warp_bitonic(T (&v)[R], uint32_t kmax = 32u * R)
           }
         }
       }
+    }
+  }
+}
+
+// the same network for one element per lane, every stage unrolled
+template <typename T>
+__device__ __forceinline__ void warp_bitonic32(T &v) {
+  const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+  for (uint32_t k = 2; k <= 32; k <<= 1) {
+    const bool up = (lane & k) == 0;
+#pragma unroll
+    for (uint32_t lj = k / 2; lj >= 1; lj >>= 1) {
+      const bool keep_max = ((lane & lj) == 0) != up;
+      const T o = shfl_x(v, (int)lj);
+      if (key_lt(o, v) != keep_max) v = o;
     }
   }
 }
@@ -958,10 +1002,12 @@ __device__ __forceinline__ void seg_emit(const SegOut &o, bool valid, uint64_t g
 // ---------------------------------------------------------------------------
 // sub-bucket runs of the split buckets: one warp per run, sorted and
 // segmented in registers.  Warp tasks are 32 consecutive sub-buckets of a
-// split bucket; a run starts at the first non-empty sub-bucket of the task
-// and wherever a sub-bucket's offset enters a new kSubSpan-slot span, so a
-// run holds fewer than kSubSpan particles plus its last sub-bucket.  A run
-// of more than kRunCap particles becomes a k_local unit.
+// split bucket.  Runs are packed greedily: a run opens at a non-empty
+// sub-bucket, takes the smallest window of 32, 64 or kRunCap slots that
+// holds it, and adds the following sub-buckets while they fit.  Sorting a
+// run of whole sub-buckets sorts each of them, since the sub-buckets are
+// ordered by digit.  A sub-bucket of more than kRunCap particles becomes a
+// k_local unit.
 // ---------------------------------------------------------------------------
 constexpr int kRunCap = 128;
 
@@ -977,7 +1023,9 @@ __device__ __forceinline__ void sub_run_r(const unsigned long long *ks, const ui
     const int i = lane * R + r;
     v[r] = i < c ? win_make<MODE>(ks[i], PERM ? is[i] : 0u, base) : win_pad<MODE>();
   }
-  if (c > 1) {
+  if constexpr (R == 1) {
+    warp_bitonic32(v[0]);
+  } else {
     uint32_t kmax = 2u;
     while (kmax < (uint32_t)c) kmax <<= 1;
     warp_bitonic<R>(v, kmax);
@@ -1006,7 +1054,7 @@ __device__ __forceinline__ void sub_run(const unsigned long long *ks, const uint
 }
 
 template <bool PERM>
-__global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
+__global__ void __launch_bounds__(kSubThreads, kSubCtas) k_subsort(SubsortArgs A) {
   __shared__ uint32_t s_hist[kAlpha];
   __shared__ unsigned long long s_max;
   __shared__ int s_status;
@@ -1041,7 +1089,12 @@ __global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
   unsigned long long my_max = 0ull;
   const uint32_t ntask = s_nchunk;
   const uint32_t warps = gridDim.x * (kSubThreads / 32);
-  for (uint32_t t = blockIdx.x * (kSubThreads / 32) + (threadIdx.x >> 5); t < ntask; t += warps) {
+  // first task by warp id, then from a work counter; the next index is
+  // fetched while the current task runs
+  uint32_t tn = 0u;
+  for (uint32_t t = blockIdx.x * (kSubThreads / 32) + (threadIdx.x >> 5); t < ntask;
+       t = __shfl_sync(0xffffffffu, tn, 0)) {
+    if (lane == 0) tn = warps + atomicAdd(&A.nbig[6], 1u);
     const uint32_t j = A.chunk_owner[t], ch = t - A.big_cb[j];
     const uint32_t b = A.big_list[j];
     const uint64_t lo = A.bstart[b];
@@ -1057,35 +1110,36 @@ __global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
     const uint32_t c = nx - off;
     const uint32_t ne = __ballot_sync(0xffffffffu, c > 0);
     if (!ne) continue;
-    const uint32_t pv = __shfl_up_sync(0xffffffffu, off, 1);
-    const bool cut =
-        c > 0 && ((uint32_t)lane == (uint32_t)(__ffs(ne) - 1) || off / kSubSpan != pv / kSubSpan);
-    uint32_t M = __ballot_sync(0xffffffffu, cut);
-    const uint32_t chunk_end = __shfl_sync(0xffffffffu, nx, 31);
     const unsigned long long bucket_base = (unsigned long long)b << part_shift;
     const unsigned long long *ks = A.keys_alt + lo;
     const uint32_t *is = PERM ? A.idx_alt + lo : nullptr;
-    while (M) {
-      const int l0 = __ffs(M) - 1;
-      M &= M - 1u;
-      const int l1 = M ? __ffs(M) - 1 : 32;
+    int l0 = __ffs(ne) - 1;
+    while (l0 >= 0) {
+      // a run: from sub-bucket l0, whole sub-buckets while the run fits the
+      // smallest window of 32, 64 or 128 slots that holds sub-bucket l0
       const uint32_t w0 = __shfl_sync(0xffffffffu, off, l0);
-      const uint32_t wend = __shfl_sync(0xffffffffu, off, l1 & 31);
-      const uint32_t w1 = l1 == 32 ? chunk_end : wend;
+      const uint32_t c0 = __shfl_sync(0xffffffffu, c, l0);
+      const uint32_t cap = c0 <= 32u ? 32u : (c0 <= 64u ? 64u : (uint32_t)kRunCap);
+      const uint32_t fit = __ballot_sync(0xffffffffu, lane >= l0 && nx - w0 <= cap);
+      const int L = fit ? 31 - __clz(fit) : l0;
+      const uint32_t w1 = __shfl_sync(0xffffffffu, nx, L);
+      const uint32_t upto = L == 31 ? 0xffffffffu : ((2u << L) - 1u);
+      const uint32_t rest = ne & ~upto;
+      const int l_next = rest ? __ffs(rest) - 1 : -1;
       const int wc = (int)(w1 - w0);
-      if (wc > kRunCap) {
+      if (c0 > (uint32_t)kRunCap) {  // one sub-bucket too large for a warp: a k_local unit
         if (lane == 0) {
           const uint32_t u = atomicAdd(A.nunit, 1u);
           A.u_lo[u] = (uint32_t)(lo + w0);
           A.u_cnt[u] = (uint32_t)wc;
           A.u_meta[u] = 1u;  // keys in the level-2 buffer
         }
+        l0 = l_next;
         continue;
       }
-      // digits of the run: l0 .. last non-empty lane before l1
-      const uint32_t below = l1 == 32 ? ne : (ne & ((1u << l1) - 1u));
+      // digits of the run: [g0, g1), g1 one past its last non-empty sub-bucket
       const uint32_t g0 = ch * 32u + (uint32_t)l0;
-      const uint32_t g1 = ch * 32u + (uint32_t)(32 - __clz(below));
+      const uint32_t g1 = ch * 32u + (uint32_t)(32 - __clz(ne & upto));
       const unsigned long long base = bucket_base | ((unsigned long long)g0 << shift2);
       const int mode = window_mode((unsigned long long)(g1 - g0) << shift2, PERM);
       const uint64_t g = lo + w0;
@@ -1099,6 +1153,7 @@ __global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
           else sub_run<3, true>(ks + w0, is + w0, wc, base, g, o, s_hist, my_max);
         }
       }
+      l0 = l_next;
     }
   }
   __syncthreads();
@@ -1111,8 +1166,8 @@ __global__ void __launch_bounds__(kSubThreads) k_subsort(SubsortArgs A) {
 
 void launch_subsort(const SubsortArgs &a, int sms, cudaStream_t s) {
   note_launch();
-  if (a.perm) k_subsort<true><<<8 * sms, kSubThreads, 0, s>>>(a);
-  else k_subsort<false><<<8 * sms, kSubThreads, 0, s>>>(a);
+  if (a.perm) k_subsort<true><<<kSubCtas * sms, kSubThreads, 0, s>>>(a);
+  else k_subsort<false><<<kSubCtas * sms, kSubThreads, 0, s>>>(a);
 }
 
 // ---------------------------------------------------------------------------

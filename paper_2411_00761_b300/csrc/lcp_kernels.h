@@ -107,7 +107,8 @@ void launch_local(const LocalArgs &a, int ctas, cudaStream_t s);
 // runs too large for a warp are appended to the unit list
 struct SubsortArgs {
   const Plan *plan;
-  const uint32_t *big_list, *big_cb, *chunk_owner, *nbig;
+  const uint32_t *big_list, *big_cb, *chunk_owner;
+  uint32_t *nbig;  // [6]: work counter (zeroed by the split)
   const unsigned long long *bstart;
   const uint32_t *sub_off;
   const unsigned long long *keys_alt;      // split keys
