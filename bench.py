@@ -116,12 +116,18 @@ def stage_bytes(stage: str, N, D, M, K, C):
     return table.get(stage, 0)
 
 
-# DRAM traffic of a stage's kernel from a committed ncu summary (a smaller
-# frame of the same workload), scaled by the particle count; None unless the
-# kernel source still has the hash recorded at capture
+# DRAM traffic of a stage's kernels from a committed ncu summary (a smaller
+# frame of the same workload), summed over the kernels the summary lists and
+# scaled by the particle count; None unless every listed source file still
+# has the hash recorded at capture
+_SORT = ("paper_2411_00761_b300/csrc/k_sort.cu",)
 TRAFFIC_PROFILES = {
-    ("cosmology", "s.subsort"): ("profiles/k_subsort_cosmology_16M.md",
-                                 "paper_2411_00761_b300/csrc/k_sort.cu", 16777216),
+    ("cosmology", "s.subsort"): ("profiles/k_subsort_cosmology_16M.md", _SORT, 16777216),
+    ("cosmology", "s.split"): ("profiles/k_split_cosmology_16M.md", _SORT, 16777216),
+    ("cosmology", "s.scatter"): ("profiles/k_scatter_cosmology_16M.md", _SORT, 16777216),
+    ("cosmology", "d.expand"): ("profiles/k_expand_blocks_cosmology_16M.md",
+                                ("paper_2411_00761_b300/csrc/k_decode.cu",
+                                 "paper_2411_00761_b300/csrc/lcp_common.cuh"), 16777216),
 }
 
 
@@ -131,17 +137,20 @@ def measured_traffic(workload: str, stage: str, N: int):
     ent = TRAFFIC_PROFILES.get((workload, stage))
     if ent is None:
         return None
-    prof, src, n_cap = ent
+    prof, srcs, n_cap = ent
     try:
         text = open(os.path.join(ROOT, prof)).read()
-        h = hashlib.sha1(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
-        if h not in text:
-            return None
+        for src in srcs:
+            h = hashlib.sha1(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+            if h not in text:
+                return None
         units = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
         tot = 0.0
         for key in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
-            m = re.search(r"`" + re.escape(key) + r"`\) \| ([0-9.]+) \| (\w+)", text)
-            tot += float(m.group(1)) * units[m.group(2)]
+            ms = list(re.finditer(r"`" + re.escape(key) + r"`\) \| ([0-9.]+) \| (\w+)", text))
+            if not ms:
+                return None
+            tot += sum(float(m.group(1)) * units[m.group(2)] for m in ms)
         return tot * N / n_cap
     except Exception:
         return None

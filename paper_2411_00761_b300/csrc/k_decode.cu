@@ -647,8 +647,30 @@ __global__ void __launch_bounds__(kBsThreads) k_bscan_sum(const unsigned long lo
   }
 }
 
-// tile bases: id base, count carry-in, start base (one CTA).  Rounds of 1024
-// tiles, one per thread (coalesced; the next round's aggregates loaded
+// Two-level tile bases.  Level 1: CTA c scans the aggregates of tiles
+// [1024 c, 1024 c + 1024), one per thread, coalesced; each tile's aggregate
+// is replaced by its bases within the chunk (id base, count carry-in, start
+// base, and the chunk's blocks before it), and the chunk's own aggregate goes
+// to cagg[c].  Level 2 (k_bscan_top) scans the chunk aggregates.  A tile's
+// start base is then the chunk's start base + the chunk's count carry-in x
+// the chunk's blocks before the tile + the tile's start base in the chunk.
+constexpr int kBsChunk = 1024;
+__global__ void __launch_bounds__(kBsChunk) k_bscan_chunk(BsAgg *__restrict__ agg, uint32_t tiles,
+                                                          BsAgg *__restrict__ cagg) {
+  __shared__ unsigned long long s_warp[32];
+  const uint32_t t = blockIdx.x * kBsChunk + threadIdx.x;
+  const BsAgg g = t < tiles ? agg[t] : BsAgg{0, 0, 0, 0};
+  unsigned long long ta, tb, tl, ts;
+  const unsigned long long ra = blk_exscan<kBsChunk>(g.a, s_warp, ta);
+  const unsigned long long rb = blk_exscan<kBsChunk>(g.b, s_warp, tb);
+  const unsigned long long rl = blk_exscan<kBsChunk>(g.len, s_warp, tl);
+  const unsigned long long rs = blk_exscan<kBsChunk>(g.len * rb + g.p, s_warp, ts);
+  if (t < tiles) agg[t] = BsAgg{ra, rb, rs, rl};
+  if (threadIdx.x == 0) cagg[blockIdx.x] = BsAgg{ta, tb, ts, tl};
+}
+
+// chunk bases: id base, count carry-in, start base (one CTA).  Rounds of
+// 1024 chunks, one per thread (coalesced; the next round's aggregates loaded
 // before the current one is scanned), with the three running carries.
 __global__ void __launch_bounds__(1024) k_bscan_top(BsAgg *__restrict__ agg, uint32_t tiles) {
   __shared__ unsigned long long s_warp[32];
@@ -707,11 +729,12 @@ constexpr int kXPer = kBsTile / kXThreads;  // blocks, then slots, per thread
 static_assert(kXPer == 4 && kExpTile == kXThreads * 4, "four blocks / slots per thread");
 
 template <int D>
-__global__ void __launch_bounds__(kXThreads) k_expand_blocks(
+__global__ void __launch_bounds__(kXThreads, 3) k_expand_blocks(
     const Plan *__restrict__ plan, const unsigned long long *__restrict__ sid,
     const unsigned long long *__restrict__ scnt, uint64_t M, const BsAgg *__restrict__ agg,
-    const uint32_t *__restrict__ s_rel, uint64_t nb, uint64_t n, uint32_t log2_chunk,
-    float *__restrict__ out, int32_t *__restrict__ qout, int *__restrict__ err) {
+    const BsAgg *__restrict__ cagg, const uint32_t *__restrict__ s_rel, uint64_t nb, uint64_t n,
+    uint32_t log2_chunk, float *__restrict__ out, int32_t *__restrict__ qout,
+    int *__restrict__ err) {
   __shared__ FieldPlan sF[D];
   __shared__ uint32_t sb_f[kBsTile][D];  // per-axis block corners
   __shared__ unsigned long long s_st[kBsTile];  // absolute block starts
@@ -721,7 +744,13 @@ __global__ void __launch_bounds__(kXThreads) k_expand_blocks(
   __shared__ uint32_t s_lp, s_cv, s_cb;
   if (threadIdx.x < D) sF[threadIdx.x] = plan->f[threadIdx.x];
   if (threadIdx.x == 0) s_lp = plan->lp;
-  const BsAgg base = agg[blockIdx.x];  // a: id base, b: count carry-in, p: first start
+  BsAgg base;  // a: id base, b: count carry-in, p: first start
+  {
+    const BsAgg lb = agg[blockIdx.x], cb = cagg[blockIdx.x / kBsChunk];
+    base.a = cb.a + lb.a;
+    base.b = cb.b + lb.b;
+    base.p = cb.p + cb.b * lb.len + lb.p;
+  }
   const uint64_t b0 = (uint64_t)blockIdx.x * kBsTile + (uint64_t)threadIdx.x * kXPer;
   // ---- blocks: ids, counts, starts ----
   unsigned long long a[kXPer], dl[kXPer];
@@ -926,8 +955,9 @@ static void expand_blocks_t(const Plan *plan, const unsigned long long *sid,
   const uint64_t tiles = (M + kBsTile - 1) / kBsTile;
   if (tiles == 0) return;
   note_launch();
-  k_expand_blocks<D><<<(unsigned)tiles, kXThreads, 0, s>>>(plan, sid, scnt, M, agg, s_rel, nb, n,
-                                                          log2_chunk, out, qout, err);
+  k_expand_blocks<D><<<(unsigned)tiles, kXThreads, 0, s>>>(plan, sid, scnt, M, agg, agg + tiles,
+                                                          s_rel, nb, n, log2_chunk, out, qout,
+                                                          err);
 }
 
 void launch_expand_blocks(uint32_t d, const Plan *plan, const unsigned long long *sid,
@@ -947,16 +977,25 @@ void launch_expand_blocks(uint32_t d, const Plan *plan, const unsigned long long
   }
 }
 
-// block-tile aggregates and their bases only (the expand applies them)
+// block-tile aggregates and their bases only (the expand applies them):
+// agg holds the tiles' entries, then the chunks'
+uint64_t block_bases_bytes(uint64_t M) {
+  const uint64_t tiles = (M + kBsTile - 1) / kBsTile;
+  return (tiles + (tiles + kBsChunk - 1) / kBsChunk + 1) * sizeof(BsAgg);
+}
+
 void launch_block_bases(const unsigned long long *sid, const unsigned long long *scnt, uint64_t M,
                         void *agg, cudaStream_t s) {
   if (M == 0) return;
   const uint64_t tiles = (M + kBsTile - 1) / kBsTile;
+  const uint64_t chunks = (tiles + kBsChunk - 1) / kBsChunk;
   BsAgg *g = reinterpret_cast<BsAgg *>(agg);
   note_launch();
   k_bscan_sum<<<(unsigned)tiles, kBsThreads, 0, s>>>(sid, scnt, M, g);
   note_launch();
-  k_bscan_top<<<1, 1024, 0, s>>>(g, (uint32_t)tiles);
+  k_bscan_chunk<<<(unsigned)chunks, kBsChunk, 0, s>>>(g, (uint32_t)tiles, g + tiles);
+  note_launch();
+  k_bscan_top<<<1, 1024, 0, s>>>(g + tiles, (uint32_t)chunks);
 }
 
 // raw outliers of an LCP-S frame go to the last K slots; their codes (for a

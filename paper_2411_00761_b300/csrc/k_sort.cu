@@ -191,13 +191,23 @@ __global__ void __launch_bounds__(512) k_scatter(const unsigned long long *__res
   const uint32_t shift = plan->part_shift, nb = nb1 - 1;
   const uint64_t lo = (uint64_t)blockIdx.x * span;
   const uint64_t hi = min(n, lo + span);
-  constexpr int kIlp = 8;  // loads, then cursor updates, in flight per thread
-  for (uint64_t i0 = lo; i0 < hi; i0 += (uint64_t)kIlp * blockDim.x) {
+  // kIlp keys per thread per round; the next round's keys are loaded before
+  // this round's cursor updates and stores, so loads stay in flight
+  constexpr int kIlp = 4;
+  const uint64_t step = (uint64_t)kIlp * blockDim.x;
+  unsigned long long kn[kIlp];
+#pragma unroll
+  for (int r = 0; r < kIlp; ++r) {
+    const uint64_t i = lo + (uint64_t)r * blockDim.x + threadIdx.x;
+    kn[r] = i < hi ? __ldcs(keys + i) : 0ull;
+  }
+  for (uint64_t i0 = lo; i0 < hi; i0 += step) {
     unsigned long long k[kIlp];
 #pragma unroll
     for (int r = 0; r < kIlp; ++r) {
-      const uint64_t i = i0 + (uint64_t)r * blockDim.x + threadIdx.x;
-      k[r] = i < hi ? __ldcs(keys + i) : 0ull;
+      k[r] = kn[r];
+      const uint64_t i = i0 + step + (uint64_t)r * blockDim.x + threadIdx.x;
+      kn[r] = i < hi ? __ldcs(keys + i) : 0ull;
     }
     // one cursor update per run of lanes with the same bucket
     uint32_t pos[kIlp];
@@ -636,14 +646,25 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
       for (uint32_t d = threadIdx.x; d < nsub; d += kSplitThreads) h[d] = base[d];
     }
     __syncthreads();
-    for (uint32_t t0 = c0; t0 < c1; t0 += kSplitThreads * kSplitIlp) {
+    // scatter; the next round's keys are loaded before this round's cursor
+    // updates and stores
+    constexpr uint32_t kStep = kSplitThreads * kSplitIlp;
+    unsigned long long kn[kSplitIlp];
+#pragma unroll
+    for (int r = 0; r < kSplitIlp; ++r) {
+      const uint32_t u = c0 + r * kSplitThreads + threadIdx.x;
+      kn[r] = u < c1 ? kb[u] : 0ull;
+    }
+    for (uint32_t t0 = c0; t0 < c1; t0 += kStep) {
       unsigned long long k[kSplitIlp];
       uint32_t ix[kSplitIlp];
 #pragma unroll
       for (int r = 0; r < kSplitIlp; ++r) {
         const uint32_t u = t0 + r * kSplitThreads + threadIdx.x;
-        k[r] = u < c1 ? kb[u] : 0ull;
+        k[r] = kn[r];
         ix[r] = (idx_out && u < c1) ? idx[lo + u] : 0u;
+        const uint32_t un = u + kStep;
+        kn[r] = un < c1 ? kb[un] : 0ull;
       }
       uint32_t pos[kSplitIlp];
 #pragma unroll

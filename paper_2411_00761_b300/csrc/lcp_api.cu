@@ -1039,7 +1039,7 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
     }
     prof_end(c, s);
     if (M > 0) {
-      TRY(grow(w.scan_tmp, (M / 1024 + 2) * 32));
+      TRY(grow(w.scan_tmp, block_bases_bytes(M)));
       prof_begin(c, "d.block_scans", s);
       launch_block_bases(P<unsigned long long>(w.s_id), P<unsigned long long>(w.s_cnt), M,
                          w.scan_tmp.p, s);

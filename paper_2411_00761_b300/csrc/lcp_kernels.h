@@ -208,8 +208,9 @@ void launch_scan_u64(const unsigned long long *in, uint64_t n, int mode, bool in
 void launch_check_counts(const unsigned long long *counts, uint64_t m,
                          const unsigned long long *starts_total, uint64_t nb, int *err, int sms,
                          cudaStream_t s);
-// block-tile bases (agg: 32 bytes per 1024 blocks + 32) and the fused
-// expand over block tiles
+// block-tile bases (agg: block_bases_bytes(M)) and the fused expand over
+// block tiles
+uint64_t block_bases_bytes(uint64_t M);
 void launch_block_bases(const unsigned long long *sid, const unsigned long long *scnt, uint64_t M,
                         void *agg, cudaStream_t s);
 void launch_expand_blocks(uint32_t d, const Plan *plan, const unsigned long long *sid,
