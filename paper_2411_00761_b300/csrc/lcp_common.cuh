@@ -20,7 +20,7 @@ constexpr int kMaxD = 8;
 constexpr int kAlpha = 4096;  // Huffman alphabet; the last symbol escapes
 constexpr int kEsc = 4095;
 constexpr int kLmax = 24;      // longest Huffman code
-constexpr int kFastBits = 11;  // first-level decode table index bits
+constexpr int kFastBits = 12;  // first-level decode table index bits
 constexpr unsigned long long kOutlierBit = 1ull << 63;
 
 enum Status : int {
