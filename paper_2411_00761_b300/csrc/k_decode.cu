@@ -905,9 +905,7 @@ __global__ void __launch_bounds__(kXThreads, 3) k_expand_blocks(
     }
 #pragma unroll
     for (int f = 0; f < D; ++f) {
-      const uint32_t c8 = sF[f].c8, sticky = sF[f].sticky, qmax = sF[f].qmax;
-      const long long mb = sF[f].mb;
-      const int32_t g1 = sF[f].g1;
+      const uint32_t qmax = sF[f].qmax;
       float r[4];
       int32_t q4[4];
       bool over = false;
@@ -918,7 +916,23 @@ __global__ void __launch_bounds__(kXThreads, 3) k_expand_blocks(
         const uint32_t q = sb_f[bj < (uint32_t)kBsTile ? bj : 0u][f] + ((rel[j] >> (f * lp)) & pm);
         over |= valid && (bj >= (uint32_t)kBsTile || q > qmax);
         q4[j] = (int32_t)q;
-        r[j] = reconstruct_c((long long)q, c8, mb, sticky, g1, sF[f]);
+      }
+      if (qmax < (1u << 23)) {  // every code of the field takes the binary32 path
+        const float fm = sF[f].m, fe = sF[f].e;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          float z;
+          r[j] = recon_rn_f32((long long)(uint32_t)q4[j], fm, fe, z)
+                     ? z
+                     : recon_slow((long long)(uint32_t)q4[j], sF[f]);
+        }
+      } else {
+        const uint32_t c8 = sF[f].c8, sticky = sF[f].sticky;
+        const long long mb = sF[f].mb;
+        const int32_t g1 = sF[f].g1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          r[j] = reconstruct_c((long long)(uint32_t)q4[j], c8, mb, sticky, g1, sF[f]);
       }
       if (over) atomicExch(err, 1);
       float *o = out + (uint64_t)f * n + k0;

@@ -390,6 +390,41 @@ __device__ __forceinline__ float reconstruct(long long q, const FieldPlan &F) {
   return recon_wide(q, F);
 }
 
+// Q2 in binary32 arithmetic alone, for 0 <= q < 2^23 (so that 2q+1 is
+// exact): the product (2q+1) e is split exactly into ph + pl (FMA), m + ph
+// into th + tl (TwoSum), and RN(m + ph + pl) = RN(th + RO(tl + pl)) with RO
+// rounding to odd (round toward zero, lowest bit set when inexact) -- the
+// correctly rounded sum of three terms by rounding to odd of Boldo and
+// Melquiond ("Emulation of FMA and correctly rounded sums: proved algorithms
+// using rounding to odd", IEEE Trans. Computers 57(4), 2008).  Returns false
+// (the caller falls back) outside that range or when the result is
+// subnormal.  These are FMA-pipe operations; the 64-bit integer conversion
+// of reconstruct() issues on the FP64 pipe.
+__device__ __forceinline__ bool recon_rn_f32(long long q, float m, float e, float &z) {
+  if ((unsigned long long)q >= (1ull << 23)) return false;
+  const float qf = __int2float_rn((int)(2 * q + 1));
+  const float ph = __fmul_rn(qf, e);
+  const float pl = __fmaf_rn(qf, e, -ph);
+  const float th = __fadd_rn(m, ph);
+  const float bb = __fsub_rn(th, m);
+  const float aa = __fsub_rn(th, bb);
+  const float tl = __fadd_rn(__fsub_rn(m, aa), __fsub_rn(ph, bb));
+  const float rz = __fadd_rz(tl, pl);
+  const bool inexact = __fadd_ru(tl, pl) != __fadd_rd(tl, pl);
+  const float v = __uint_as_float(__float_as_uint(rz) | (inexact ? 1u : 0u));
+  z = __fadd_rn(th, v);
+  if (z == 0.0f) {
+    z = 0.0f;
+    return true;
+  }
+  return fabsf(z) >= 0x1p-126f;
+}
+
+// out-of-line Q2 for the rare values the binary32 path declines
+static __device__ __noinline__ float recon_slow(long long q, const FieldPlan &F) {
+  return reconstruct(q, F);
+}
+
 // reconstruct() with the plan's constants already in registers; Fs (the
 // plan, e.g. in shared memory) serves the rare wide fallback
 __device__ __forceinline__ float reconstruct_c(long long q, uint32_t c8, long long mb,

@@ -194,6 +194,39 @@ def test_sort_paths(ctx, orc):
     check_s(ctx, orc, c[:, rng.permutation(c.shape[1])], 1e-3, "abs", 8)
 
 
+# Field minima off the bin grid, from near zero to large offsets, and bin counts
+# from ~10^2 to above 2^23, so that reconstruction (Eq. quantization, Q2) runs
+# both its binary32 path (codes below 2^23) and its 64-bit path, in the LCP-S
+# expand and in the LCP-T decode.
+Q2_FRAMES = [
+    ((1.0e6, -3.7e4, 2.5e-3), (100.0, 100.0, 100.0), 1e-3, "abs"),
+    ((-0.75, 123.456, -9.9e3), (1.0, 1.0, 1.0), 3.3e-6, "abs"),
+    ((0.0, 50.0, -100.0), (1.0, 1e-4, 1e-4), 2e-8, "abs"),  # 2.5e7 bins in the first field
+    ((5.0e4, -5.0e4, 1.0), (1.0e4, 1.0e4, 1.0e4), 1e-4, "rel"),
+]
+
+
+@pytest.mark.parametrize("offs,scale,eb,mode", Q2_FRAMES)
+def test_decode_q2_offsets_and_bounds(ctx, orc, lcp, offs, scale, eb, mode):
+    rng = np.random.default_rng(11)
+    sc = np.array(scale)[:, None]
+    X0 = (rng.random((3, 20011)) * sc + np.array(offs)[:, None]).astype(np.float32)
+    check_s(ctx, orc, X0, eb, mode, 8)
+    X1 = (X0 + rng.normal(0.0, 1e-4, X0.shape) * sc).astype(np.float32)
+    tr = lcp.Trajectory(ctx, batch=10, p=8)
+    r0 = ctx.compress(to_dev(X0), eb, mode, traj=tr, method="spatial", perm=True)
+    o0 = orc.compress_s(X0, eb, mode, 8, flags=1)
+    assert gpu_bytes(r0) == o0["bytes"]
+    r1 = ctx.compress(to_dev(X1), eb, mode, traj=tr, method="temporal")
+    o1 = orc.compress_t(X1, eb, mode, o0["q"], o0["pi"])
+    assert gpu_bytes(r1) == o1["bytes"]
+    dt = lcp.Trajectory(ctx, batch=10, p=8)
+    ctx.decompress(r0["bytes"], traj=dt)
+    Y1 = ctx.decompress(r1["bytes"], traj=dt).cpu().numpy()
+    Yo1, _ = orc.decompress(o1["bytes"], o0["q"])
+    assert np.array_equal(Y1.view(np.uint32), Yo1.view(np.uint32))
+
+
 # ---------------------------------------------------------------------------
 # LCP-T and the hybrid (Algorithm 1 with the LCP-FSM)
 # ---------------------------------------------------------------------------
