@@ -151,6 +151,26 @@ LCP_API lcp_status lcp_select(lcp_ctx *ctx, lcp_traj *traj, const float *d_field
                       uint64_t *est_s, uint64_t *est_t, void *stream);
 
 /*
+ * Block-size search on a sample (Sec. "Best block size"): the candidates are
+ * p = 2^k, 0 <= k <= 16, within the domain (p^d <= 2^32), each judged by the
+ * exact LCP-S container size of a sample of the frame coded with that p;
+ * the smallest wins, ties to the smaller p.  The sample is the frame's first
+ * S particles in storage order, coded with the same eb and mode: S = sample
+ * when 0 < sample <= n, S = min(n, max(65536, ceil(n / 8))) when sample == 0.
+ *   d_fields:  device float32 [d][n], field-major, 16-byte aligned.
+ *   p_best:    receives the chosen p.
+ *   sizes:     optional host array of 17 entries; sizes[k] receives the
+ *              sample's container size for p = 2^k, 0 where that p is
+ *              outside the domain.
+ * Returns ERR_RANGE when no candidate is in the domain.  Synchronizes
+ * `stream`.
+ */
+LCP_API lcp_status lcp_choose_block_size(lcp_ctx *ctx, const float *d_fields, uint64_t n,
+                                         uint32_t d, double eb, lcp_eb_mode mode,
+                                         uint64_t sample, uint32_t *p_best, uint64_t *sizes,
+                                         void *stream);
+
+/*
  * Trajectory state for Algorithm 1: batch_size frames per batch (the first
  * frame of a batch is predicted from the last spatial anchor frame).  p is
  * the block multiplier its LCP-S frames use (nonzero).  A trajectory object

@@ -131,6 +131,31 @@ def decode_trajectory(containers):
     return frames
 
 
+# Sec. "Best block size": the candidates p = 2^k, 0 <= k <= 16
+BLOCK_CANDIDATES_ALL = tuple(1 << k for k in range(17))
+
+
+def sample_size(n: int) -> int:
+    """Particles in the search sample when the caller gives none: an eighth
+    of the frame, at least 65536 (all of a smaller frame)."""
+    return min(n, max(65536, -(-n // 8)))
+
+
+def choose_block_size_sampled(X, eb: float, mode="abs", sample: int = 0,
+                              log2_chunk: int = 10) -> tuple[int, dict]:
+    """Sec. "Best block size": each candidate p = 2^k (0 <= k <= 16) within
+    the domain is judged by the exact LCP-S container size of a sample of the
+    frame; the smallest wins, ties to the smaller p.  The paper leaves the
+    sampling open; here the sample is the frame's first S particles in
+    storage order, coded with the same bound and mode (S = sample, or
+    sample_size(n) when 0)."""
+    X = np.asarray(X, dtype=np.float32)
+    n = X.shape[1]
+    S = sample if sample else sample_size(n)
+    return choose_block_size(np.ascontiguousarray(X[:, :S]), eb, mode, BLOCK_CANDIDATES_ALL,
+                             log2_chunk)
+
+
 def choose_block_size(X, eb: float, mode="abs", candidates=BLOCK_CANDIDATES,
                       log2_chunk: int = 10) -> tuple[int, dict]:
     """Exact compressed size per candidate p; returns (best p, sizes)."""

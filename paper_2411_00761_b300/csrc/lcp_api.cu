@@ -49,7 +49,7 @@ struct Workspace {
       s_id, s_cnt, hist, maxv, nvals, mcount, kcount, desc, codes, lens,
       tables, chunk_bits, chunk_off, outl_idx, summary, q_in, q_slot, perm, sym, patch_s,
       patch_i, patch_x, patch_s2, patch_i2, patch_so, patch_io, dec_fields, hufft, err,
-      scan_tmp, scan_base, bid, counts, starts, cand, tq, fplan, fstatus, cbwork;
+      scan_tmp, scan_base, bid, counts, starts, cand, tq, fplan, fstatus, cbwork, sample;
 };
 
 __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
@@ -850,6 +850,52 @@ lcp_status lcp_compress(lcp_ctx *c, lcp_traj *traj, const float *d_fields, uint6
   *out_size = total;
   if (chosen) *chosen = LCP_SPATIAL;
   return (lcp_status)st;
+}
+
+lcp_status lcp_choose_block_size(lcp_ctx *c, const float *d_fields, uint64_t n, uint32_t d,
+                                 double eb, lcp_eb_mode mode, uint64_t sample, uint32_t *p_best,
+                                 uint64_t *sizes, void *stream) {
+  if (!c || !p_best) return LCP_ERR_ARG;
+  int st = check_frame_args(d_fields, n, d, eb, mode);
+  if (st != OK) return (lcp_status)st;
+  if (sample > n) return LCP_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t S = sample ? sample : std::min<uint64_t>(n, std::max<uint64_t>(65536, (n + 7) / 8));
+  const float *Xs = d_fields;
+  if (S < n) {  // the first S particles of every field, contiguous
+    st = grow(c->ws.sample, (size_t)S * d * 4);
+    if (st != OK) return (lcp_status)st;
+    if (cudaMemcpy2DAsync(c->ws.sample.p, S * 4, d_fields, n * 4, S * 4, d,
+                          cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      return LCP_ERR_CUDA;
+    }
+    Xs = reinterpret_cast<const float *>(c->ws.sample.p);
+  }
+  uint64_t best = ~0ull;
+  int last = ERR_RANGE;
+  *p_best = 0;
+  for (uint32_t k = 0; k <= 16; ++k) {
+    const uint32_t p = 1u << k;
+    if (sizes) sizes[k] = 0;
+    if (check_p(p, d) != OK) continue;
+    uint64_t total = 0;
+    st = compress_s_impl(c, Xs, S, d, eb, mode, p, 0, nullptr, 0, true, nullptr, nullptr, &total,
+                         s);
+    if (st == ERR_RANGE || st == ERR_ARG) {
+      last = st;
+      continue;
+    }
+    if (st != OK) return (lcp_status)st;
+    if (sizes) sizes[k] = total;
+    if (total < best) {
+      best = total;
+      *p_best = p;
+    }
+  }
+  return *p_best ? LCP_OK : (lcp_status)last;
 }
 
 lcp_status lcp_select(lcp_ctx *c, lcp_traj *traj, const float *d_fields, uint64_t n, uint32_t d,

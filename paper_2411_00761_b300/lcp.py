@@ -38,6 +38,8 @@ SIGNATURES = {
                            C.POINTER(_u32), _vp]),
     "lcp_select": (C.c_int, [_vp, _vp, _vp, _u64, _u32, C.c_double, C.c_int, C.POINTER(C.c_int),
                              C.POINTER(_u64), C.POINTER(_u64), _vp]),
+    "lcp_choose_block_size": (C.c_int, [_vp, _vp, _u64, _u32, C.c_double, C.c_int, _u64,
+                                        C.POINTER(_u32), C.POINTER(_u64), _vp]),
     "lcp_traj_create": (C.c_int, [_vp, _u32, _u32, C.POINTER(C.c_void_p)]),
     "lcp_traj_destroy": (C.c_int, [_vp]),
     "lcp_quantize": (C.c_int, [_vp, _u64, C.c_float, C.c_float, C.c_float, _vp, _vp, _vp, _vp]),
@@ -249,6 +251,18 @@ class Context:
                                C.byref(ch), C.byref(es), C.byref(et), _stream(stream)),
                "lcp_select")
         return ("temporal" if ch.value == TEMPORAL else "spatial"), es.value, et.value
+
+    def choose_block_size(self, X: torch.Tensor, eb: float, mode="abs", sample: int = 0,
+                          stream=None):
+        """lcp_choose_block_size: (best p, {p: sample container size}) over
+        p = 2^0 .. 2^16 within the domain."""
+        d, n = X.shape
+        pb = C.c_uint32(0)
+        sizes = (C.c_uint64 * 17)()
+        _check(_lib.lcp_choose_block_size(self.h, _ptr(X), n, d, float(eb), _mode(mode), sample,
+                                          C.byref(pb), sizes, _stream(stream)),
+               "lcp_choose_block_size")
+        return pb.value, {1 << k: sizes[k] for k in range(17) if sizes[k]}
 
 
 class Trajectory:

@@ -170,6 +170,19 @@ def test_block_size_autotune_matches_oracle(ctx, orc):
     assert gpu_bytes(r) == orc.compress_s(Xf, 1e-4, "rel", best)["bytes"]
 
 
+@pytest.mark.parametrize("name,Xf,eb,mode,sample", [
+    ("uniform_clusters", synth.uniform_clusters(150001, 3), 1e-3, "abs", 0),   # p = 1 .. 1024
+    ("cosmology6", synth.cosmology(100003, 4), 1e-3, "rel", 0),                # p = 1 .. 32
+    ("md_fcc_given_sample", synth.md_fcc(70001, 2, cells=28), 1e-4, "rel", 30011),
+])
+def test_choose_block_size_matches_oracle(ctx, orc, name, Xf, eb, mode, sample):
+    from oracle import hybrid
+    p_ref, sizes_ref = hybrid.choose_block_size_sampled(Xf, eb, mode, sample)
+    p, sizes = ctx.choose_block_size(to_dev(Xf), eb, mode, sample)
+    assert sizes == sizes_ref
+    assert p == p_ref
+
+
 def test_sort_paths(ctx, orc):
     """Sort units whose digit groups need every path of the unit sort:
     windows of 2..512 particles sorted by one warp (32- and 64-bit keys,
