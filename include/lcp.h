@@ -179,6 +179,32 @@ LCP_API lcp_status lcp_choose_block_size(lcp_ctx *ctx, const float *d_fields, ui
 LCP_API lcp_status lcp_traj_create(lcp_ctx *ctx, uint32_t batch_size, uint32_t p, lcp_traj **out);
 LCP_API lcp_status lcp_traj_destroy(lcp_traj *traj);
 
+/*
+ * Checkpoint and resume of a trajectory (encoder or decoder side).  A frame
+ * depends only on its batch and the batch's anchor (Sec. "Batch
+ * compression", Algorithm 1), so the whole reference state is: the previous
+ * frame's and the last anchor's slot codes and slot permutation, the LCP-FSM
+ * state with its S-size estimate, and the frame counter.  The paper has no
+ * checkpoint format; this one is the library's own.
+ *
+ * lcp_traj_export writes that state as a self-contained byte image into
+ * host memory (little-endian; a 56-byte header, then the previous frame's
+ * codes [d][n] int32 and permutation [n] uint32, then the anchor's, each
+ * present only when the trajectory has it).  *size receives the image size;
+ * with host_out NULL or cap below it nothing is written and ERR_CAPACITY is
+ * returned.  The trajectory is unchanged.  Synchronizes `stream`.
+ *
+ * lcp_traj_import creates a trajectory on ctx from such an image (the
+ * context may be another one, on another device): frames coded or decoded
+ * through it continue exactly as through the exported one.  A malformed
+ * image returns ERR_FORMAT; *out is NULL on any error.  Synchronizes
+ * `stream`.
+ */
+LCP_API lcp_status lcp_traj_export(const lcp_traj *traj, void *host_out, size_t cap,
+                                   size_t *size, void *stream);
+LCP_API lcp_status lcp_traj_import(lcp_ctx *ctx, const void *host_in, size_t size,
+                                   lcp_traj **out, void *stream);
+
 /* Device memory a context's workspace / a trajectory's state holds (bytes). */
 LCP_API uint64_t lcp_ctx_device_bytes(const lcp_ctx *ctx);
 LCP_API uint64_t lcp_traj_device_bytes(const lcp_traj *traj);

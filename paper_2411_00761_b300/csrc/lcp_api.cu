@@ -64,7 +64,10 @@ struct DeviceGuard {
   bool ok = true;
   explicit DeviceGuard(int dev) {
     if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) {
+      ok = false;
+      cudaGetLastError();  // leave no stale error for the next call
+    }
   }
   ~DeviceGuard() {
     int cur = -1;
@@ -133,6 +136,7 @@ struct lcp_ctx {
 
 struct lcp_traj {
   lcp_ctx *ctx = nullptr;
+  int device = 0;  // the device of its buffers (the context may be destroyed first)
   uint32_t batch = 1, p = 8;
   uint64_t t = 0;
   uint64_t n = 0;
@@ -651,6 +655,7 @@ lcp_status lcp_traj_create(lcp_ctx *c, uint32_t batch_size, uint32_t p, lcp_traj
   if (!c || !out || batch_size == 0 || p == 0 || (p & (p - 1)) || p > 65536) return LCP_ERR_ARG;
   lcp_traj *t = new lcp_traj();
   t->ctx = c;
+  t->device = c->device;
   t->batch = batch_size;
   t->p = p;
   *out = t;
@@ -659,11 +664,124 @@ lcp_status lcp_traj_create(lcp_ctx *c, uint32_t batch_size, uint32_t p, lcp_traj
 
 lcp_status lcp_traj_destroy(lcp_traj *t) {
   if (!t) return LCP_ERR_ARG;
-  DeviceGuard g(t->ctx->device);
+  DeviceGuard g(t->device);
   DevBuf *bufs[] = {&t->prev_q, &t->prev_pi, &t->anc_q, &t->anc_pi, &t->new_q, &t->new_pi};
   for (DevBuf *b : bufs)
     if (b->p) cudaFree(b->p);
   delete t;
+  return LCP_OK;
+}
+
+namespace {
+// trajectory image: this header, then prev_q [d][n] int32, prev_pi [n]
+// uint32 (when bit0 of flags), anc_q, anc_pi (when bit1)
+constexpr uint32_t kTrajMagic = 0x5354434cu;  // "LCTS"
+constexpr uint32_t kTrajVersion = 1;
+struct TrajImage {
+  uint32_t magic, version;
+  uint32_t batch, p;
+  uint64_t t, n;
+  uint32_t d, flags;  // bit0 previous frame, bit1 anchor, bit2 S size known
+  int32_t state, counter;
+  uint64_t s_est;
+};
+static_assert(sizeof(TrajImage) == 56, "image header layout");
+
+size_t traj_image_size(uint64_t n, uint32_t d, uint32_t flags) {
+  const size_t per = (size_t)n * d * 4 + (size_t)n * 4;
+  return sizeof(TrajImage) + ((flags & 1u) ? per : 0) + ((flags & 2u) ? per : 0);
+}
+}  // namespace
+
+lcp_status lcp_traj_export(const lcp_traj *t, void *host_out, size_t cap, size_t *size,
+                           void *stream) {
+  if (!t || !size) return LCP_ERR_ARG;
+  const uint32_t flags =
+      (t->has_prev ? 1u : 0u) | (t->has_anchor ? 2u : 0u) | (t->s_known ? 4u : 0u);
+  const size_t need = traj_image_size(t->n, t->d, flags);
+  *size = need;
+  if (!host_out || cap < need) return LCP_ERR_CAPACITY;
+  DeviceGuard g(t->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  TrajImage h{kTrajMagic, kTrajVersion, t->batch, t->p, t->t, t->n, t->d, flags,
+              t->state, t->counter, t->s_est};
+  memcpy(host_out, &h, sizeof h);
+  uint8_t *o = reinterpret_cast<uint8_t *>(host_out) + sizeof h;
+  const size_t qb = (size_t)t->n * t->d * 4, pb = (size_t)t->n * 4;
+  cudaStream_t s = (cudaStream_t)stream;
+  const DevBuf *src[4] = {&t->prev_q, &t->prev_pi, &t->anc_q, &t->anc_pi};
+  const bool have[4] = {t->has_prev, t->has_prev, t->has_anchor, t->has_anchor};
+  for (int k = 0; k < 4; ++k) {
+    if (!have[k]) continue;
+    const size_t b = (k & 1) ? pb : qb;
+    if (b && cudaMemcpyAsync(o, src[k]->p, b, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+      cudaGetLastError();
+      return LCP_ERR_CUDA;
+    }
+    o += b;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return LCP_ERR_CUDA;
+  }
+  return LCP_OK;
+}
+
+lcp_status lcp_traj_import(lcp_ctx *c, const void *host_in, size_t size, lcp_traj **out,
+                           void *stream) {
+  if (!c || !host_in || !out) return LCP_ERR_ARG;
+  *out = nullptr;
+  TrajImage h;
+  if (size < sizeof h) return LCP_ERR_FORMAT;
+  memcpy(&h, host_in, sizeof h);
+  const bool shape_ok = h.n == 0 ? h.d <= 8 : (h.d >= 1 && h.d <= 8 && h.n < (1ull << 32));
+  if (h.magic != kTrajMagic || h.version != kTrajVersion || h.batch == 0 || h.p == 0 ||
+      (h.p & (h.p - 1)) || h.p > 65536 || (h.flags & ~7u) || !shape_ok || h.state < 0 ||
+      h.state > 16 || h.counter < 0 || h.counter > 16 ||
+      size != traj_image_size(h.n, h.d, h.flags))
+    return LCP_ERR_FORMAT;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  lcp_traj *t = new lcp_traj();
+  t->ctx = c;
+  t->device = c->device;
+  t->batch = h.batch;
+  t->p = h.p;
+  t->t = h.t;
+  t->n = h.n;
+  t->d = h.d;
+  t->has_prev = (h.flags & 1u) != 0;
+  t->has_anchor = (h.flags & 2u) != 0;
+  t->s_known = (h.flags & 4u) != 0;
+  t->state = h.state;
+  t->counter = h.counter;
+  t->s_est = h.s_est;
+  const uint8_t *in = reinterpret_cast<const uint8_t *>(host_in) + sizeof h;
+  const size_t qb = (size_t)h.n * h.d * 4, pb = (size_t)h.n * 4;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBuf *dst[4] = {&t->prev_q, &t->prev_pi, &t->anc_q, &t->anc_pi};
+  const bool have[4] = {t->has_prev, t->has_prev, t->has_anchor, t->has_anchor};
+  int st = OK;
+  for (int k = 0; k < 4 && st == OK; ++k) {
+    if (!have[k]) continue;
+    const size_t b = (k & 1) ? pb : qb;
+    st = grow(*dst[k], b);
+    if (st == OK && b &&
+        cudaMemcpyAsync(dst[k]->p, in, b, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      st = ERR_CUDA;
+    }
+    in += b;
+  }
+  if (st == OK && cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    st = ERR_CUDA;
+  }
+  if (st != OK) {
+    lcp_traj_destroy(t);
+    return (lcp_status)st;
+  }
+  *out = t;
   return LCP_OK;
 }
 

@@ -42,6 +42,8 @@ SIGNATURES = {
                                         C.POINTER(_u32), C.POINTER(_u64), _vp]),
     "lcp_traj_create": (C.c_int, [_vp, _u32, _u32, C.POINTER(C.c_void_p)]),
     "lcp_traj_destroy": (C.c_int, [_vp]),
+    "lcp_traj_export": (C.c_int, [_vp, _vp, _sz, C.POINTER(_sz), _vp]),
+    "lcp_traj_import": (C.c_int, [_vp, _vp, _sz, C.POINTER(C.c_void_p), _vp]),
     "lcp_quantize": (C.c_int, [_vp, _u64, C.c_float, C.c_float, C.c_float, _vp, _vp, _vp, _vp]),
     "lcp_ctx_profile": (C.c_int, [_vp, C.c_int]),
     "lcp_kernel_launches": (_u64, []),
@@ -274,6 +276,29 @@ class Trajectory:
         h = C.c_void_p()
         _check(_lib.lcp_traj_create(ctx.h, batch, p, C.byref(h)), "lcp_traj_create")
         self.h = h
+
+    def export(self, stream=None) -> bytes:
+        """lcp_traj_export: the reference state as a host byte image."""
+        size = C.c_size_t(0)
+        st = _lib.lcp_traj_export(self.h, None, 0, C.byref(size), _stream(stream))
+        if st != ERR_CAPACITY:
+            _check(st, "lcp_traj_export")
+        buf = C.create_string_buffer(max(size.value, 1))
+        _check(_lib.lcp_traj_export(self.h, buf, size.value, C.byref(size), _stream(stream)),
+               "lcp_traj_export")
+        return buf.raw[: size.value]
+
+    @classmethod
+    def restore(cls, ctx: Context, image: bytes, stream=None) -> "Trajectory":
+        """lcp_traj_import: a trajectory on ctx continuing an exported one."""
+        self = cls.__new__(cls)
+        self.ctx = ctx
+        self.h = None
+        h = C.c_void_p()
+        _check(_lib.lcp_traj_import(ctx.h, image, len(image), C.byref(h), _stream(stream)),
+               "lcp_traj_import")
+        self.h = h
+        return self
 
     def close(self):
         if self.h:
