@@ -290,8 +290,10 @@ def run_reference(args):
         "value": val, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 in, integer codes",
-        "data": "synthetic", "config": {"workload": name, "desc": w["desc"], "p": p,
-                                        "sample_particles": n_sample},
+        "data": "synthetic",
+        "config": {"workload": name, "desc": w["desc"], "particles": int(X.shape[1]),
+                   "fields": int(X.shape[0]), "eb": w["eb"], "eb_mode": w["mode"], "p": p,
+                   "parallelism": "one CPU core (the oracle)", "sample_particles": n_sample},
         "cpu_baseline": {"value": val, "unit": "GB/s", "cores": 1, "kind": "oracle",
                          "sample": f"first {n_sample} particles of the frame per step"},
         "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
