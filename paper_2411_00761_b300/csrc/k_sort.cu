@@ -362,9 +362,10 @@ __device__ int cta_sort(unsigned long long *k, uint32_t *i, unsigned long long *
 // ---------------------------------------------------------------------------
 // level-2 partition of buckets above kSplitMin keys: each such bucket is
 // split by the next sub_bits_for(count) key bits (still block-id bits, so no
-// block crosses a sub-bucket), one CTA per bucket.  Sort units (k_local): the
-// ordered list of key ranges holding consecutive unsplit buckets merged
-// greedily up to kCap keys, and the outlier bucket.
+// block crosses a sub-bucket), one CTA per bucket of up to kSplitChunk keys,
+// larger buckets in kSplitChunk-key tasks on several CTAs.  Sort units
+// (k_local): the ordered list of key ranges holding consecutive unsplit
+// buckets merged greedily up to kCap keys, and the outlier bucket.
 // ---------------------------------------------------------------------------
 // level-2 digit width of a split bucket of cnt keys (maxsub: block-id bits
 // below the level-1 digit)
