@@ -66,6 +66,12 @@ _i64p = C.POINTER(C.c_int64)
 _szp = C.POINTER(C.c_size_t)
 
 
+class _FieldPlan(C.Structure):
+    """orc_field_plan (lcp_oracle.h)."""
+    _fields_ = [("min_f", C.c_float), ("max_f", C.c_float), ("eb_f", C.c_double),
+                ("e", C.c_float), ("qmax", C.c_uint32)]
+
+
 def _declare(L):
     L.orc_q1.restype = C.c_int64
     L.orc_q1.argtypes = [C.c_float, C.c_float, C.c_float]
@@ -92,6 +98,9 @@ def _declare(L):
                                  _u64p]
     L.orc_peek.restype = C.c_int
     L.orc_peek.argtypes = [_u8p, C.c_size_t, _u64p, _u32p, _u32p, _u32p]
+    L.orc_plan.restype = C.c_int
+    L.orc_plan.argtypes = [_fp, C.c_uint64, C.c_uint32, C.c_double, C.c_int,
+                           C.POINTER(_FieldPlan)]
     L.orc_decompress.restype = C.c_int
     L.orc_decompress.argtypes = [_u8p, C.c_size_t, _i32p, _fp, C.c_uint64, _i32p]
 
@@ -149,6 +158,19 @@ def huffman_lengths(freq) -> np.ndarray:
     ln = np.zeros(4096, dtype=np.uint8)
     lib().orc_huffman_lengths(_ptr(f, _u64p), _ptr(ln, _u8p))
     return ln[: max(freq.size, 1)]
+
+
+def plan(X, eb: float, mode="abs") -> list[dict]:
+    """Per-field grid of a frame (orc_plan): min, max, resolved bound eb_f,
+    effective bound e (largest f32 <= eb_f) and qmax."""
+    X = _fields(X)
+    d, n = X.shape
+    out = (_FieldPlan * d)()
+    st = lib().orc_plan(_ptr(X, _fp), n, d, eb, _mode(mode), out)
+    if st != OK:
+        raise OracleError(st, "plan")
+    return [dict(min=out[f].min_f, max=out[f].max_f, eb=out[f].eb_f, e=out[f].e,
+                 qmax=int(out[f].qmax)) for f in range(d)]
 
 
 def max_compressed_size(n: int, d: int) -> int:
