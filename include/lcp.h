@@ -180,6 +180,23 @@ LCP_API lcp_status lcp_traj_create(lcp_ctx *ctx, uint32_t batch_size, uint32_t p
 LCP_API lcp_status lcp_traj_destroy(lcp_traj *traj);
 
 /*
+ * Anchor bound scaling (Sec. "Best error-bound scale for anchor frames";
+ * the paper picks 5).  With scale > 1, an anchor -- a first-in-batch frame
+ * the LCP-FSM codes LCP-S -- is written with bound eb / scale while the FSM
+ * sees temporal correlation (its state is T or S2 when the frame is planned;
+ * a trajectory's first frame counts as correlated); the bound stays eb when
+ * eb / scale leaves the codec's domain, and the FSM keeps deciding on sizes
+ * at eb.  A T frame whose reference is such an anchor is predicted in value
+ * space: every reference code is reconstructed on the anchor's grid (Q2),
+ * quantized on the frame's grid (Q1) and clamped to [0, qmax]; its container
+ * sets flag bit2 so that decoders do the same.  scale == 1 (the default)
+ * turns it off.  scale in [1, 1024], else ERR_ARG.  Set it before the first
+ * frame; encoder and decoder trajectories need no matching setting (the
+ * containers carry the bounds and the flag).
+ */
+LCP_API lcp_status lcp_traj_set_anchor_scale(lcp_traj *traj, uint32_t scale);
+
+/*
  * Checkpoint and resume of a trajectory (encoder or decoder side).  A frame
  * depends only on its batch and the batch's anchor (Sec. "Batch
  * compression", Algorithm 1), so the whole reference state is: the previous
@@ -188,9 +205,11 @@ LCP_API lcp_status lcp_traj_destroy(lcp_traj *traj);
  * checkpoint format; this one is the library's own.
  *
  * lcp_traj_export writes that state as a self-contained byte image into
- * host memory (little-endian; a 56-byte header, then the previous frame's
+ * host memory (little-endian; a 64-byte header, then the previous frame's
  * codes [d][n] int32 and permutation [n] uint32, then the anchor's, each
- * present only when the trajectory has it).  *size receives the image size;
+ * present only when the trajectory has it, then the two frames' grids in the
+ * library's internal form, so an image is read back by the same library
+ * version only).  *size receives the image size;
  * with host_out NULL or cap below it nothing is written and ERR_CAPACITY is
  * returned.  The trajectory is unchanged.  Synchronizes `stream`.
  *

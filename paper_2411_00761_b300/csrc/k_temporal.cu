@@ -127,6 +127,44 @@ __global__ void __launch_bounds__(512) k_recon_t(const Plan *__restrict__ plan, 
   }
 }
 
+// value-space prediction across grids (Sec. "Best error-bound scale for
+// anchor frames"): a reference code on the reference's grid (Q2) quantized on
+// this frame's grid (Q1), clamped to [0, qmax]
+__global__ void __launch_bounds__(512) k_requant(const Plan *__restrict__ plan, uint64_t n,
+                                                 const int32_t *__restrict__ qref, RefGrid g,
+                                                 int32_t *__restrict__ qout) {
+  __shared__ FieldPlan F;
+  const int f = blockIdx.y;
+  if (threadIdx.x == 0) F = plan->f[f];
+  __syncthreads();
+  const FieldPlan &R = g.f[f];
+  const double inv2e = 0.5 / (double)F.e;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
+       j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t s = (uint64_t)f * n + j;
+    const float x = reconstruct((long long)qref[s], R);
+    int32_t q = 0;
+    if (x >= F.m) {
+      if (((double)x - (double)F.m) * inv2e >= (double)F.qmax + 1.0) {
+        q = (int32_t)F.qmax;  // beyond the grid: no exact Q1 needed
+      } else {
+        bool chk;
+        const int32_t r = quantize(x, F, chk);
+        q = r > (int32_t)F.qmax ? (int32_t)F.qmax : r;
+      }
+    }
+    qout[s] = q;
+  }
+}
+
+void launch_requant(const Plan *plan, uint64_t n, uint32_t d, const int32_t *qref,
+                    const RefGrid &g, int32_t *qout, int sms, cudaStream_t s) {
+  if (n == 0) return;
+  unsigned gx = (unsigned)std::min<unsigned long long>((n + 511) / 512, (unsigned long long)(4 * sms));
+  note_launch();
+  k_requant<<<dim3(gx, d), 512, 0, s>>>(plan, n, qref, g, qout);
+}
+
 void launch_recon_t(const Plan *plan, uint64_t n, uint32_t d, const uint32_t *sym,
                     const int32_t *qref, float *out, int32_t *qnew, int *err, int sms,
                     cudaStream_t s) {

@@ -17,6 +17,7 @@ namespace {
 
 constexpr uint32_t kLog2Chunk = 10;  // chunk of 1024 symbols
 constexpr uint32_t kFlagFirst = 1u, kFlagRefAnchor = 2u;
+constexpr uint32_t kFlagRequant = 4u;  // reference codes re-quantized on the frame's grid
 
 struct DevBuf {
   void *p = nullptr;
@@ -49,7 +50,7 @@ struct Workspace {
       s_id, s_cnt, hist, maxv, nvals, mcount, kcount, desc, codes, lens,
       tables, chunk_bits, chunk_off, outl_idx, summary, q_in, q_slot, perm, sym, patch_s,
       patch_i, patch_x, patch_s2, patch_i2, patch_so, patch_io, dec_fields, hufft, err,
-      scan_tmp, scan_base, bid, counts, starts, cand, tq, fplan, fstatus, cbwork, sample;
+      scan_tmp, scan_base, bid, counts, starts, cand, tq, fplan, fstatus, cbwork, sample, rq;
 };
 
 __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
@@ -146,6 +147,12 @@ struct lcp_traj {
   int state = 2, counter = 0;
   bool s_known = false;
   uint64_t s_est = 0;
+  // anchor bound scaling: anchors coded at eb / anchor_scale (1: off); the
+  // grids of the previous frame and the anchor, and whether each is a scaled
+  // anchor (frames predicted from it re-quantize its codes)
+  uint32_t anchor_scale = 1;
+  bool prev_scaled = false, anc_scaled = false;
+  FieldPlan prev_F[kMaxD] = {}, anc_F[kMaxD] = {};
   DevBuf prev_q, prev_pi, anc_q, anc_pi, new_q, new_pi;
 };
 
@@ -432,7 +439,7 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
 int compress_t_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double eb, int mode,
                     const uint32_t *pi, const int32_t *qref, uint32_t flags, uint8_t *out,
                     size_t cap, bool size_only, int32_t *qnew, uint64_t *total_out,
-                    cudaStream_t s) {
+                    cudaStream_t s, const FieldPlan *ref_grid = nullptr) {
   Workspace &w = c->ws;
   const int sms = c->sms;
   TRY(ws_common(c, n, d));
@@ -445,6 +452,14 @@ int compress_t_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   CK(cudaGetLastError());
   int st = read_plan(c, s);
   if (st != OK) return st;
+  if (ref_grid) {  // the reference is on another grid: predict in value space
+    TRY(grow(w.rq, nd * 4));
+    RefGrid g;
+    for (uint32_t f = 0; f < d; ++f) g.f[f] = ref_grid[f];
+    launch_requant(P<Plan>(w.plan), n, d, qref, g, P<int32_t>(w.rq), sms, s);
+    CK(cudaGetLastError());
+    qref = P<int32_t>(w.rq);
+  }
   CK(cudaMemsetAsync(w.hist.p, 0, 3ull * kAlpha * 4, s));
   CK(cudaMemsetAsync(w.maxv.p, 0, 4 * 8, s));
   CK(cudaMemsetAsync(w.kcount.p, 0, 8, s));
@@ -674,37 +689,42 @@ lcp_status lcp_traj_destroy(lcp_traj *t) {
 
 namespace {
 // trajectory image: this header, then prev_q [d][n] int32, prev_pi [n]
-// uint32 (when bit0 of flags), anc_q, anc_pi (when bit1)
+// uint32 (when bit0 of flags), anc_q, anc_pi (when bit1), then the grids of
+// the previous frame and of the anchor (d field plans each)
 constexpr uint32_t kTrajMagic = 0x5354434cu;  // "LCTS"
-constexpr uint32_t kTrajVersion = 1;
+constexpr uint32_t kTrajVersion = 2;
 struct TrajImage {
   uint32_t magic, version;
   uint32_t batch, p;
   uint64_t t, n;
-  uint32_t d, flags;  // bit0 previous frame, bit1 anchor, bit2 S size known
+  uint32_t d, flags;  // bit0 previous frame, bit1 anchor, bit2 S size known,
+                      // bit3 previous frame is a scaled anchor, bit4 anchor is
   int32_t state, counter;
   uint64_t s_est;
+  uint32_t anchor_scale, pad;
 };
-static_assert(sizeof(TrajImage) == 56, "image header layout");
+static_assert(sizeof(TrajImage) == 64, "image header layout");
 
 size_t traj_image_size(uint64_t n, uint32_t d, uint32_t flags) {
   const size_t per = (size_t)n * d * 4 + (size_t)n * 4;
-  return sizeof(TrajImage) + ((flags & 1u) ? per : 0) + ((flags & 2u) ? per : 0);
+  return sizeof(TrajImage) + ((flags & 1u) ? per : 0) + ((flags & 2u) ? per : 0) +
+         2 * (size_t)d * sizeof(FieldPlan);
 }
 }  // namespace
 
 lcp_status lcp_traj_export(const lcp_traj *t, void *host_out, size_t cap, size_t *size,
                            void *stream) {
   if (!t || !size) return LCP_ERR_ARG;
-  const uint32_t flags =
-      (t->has_prev ? 1u : 0u) | (t->has_anchor ? 2u : 0u) | (t->s_known ? 4u : 0u);
+  const uint32_t flags = (t->has_prev ? 1u : 0u) | (t->has_anchor ? 2u : 0u) |
+                         (t->s_known ? 4u : 0u) | (t->prev_scaled ? 8u : 0u) |
+                         (t->anc_scaled ? 16u : 0u);
   const size_t need = traj_image_size(t->n, t->d, flags);
   *size = need;
   if (!host_out || cap < need) return LCP_ERR_CAPACITY;
   DeviceGuard g(t->device);
   if (!g.ok) return LCP_ERR_CUDA;
   TrajImage h{kTrajMagic, kTrajVersion, t->batch, t->p, t->t, t->n, t->d, flags,
-              t->state, t->counter, t->s_est};
+              t->state, t->counter, t->s_est, t->anchor_scale, 0u};
   memcpy(host_out, &h, sizeof h);
   uint8_t *o = reinterpret_cast<uint8_t *>(host_out) + sizeof h;
   const size_t qb = (size_t)t->n * t->d * 4, pb = (size_t)t->n * 4;
@@ -720,6 +740,8 @@ lcp_status lcp_traj_export(const lcp_traj *t, void *host_out, size_t cap, size_t
     }
     o += b;
   }
+  memcpy(o, t->prev_F, (size_t)t->d * sizeof(FieldPlan));
+  memcpy(o + (size_t)t->d * sizeof(FieldPlan), t->anc_F, (size_t)t->d * sizeof(FieldPlan));
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return LCP_ERR_CUDA;
@@ -736,7 +758,8 @@ lcp_status lcp_traj_import(lcp_ctx *c, const void *host_in, size_t size, lcp_tra
   memcpy(&h, host_in, sizeof h);
   const bool shape_ok = h.n == 0 ? h.d <= 8 : (h.d >= 1 && h.d <= 8 && h.n < (1ull << 32));
   if (h.magic != kTrajMagic || h.version != kTrajVersion || h.batch == 0 || h.p == 0 ||
-      (h.p & (h.p - 1)) || h.p > 65536 || (h.flags & ~7u) || !shape_ok || h.state < 0 ||
+      (h.p & (h.p - 1)) || h.p > 65536 || (h.flags & ~31u) || !shape_ok || h.state < 0 ||
+      h.anchor_scale == 0 || h.anchor_scale > 1024 ||
       h.state > 16 || h.counter < 0 || h.counter > 16 ||
       size != traj_image_size(h.n, h.d, h.flags))
     return LCP_ERR_FORMAT;
@@ -753,6 +776,9 @@ lcp_status lcp_traj_import(lcp_ctx *c, const void *host_in, size_t size, lcp_tra
   t->has_prev = (h.flags & 1u) != 0;
   t->has_anchor = (h.flags & 2u) != 0;
   t->s_known = (h.flags & 4u) != 0;
+  t->prev_scaled = (h.flags & 8u) != 0;
+  t->anc_scaled = (h.flags & 16u) != 0;
+  t->anchor_scale = h.anchor_scale;
   t->state = h.state;
   t->counter = h.counter;
   t->s_est = h.s_est;
@@ -773,6 +799,10 @@ lcp_status lcp_traj_import(lcp_ctx *c, const void *host_in, size_t size, lcp_tra
     }
     in += b;
   }
+  if (st == OK) {
+    memcpy(t->prev_F, in, (size_t)h.d * sizeof(FieldPlan));
+    memcpy(t->anc_F, in + (size_t)h.d * sizeof(FieldPlan), (size_t)h.d * sizeof(FieldPlan));
+  }
   if (st == OK && cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     st = ERR_CUDA;
@@ -782,6 +812,12 @@ lcp_status lcp_traj_import(lcp_ctx *c, const void *host_in, size_t size, lcp_tra
     return (lcp_status)st;
   }
   *out = t;
+  return LCP_OK;
+}
+
+lcp_status lcp_traj_set_anchor_scale(lcp_traj *t, uint32_t scale) {
+  if (!t || scale == 0 || scale > 1024) return LCP_ERR_ARG;
+  t->anchor_scale = scale;
   return LCP_OK;
 }
 
@@ -833,7 +869,14 @@ int traj_compress(lcp_ctx *c, lcp_traj *t, const float *X, uint64_t n, uint32_t 
   const int32_t *rq = ref_anchor ? P<int32_t>(t->anc_q) : P<int32_t>(t->prev_q);
   const uint32_t *rpi = ref_anchor ? P<uint32_t>(t->anc_pi) : P<uint32_t>(t->prev_pi);
   const uint32_t sflags = first ? kFlagFirst : 0u;
-  const uint32_t tflags = sflags | (ref_anchor ? kFlagRefAnchor : 0u);
+  // a reference that is a scaled anchor is on another grid: value-space
+  // prediction (Sec. "Best error-bound scale for anchor frames")
+  const bool ref_scaled = has_ref && (ref_anchor ? t->anc_scaled : t->prev_scaled);
+  const FieldPlan *rgrid = ref_scaled ? (ref_anchor ? t->anc_F : t->prev_F) : nullptr;
+  const uint32_t tflags =
+      sflags | (ref_anchor ? kFlagRefAnchor : 0u) | (ref_scaled ? kFlagRequant : 0u);
+  // temporal correlation as the LCP-FSM sees it when the frame is planned
+  const bool correlated = t->state == 0 || t->state == 2;
   FsmCopy f{t->state, t->counter, t->s_known, t->s_est};
   Action a;
   if (method == LCP_SPATIAL) a = A_SPATIAL;
@@ -854,13 +897,13 @@ int traj_compress(lcp_ctx *c, lcp_traj *t, const float *X, uint64_t n, uint32_t 
     if (method != LCP_AUTO) f.s_known = true, f.s_est = s_size;
   } else if (a == A_TEMPORAL) {
     TRY(compress_t_impl(c, X, n, d, eb, mode, rpi, rq, tflags, out, cap, size_only,
-                        P<int32_t>(w.tq), &t_size, s));
+                        P<int32_t>(w.tq), &t_size, s, rgrid));
     use_t = true;
   } else if (a == A_COMPARE) {
     TRY(compress_s_impl(c, X, n, d, eb, mode, t->p, sflags, out, cap, size_only,
                         P<uint32_t>(t->new_pi), P<int32_t>(t->new_q), &s_size, s));
     int st = compress_t_impl(c, X, n, d, eb, mode, rpi, rq, tflags, P<uint8_t>(w.cand),
-                             w.cand.cap, size_only, P<int32_t>(w.tq), &t_size, s);
+                             w.cand.cap, size_only, P<int32_t>(w.tq), &t_size, s, rgrid);
     if (st != OK) return st;
     use_t = t_size < s_size;
     f.s_known = true;
@@ -876,7 +919,7 @@ int traj_compress(lcp_ctx *c, lcp_traj *t, const float *X, uint64_t n, uint32_t 
     }
   } else {  // A_TEST: LCP-T against the LCP-S estimate
     int st = compress_t_impl(c, X, n, d, eb, mode, rpi, rq, tflags, out, cap, size_only,
-                             P<int32_t>(w.tq), &t_size, s);
+                             P<int32_t>(w.tq), &t_size, s, rgrid);
     if (st != OK && st != ERR_CAPACITY) return st;
     use_t = t_size <= f.s_est;
     if (use_t && st == ERR_CAPACITY) {
@@ -897,20 +940,45 @@ int traj_compress(lcp_ctx *c, lcp_traj *t, const float *X, uint64_t n, uint32_t 
   if (est_s) *est_s = (a == A_COMPARE) ? s_size : (f.s_known ? t->s_est : 0);
   if (est_t) *est_t = t_size;
   if (!commit) return OK;
+  // an anchor while the frames are temporally correlated: coded again at
+  // eb / anchor_scale (kept at eb when that bound leaves the domain); the
+  // LCP-FSM has decided on the size at eb
+  bool scaled = false;
+  if (!use_t && first && t->anchor_scale > 1 && correlated) {
+    uint64_t s2 = 0;
+    const int st = compress_s_impl(c, X, n, d, eb / (double)t->anchor_scale, mode, t->p, sflags,
+                                   out, cap, false, P<uint32_t>(t->new_pi), P<int32_t>(t->new_q),
+                                   &s2, s);
+    if (st == OK) {
+      scaled = true;
+      *out_size = s2;
+    } else if (st == ERR_CAPACITY) {
+      *out_size = s2;
+      return st;
+    } else if (st != ERR_RANGE && st != ERR_ARG) {
+      return st;
+    }
+  }
   // commit the reference state
   if (use_t) {
     std::swap(t->prev_q, w.tq);
     if (ref_anchor)
       CK(cudaMemcpyAsync(t->prev_pi.p, t->anc_pi.p, std::max<uint64_t>(n, 1) * 4,
                          cudaMemcpyDeviceToDevice, s));
+    t->prev_scaled = false;
   } else {
     std::swap(t->prev_q, t->new_q);
     std::swap(t->prev_pi, t->new_pi);
+    t->prev_scaled = scaled;
+    if (scaled)  // the grid of the scaled anchor, from its plan
+      for (uint32_t k = 0; k < d; ++k) t->prev_F[k] = c->h_plan->f[k];
     if (first) {
       CK(cudaMemcpyAsync(t->anc_q.p, t->prev_q.p, qb, cudaMemcpyDeviceToDevice, s));
       CK(cudaMemcpyAsync(t->anc_pi.p, t->prev_pi.p, std::max<uint64_t>(n, 1) * 4,
                          cudaMemcpyDeviceToDevice, s));
       t->has_anchor = true;
+      t->anc_scaled = scaled;
+      for (uint32_t k = 0; k < d; ++k) t->anc_F[k] = t->prev_F[k];
     }
   }
   CK(cudaStreamSynchronize(s));
@@ -1229,6 +1297,14 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
     }
     prof_end(c, s);
     const int32_t *qref = ra ? P<int32_t>(t->anc_q) : P<int32_t>(t->prev_q);
+    if (h.flags & kFlagRequant) {  // the reference is on another grid
+      TRY(grow(w.rq, nd * 4));
+      RefGrid g;
+      const FieldPlan *rg = ra ? t->anc_F : t->prev_F;
+      for (uint32_t f = 0; f < h.d; ++f) g.f[f] = rg[f];
+      launch_requant(P<Plan>(w.plan), n, h.d, qref, g, P<int32_t>(w.rq), sms, s);
+      qref = P<int32_t>(w.rq);
+    }
     prof_begin(c, "t.recon", s);
     launch_recon_t(P<Plan>(w.plan), n, h.d, P<uint32_t>(w.sym), qref, out, qout, err, sms, s);
     prof_end(c, s);
@@ -1241,11 +1317,13 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
   if (*c->h_err || c->h_plan->status != OK) return ERR_FORMAT;
   if (t) {
     std::swap(t->prev_q, t->new_q);
+    for (uint32_t k = 0; k < h.d; ++k) t->prev_F[k] = c->h_plan->f[k];  // this frame's grid
     if (h.method == 0 && first) {
       CK(cudaMemcpyAsync(t->anc_q.p, t->prev_q.p, std::max<uint64_t>(n * h.d, 1) * 4,
                          cudaMemcpyDeviceToDevice, s));
       CK(cudaStreamSynchronize(s));
       t->has_anchor = true;
+      for (uint32_t k = 0; k < h.d; ++k) t->anc_F[k] = t->prev_F[k];
     }
     t->has_prev = true;
     t->n = n;

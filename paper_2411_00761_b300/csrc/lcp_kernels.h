@@ -192,6 +192,13 @@ void launch_recon_t(const Plan *plan, uint64_t n, uint32_t d, const uint32_t *sy
                     cudaStream_t s);
 void launch_patches_apply(const uint8_t *sec, uint64_t K, uint64_t nd, float *out, int *err,
                           int sms, cudaStream_t s);
+// reference codes re-quantized on the frame's grid (plan): q' =
+// clamp(Q1_frame(Q2_ref(q)), 0, qmax), per field, [d][n] int32
+struct RefGrid {
+  FieldPlan f[kMaxD];
+};
+void launch_requant(const Plan *plan, uint64_t n, uint32_t d, const int32_t *qref,
+                    const RefGrid &g, int32_t *qout, int sms, cudaStream_t s);
 
 // --- decode (k_decode.cu) --------------------------------------------------
 void launch_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan, cudaStream_t s);

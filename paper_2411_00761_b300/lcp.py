@@ -42,6 +42,7 @@ SIGNATURES = {
                                         C.POINTER(_u32), C.POINTER(_u64), _vp]),
     "lcp_traj_create": (C.c_int, [_vp, _u32, _u32, C.POINTER(C.c_void_p)]),
     "lcp_traj_destroy": (C.c_int, [_vp]),
+    "lcp_traj_set_anchor_scale": (C.c_int, [_vp, _u32]),
     "lcp_traj_export": (C.c_int, [_vp, _vp, _sz, C.POINTER(_sz), _vp]),
     "lcp_traj_import": (C.c_int, [_vp, _vp, _sz, C.POINTER(C.c_void_p), _vp]),
     "lcp_quantize": (C.c_int, [_vp, _u64, C.c_float, C.c_float, C.c_float, _vp, _vp, _vp, _vp]),
@@ -271,11 +272,13 @@ class Trajectory:
     """Reference state of one frame sequence (lcp_traj), for compressing or for
     decompressing it."""
 
-    def __init__(self, ctx: Context, batch: int = 10, p: int = 8):
+    def __init__(self, ctx: Context, batch: int = 10, p: int = 8, anchor_scale: int = 1):
         self.ctx = ctx
         h = C.c_void_p()
         _check(_lib.lcp_traj_create(ctx.h, batch, p, C.byref(h)), "lcp_traj_create")
         self.h = h
+        if anchor_scale != 1:
+            _check(_lib.lcp_traj_set_anchor_scale(h, anchor_scale), "lcp_traj_set_anchor_scale")
 
     def export(self, stream=None) -> bytes:
         """lcp_traj_export: the reference state as a host byte image."""

@@ -80,12 +80,12 @@ def test_malformed_images_are_rejected(lcp, frames):
     ctx = lcp.Context(0)
     fresh = lcp.Trajectory(ctx, batch=BATCH, p=P)
     img0 = fresh.export()
-    assert len(img0) == 56
+    assert len(img0) == 64
     lcp.Trajectory.restore(ctx, img0).close()
     tr = lcp.Trajectory(ctx, batch=BATCH, p=P)
     encode(lcp, ctx, tr, frames[0])
     img = tr.export()
-    assert len(img) == 56 + 2 * (N * 3 * 4 + N * 4)  # previous frame and anchor
+    assert len(img) == 64 + 2 * (N * 3 * 4 + N * 4) + 2 * 3 * 80  # frames, grids
     for bad in (b"XXXX" + img[4:], img[:-4], img + b"\0"):
         with pytest.raises(lcp.LcpError) as ei:
             lcp.Trajectory.restore(ctx, bad)

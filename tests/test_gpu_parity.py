@@ -278,6 +278,29 @@ def test_hybrid_trajectory_matches_oracle(ctx, orc, lcp):
         assert np.array_equal(Y.view(np.uint32), dec_o[t].view(np.uint32)), t
 
 
+@pytest.mark.parametrize("scale", [2, 5])
+def test_anchor_scaling_matches_oracle(ctx, orc, lcp, scale):
+    """Anchors at eb / scale and value-space prediction from them (Sec. "Best
+    error-bound scale for anchor frames"): containers byte-identical to the
+    oracle's Algorithm 1, frames decoded bit-identical."""
+    from oracle import hybrid
+    frames = list(synth.brownian_trajectory(20011, 10, 3, sigma=0.02))
+    enc = hybrid.encode_trajectory(frames, 1e-3, "abs", 8, batch=4, anchor_scale=scale)
+    assert any(orc.peek(b)["flags"] & hybrid.FLAG_REF_REQUANT for b, _ in enc)
+    tr = lcp.Trajectory(ctx, batch=4, p=8, anchor_scale=scale)
+    got = []
+    for X in frames:
+        r = ctx.compress(to_dev(X), 1e-3, "abs", 8, method="auto", traj=tr)
+        got.append(gpu_bytes(r))
+    for t, (b, _) in enumerate(enc):
+        assert got[t] == b, t
+    dec = hybrid.decode_trajectory([b for b, _ in enc])
+    dt = lcp.Trajectory(ctx, batch=4, p=8)
+    for t, b in enumerate(got):
+        Y = ctx.decompress(to_dev(np.frombuffer(b, np.uint8)), traj=dt).cpu().numpy()
+        assert np.array_equal(Y.view(np.uint32), dec[t].view(np.uint32)), t
+
+
 def test_select_is_a_query(ctx, lcp):
     frames = list(synth.brownian_trajectory(5000, 4, 2))
     tr = lcp.Trajectory(ctx, batch=10, p=8)
