@@ -156,6 +156,21 @@ def measured_traffic(workload: str, stage: str, N: int):
         return None
 
 
+def ranks_aggregate(ms: float, units: float, world: int, device) -> tuple[float, float]:
+    """Whole-job timing over ranks: the longest rank's time and the units (bytes)
+    all ranks processed, by all-reduce (NCCL on the GPU path, gloo in the CPU
+    tests); one rank returns its own figures."""
+    if world <= 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled while running."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -394,12 +409,8 @@ def run_batched(args):
         torch.cuda.synchronize(dev)
         seq_ms.append((time.perf_counter() - t0) * 1e3)
         advance()
-    ms = statistics.mean(t_step)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * raw / (ms * 1e-3) / 1e9
+    ms, units = ranks_aggregate(statistics.mean(t_step), float(raw), world, dev)
+    value = units / (ms * 1e-3) / 1e9
     pct = lambda v, q: float(np.percentile(np.array(v), q))
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -453,8 +464,12 @@ def run_serving(args):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    if world > 1:  # independent replicas; only the totals are combined
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
     w = WORKLOADS["serving"]
     seconds = w["seconds"] if args.seconds <= 0 else args.seconds
     rate = w["rate"] if args.rate <= 0 else args.rate
@@ -564,10 +579,14 @@ def run_serving(args):
             comp_bytes += r["size"]
     span_s = (last_t - first_t) * 1e-3 if first_t is not None else 1.0
     allv = lat["compress"] + lat["decompress"]
+    # whole job: bytes of all replicas over the longest replica's span
+    span_ms, raw_all = ranks_aggregate(span_s * 1e3, float(raw_done), world, dev)
+    _, n_all = ranks_aggregate(0.0, float(len(allv)), world, dev)
     pct = lambda v, q: float(np.percentile(np.array(v), q)) if v else None
     line = {
         "metric": "compress/decompress GB/s vs HBM peak at fixed eb + ratio; batched p50/p99 ms",
-        "value": raw_done / span_s / 1e9, "unit": "GB/s", "n_gpus": 1, "steps": len(allv),
+        "value": raw_all / (span_ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": world,
+        "steps": len(allv),
         "warmup": int(sum(1 for _, r in done_list if r["enqueue_ms"] < warm_ms)),
         "ms_per_step": span_s * 1e3 / max(len(allv), 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 in, integer codes",
@@ -576,12 +595,13 @@ def run_serving(args):
                    "offered_rate_req_s": rate, "seconds": seconds, "lanes": w["lanes"],
                    "max_pending": max_pending,
                    "batch": w["batch"], "hbm_budget_gb": w["budget_gb"],
-                   "parallelism": "single GPU, lanes overlap requests"},
+                   "parallelism": (f"{world} independent replicas (latency figures: rank 0)"
+                                   if world > 1 else "single GPU, lanes overlap requests")},
         "p50_ms": pct(allv, 50), "p99_ms": pct(allv, 99),
         "compress_p50_ms": pct(lat["compress"], 50), "compress_p99_ms": pct(lat["compress"], 99),
         "decompress_p50_ms": pct(lat["decompress"], 50),
         "decompress_p99_ms": pct(lat["decompress"], 99),
-        "achieved_rate_req_s": len(allv) / span_s, "requests_done": len(allv),
+        "achieved_rate_req_s": n_all / (span_ms * 1e-3), "requests_done": int(n_all),
         "offered": int(arrivals.size), "rejected_by_budget": rejected, "shed": shed,
         "failed_by_status": failed,
         "ratio": comp_raw / max(comp_bytes, 1), "server_device_gb": mem / 1e9,
@@ -590,6 +610,8 @@ def run_serving(args):
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
@@ -690,13 +712,9 @@ def main():
             dist.barrier()
     launches = lcp.kernel_launches() - launches0
     ctx.profile(False)
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms, units = ranks_aggregate(t_start.elapsed_time(t_end), float(raw), world, dev)
     ms_step = total_ms / args.steps
-    value = world * raw / (ms_step * 1e-3) / 1e9
+    value = units / (ms_step * 1e-3) / 1e9
     tcm, tdm = statistics.mean(tc), statistics.mean(td)
     peak, peak_kind = peaks()
 
