@@ -135,6 +135,41 @@ LCP_API lcp_status lcp_decompress(lcp_ctx *ctx, lcp_traj *traj, const void *d_in
                           float *d_out, uint64_t n_cap, uint64_t *n_out, uint32_t *d_fields,
                           void *stream);
 
+/*
+ * Random-access retrieval (Sec. "Spatial-Anchor-Frame-Based Batch
+ * Compression", its recursive decompression): frames first..last of one
+ * trajectory, decoded into d_outs[0 .. last - first] ([d][n_cap] each).
+ *   d_containers / sizes: host arrays of `count` entries, entry i the
+ *     container of the trajectory's frame i (device pointer) in stream order,
+ *     as lcp_compress wrote them.  Frames the request does not need may be
+ *     NULL (e.g. evicted).
+ *   A frame depends on its batch's frames before it and, when its batch
+ *   opens with an LCP-T frame, on the batch's anchor (the latest earlier
+ *   batch opening coded LCP-S).  The call decodes from the latest LCP-S frame
+ *   of first's batch at or before first (else from the anchor); frames
+ *   before `first` are decoded to codes only (no values written).  Besides
+ *   those frames, the batch openings between the anchor and first's batch
+ *   must be present (their headers show which one is the anchor).
+ *   dec: a decoder-side trajectory created with the stream's batch size
+ *     (frame t opens a batch when t % batch = 0), used as scratch state; the
+ *     call resets it and leaves it holding frame `last` as its previous frame.
+ *   ERR_STATE when a frame the chain needs is NULL or no anchor precedes an
+ *   LCP-T batch opening; ERR_ARG when the stream's batch openings do not
+ *   match dec's batch size; ERR_FORMAT for a container that is not LCP1.
+ * *n_out / *d_fields receive the shape of the frames returned.  Synchronizes
+ * `stream` (once per header round and per decoded frame).
+ */
+LCP_API lcp_status lcp_decompress_frames(lcp_ctx *ctx, lcp_traj *dec,
+                                 const void *const *d_containers, const size_t *sizes,
+                                 uint64_t count, uint64_t first, uint64_t last,
+                                 float *const *d_outs, uint64_t n_cap, uint64_t *n_out,
+                                 uint32_t *d_fields, void *stream);
+/* One frame (first = last = target) of lcp_decompress_frames. */
+LCP_API lcp_status lcp_decompress_frame(lcp_ctx *ctx, lcp_traj *dec,
+                                const void *const *d_containers, const size_t *sizes,
+                                uint64_t count, uint64_t target, float *d_out, uint64_t n_cap,
+                                uint64_t *n_out, uint32_t *d_fields, void *stream);
+
 /* Reads n, d, method and flags from a container's header (device memory). */
 LCP_API lcp_status lcp_peek(const void *d_in, size_t in_size, uint64_t *n, uint32_t *d,
                     lcp_method *method, uint32_t *flags, void *stream);
@@ -357,9 +392,10 @@ LCP_API int lcp_ctx_profile_read(lcp_ctx *ctx, char *names, float *ms, int cap);
  *   q[i]    = floor((x[i] - m) / (2 e))            (Eq. quantization)
  *   xr[i]   = RN32(m + (2 q[i] + 1) e)             (reverse quantization)
  *   viol[i] = |x[i] - xr[i]| > e                   (Eq. abs violated)
- * all over the reals, bit-exact.  Requires x[i] >= m, q < 2^30 and
- * |x|, |m| < 2^32 * 2e (ERR_RANGE otherwise; checked per call on the host
- * from m, e and the caller-supplied max_abs bound).
+ * all over the reals, bit-exact.  Requires x[i] >= m (results are
+ * unspecified otherwise) and q < 2^30 (ERR_RANGE otherwise, checked on the
+ * device for every value).  max_abs is unused; it is kept so that the
+ * signature stays stable.
  */
 LCP_API lcp_status lcp_quantize(const float *d_x, uint64_t n, float m, float e, float max_abs,
                         int32_t *d_q, float *d_xr, uint8_t *d_viol, void *stream);
@@ -379,8 +415,9 @@ LCP_API lcp_status lcp_quantize(const float *d_x, uint64_t n, float m, float e, 
  *   - n may be at most LCP_NOALLOC_MAX_ELEMENTS; larger n returns LCP_ERR_ARG
  *     before any work is queued.
  *   - The first call on each device resolves the device address of that
- *     array (cudaGetSymbolAddress); make that first call before any stream
- *     capture.
+ *     array (cudaGetSymbolAddress).
+ *   - No call can be recorded inside a stream capture: every call
+ *     synchronizes `stream` and copies its status to the host.
  *   - All calls share the array: the call clears the counter it needs, but
  *     two calls whose work overlaps on the GPU (on different streams, or
  *     from different threads) race on it.  Serialize them.

@@ -243,14 +243,17 @@ int orc_plan(const float *fields, uint64_t n, uint32_t d, double eb, int eb_mode
     plan[f].max_f = mx;
     plan[f].eb_f = ebf;
     plan[f].e = e;
-    /* a quotient estimate at or above 2^31 is certainly out of range (the
-     * exact count below is then skipped); otherwise the exact floor decides */
+    /* The bins of a field must number below 2^30 (the key space rule).  A
+     * quotient estimate at or above 2^31 settles that without the exact
+     * count: the double estimate is within a relative 2^-51 of the exact
+     * quotient, whose floor is then at least 2^31 - 1 >= 2^30, so the frame
+     * is refused exactly when the exact rule below would refuse it. */
     double qest = ((double)mx - (double)mn) / (2.0 * (double)e);
     if (!(qest < 2147483648.0)) return ORC_ERR_RANGE;
     int64_t qmax = orc_q1(mx, mn, e);
     if (qmax >= (1ll << 30)) return ORC_ERR_RANGE;
-    double amax = fmax(fabs((double)mn), fabs((double)mx));
-    if (!(amax < ldexp(2.0 * (double)e, 32))) return ORC_ERR_RANGE;
+    /* No rule on |value| / eb: Eq. quantization is defined for every real
+     * value, and the exact arithmetic above covers every finite binary32. */
     plan[f].qmax = (uint32_t)qmax;
   }
   return ORC_OK;

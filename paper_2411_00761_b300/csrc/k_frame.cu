@@ -267,7 +267,8 @@ void launch_quantize_s(const float *fields, uint64_t n, uint32_t d, const Plan *
 // ---------------------------------------------------------------------------
 __global__ void k_element_rules(const float *__restrict__ x, uint64_t n,
                                 const FieldPlan *__restrict__ fp, int32_t *__restrict__ q,
-                                float *__restrict__ xr, uint8_t *__restrict__ viol) {
+                                float *__restrict__ xr, uint8_t *__restrict__ viol,
+                                int *__restrict__ status) {
   const FieldPlan F = *fp;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (uint64_t)gridDim.x * blockDim.x) {
@@ -278,6 +279,7 @@ __global__ void k_element_rules(const float *__restrict__ x, uint64_t n,
     q[i] = qq;
     xr[i] = r;
     viol[i] = violates(v, r, F.e) ? 1 : 0;
+    if (qq < 0 || qq >= (1 << 30)) atomicExch(status, ERR_RANGE);  // outside the domain
   }
 }
 
@@ -287,18 +289,18 @@ __global__ void k_field_plan(float m, float e, float max_abs, FieldPlan *fp, int
   FieldPlan F;
   double ebf = (double)e;
   int st = plan_field(m, m, ebf, 0, 0, F);
-  if (st == OK && !((double)max_abs < ldexp(2.0 * (double)e, 32))) st = ERR_RANGE;
+  (void)max_abs;  // bounds q on the host (q < 2^30); no rule on |x| here
   *fp = F;
   *status = st;
 }
 
 void launch_element_rules(const float *x, uint64_t n, FieldPlan *fp_dev, int32_t *q, float *xr,
-                          uint8_t *viol, cudaStream_t s) {
+                          uint8_t *viol, int *status, cudaStream_t s) {
   if (n == 0) return;
   uint64_t blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   note_launch();
-  k_element_rules<<<(unsigned)blocks, 256, 0, s>>>(x, n, fp_dev, q, xr, viol);
+  k_element_rules<<<(unsigned)blocks, 256, 0, s>>>(x, n, fp_dev, q, xr, viol, status);
 }
 
 void launch_field_plan(float m, float e, float max_abs, FieldPlan *fp, int *status,

@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kNaThreads) k_element_rules_noalloc(
   __shared__ bool s_last;
   if (threadIdx.x == 0) {
     st = plan_field(m, m, (double)e, 0, 0, F);
-    if (st == OK && !((double)max_abs < ldexp(2.0 * (double)e, 32))) st = ERR_RANGE;
+    (void)max_abs;  // unused: the kernel checks q < 2^30 on every value
     s_cnt = 0u;
   }
   __syncthreads();
@@ -67,11 +67,14 @@ __global__ void __launch_bounds__(kNaThreads) k_element_rules_noalloc(
         xr[i] = r;
         viol[i] = bad ? 1 : 0;
         c += bad;
+        if (qq < 0 || qq >= (1 << 30)) c |= 0x80000000u;  // outside the domain
       }
     }
   }
-  c = __reduce_add_sync(0xffffffffu, c);
+  const bool out_of_range = __any_sync(0xffffffffu, (c & 0x80000000u) != 0u);
+  c = __reduce_add_sync(0xffffffffu, c & 0x7fffffffu);
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(&s_cnt, c);
+  if ((threadIdx.x & 31) == 0 && out_of_range) atomicOr(&s_cnt, 0x80000000u);
   __syncthreads();
   if (threadIdx.x == 0) {
     scr->partial[blockIdx.x] = s_cnt;
@@ -82,10 +85,14 @@ __global__ void __launch_bounds__(kNaThreads) k_element_rules_noalloc(
   if (s_last && threadIdx.x == 0) {
     __threadfence();
     unsigned long long t = 0;
-    for (unsigned int b = 0; b < gridDim.x; ++b)
-      t += *(volatile unsigned int *)&scr->partial[b];
+    bool range = false;
+    for (unsigned int b = 0; b < gridDim.x; ++b) {
+      const unsigned int v = *(volatile unsigned int *)&scr->partial[b];
+      t += v & 0x7fffffffu;
+      range |= (v & 0x80000000u) != 0u;
+    }
     scr->total = t;
-    scr->status = st;
+    scr->status = (st == OK && range) ? ERR_RANGE : st;
   }
 }
 
@@ -121,8 +128,6 @@ extern "C" lcp_status lcp_quantize_noalloc(const float *d_x, uint64_t n, float m
   if (n > LCP_NOALLOC_MAX_ELEMENTS) return LCP_ERR_ARG;
   if (n > 0 && (!d_x || !d_q || !d_xr || !d_viol)) return LCP_ERR_ARG;
   if (!(e > 0.0f)) return LCP_ERR_ARG;
-  double qest = ((double)max_abs + fabs((double)m)) / (2.0 * (double)e);
-  if (!(qest < 1073741824.0)) return LCP_ERR_RANGE;
   NoallocScratch *scr = nullptr;
   int st = noalloc_scratch(&scr);
   if (st != OK) return (lcp_status)st;

@@ -121,8 +121,10 @@ __global__ void __launch_bounds__(512) k_recon_t(const Plan *__restrict__ plan, 
       atomicExch(err, 1);
       q = 0;
     }
-    float z;
-    out[s] = recon_rn_f32(q, F.m, F.e, z) ? z : reconstruct(q, F);
+    if (out) {  // null: codes only (a reference frame)
+      float z;
+      out[s] = recon_rn_f32(q, F.m, F.e, z) ? z : reconstruct(q, F);
+    }
     qnew[s] = (int32_t)q;
   }
 }

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "../../include/lcp.h"
 #include "lcp_kernels.h"
@@ -50,7 +51,7 @@ struct Workspace {
       s_id, s_cnt, hist, maxv, nvals, mcount, kcount, desc, codes, lens,
       tables, chunk_bits, chunk_off, outl_idx, summary, q_in, q_slot, perm, sym, patch_s,
       patch_i, patch_x, patch_s2, patch_i2, patch_so, patch_io, dec_fields, hufft, err,
-      scan_tmp, scan_base, bid, counts, starts, cand, tq, fplan, fstatus, cbwork, sample, rq;
+      scan_tmp, cand, tq, fplan, fstatus, cbwork, sample, rq, lut;
 };
 
 __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
@@ -1136,7 +1137,10 @@ struct Header {
 int read_header(lcp_ctx *c, const uint8_t *in, size_t in_size, Header &h, cudaStream_t s) {
   if (!in || !aligned16(in) || in_size < 48) return ERR_FORMAT;
   uint8_t *st = c->h_stage;
-  CK(cudaMemcpyAsync(st, in, 48, cudaMemcpyDeviceToHost, s));
+  // the fixed header with the largest field table and directory (8 fields, 4
+  // sections): one copy
+  const size_t head = std::min<size_t>(in_size, 48 + 16 * 8 + 16 * 4 + 16);
+  CK(cudaMemcpyAsync(st, in, head, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (st[0] != 'L' || st[1] != 'C' || st[2] != 'P' || st[3] != '1' || st[4] != 1) return ERR_FORMAT;
   h.method = st[5];
@@ -1152,9 +1156,7 @@ int read_header(lcp_ctx *c, const uint8_t *in, size_t in_size, Header &h, cudaSt
   h.total = rd64(st + 40);
   h.ns = h.method == 0 ? 3 : 1;
   const uint64_t H = 48ull + 16ull * h.d + 16ull * h.ns + 16ull;
-  if (h.total > in_size || h.total < H || h.n >= (1ull << 32)) return ERR_FORMAT;
-  CK(cudaMemcpyAsync(st, in, H, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  if (h.total > in_size || h.total < H || h.n >= (1ull << 32) || H > head) return ERR_FORMAT;
   for (uint32_t f = 0; f < h.d; ++f) {
     memcpy(&h.m[f], st + 48 + 16 * f, 4);
     memcpy(&h.e[f], st + 52 + 16 * f, 4);
@@ -1211,14 +1213,22 @@ int read_header(lcp_ctx *c, const uint8_t *in, size_t in_size, Header &h, cudaSt
   return OK;
 }
 
+// codes_only: a frame decoded only as the reference of later frames (its
+// codes into the trajectory, no values; out is ignored)
 int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, float *out,
-                    uint64_t n_cap, uint64_t *n_out, uint32_t *d_out, cudaStream_t s) {
+                    uint64_t n_cap, uint64_t *n_out, uint32_t *d_out, cudaStream_t s,
+                    bool codes_only = false) {
   Header h;
   TRY(read_header(c, in, in_size, h, s));
   if (n_out) *n_out = h.n;
   if (d_out) *d_out = h.d;
-  if (h.n > n_cap) return ERR_CAPACITY;
-  if (h.n > 0 && (!out || !aligned16(out))) return ERR_ARG;
+  if (codes_only) {
+    if (!t) return ERR_ARG;
+    out = nullptr;
+  } else {
+    if (h.n > n_cap) return ERR_CAPACITY;
+    if (h.n > 0 && (!out || !aligned16(out))) return ERR_ARG;
+  }
   const bool first = (h.flags & kFlagFirst) != 0;
   const bool ra = (h.flags & kFlagRefAnchor) != 0;
   if (h.method == 1) {
@@ -1251,36 +1261,69 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
   int32_t *qout = t ? P<int32_t>(t->new_q) : nullptr;
   if (h.method == 0) {
     const uint64_t nb = n - h.K, M = h.M, mm = std::max<uint64_t>(M, 1);
-    TRY(grow(w.s_id, mm * 8));
-    TRY(grow(w.s_cnt, mm * 8));
-    TRY(grow(w.s_rel, nn * 4));
-    TRY(grow(w.bid, mm * 8));
-    TRY(grow(w.counts, mm * 8));
-    TRY(grow(w.starts, mm * 8));
-    TRY(grow(w.btot, 16));
-    const uint64_t tiles = mm / 4096 + 2;
-    TRY(grow(w.scan_tmp, tiles * 8));
-    TRY(grow(w.scan_base, (tiles + 1) * 8));
+    // block-id and count deltas in 4 bytes unless a stream's largest value
+    // needs 8; relative-location deltas of a fixed-width stream are read by
+    // the expand straight from the container
+    const bool wide = h.si[0].maxv >= (1ull << 32) || h.si[1].maxv >= (1ull << 32);
+    const bool rel_fixed = h.si[2].coder == 0;
+    TRY(grow(w.s_id, mm * (wide ? 8 : 4)));
+    TRY(grow(w.s_cnt, mm * (wide ? 8 : 4)));
+    if (!rel_fixed) TRY(grow(w.s_rel, nn * 4));
+    // block-scan aggregates: one per chunk from the Huffman decode when both
+    // block streams are Huffman-coded, else one per 1024 blocks
+    const bool fused = h.si[0].coder == 1 && h.si[1].coder == 1;
+    const uint32_t agg_log2 = fused ? h.log2_chunk : 10u;
+    TRY(grow(w.scan_tmp, block_bases_bytes(mm, agg_log2)));
+    LutOffsets lo;
+    lo.off[0] = 0;
+    for (uint32_t f = 0; f < h.d; ++f)
+      lo.off[f + 1] = (uint32_t)std::min<uint64_t>((uint64_t)lo.off[f] + h.qmax[f] + 1ull,
+                                                  0xffffffffull);
+    const bool lut = out && lo.off[h.d] <= kLutMax;
+    if (lut) TRY(grow(w.lut, (size_t)lo.off[h.d] * 4));
     prof_begin(c, "d.streams", s);
     {
       const uint8_t *secs[3] = {in + h.off[0], in + h.off[1], in + h.off[2]};
-      void *outs[3] = {w.s_id.p, w.s_cnt.p, w.s_rel.p};
-      const int wide[3] = {1, 1, 0};
-      launch_decode_streams(3, secs, h.si, ht, outs, wide, err, sms, s);
+      void *outs[3] = {w.s_id.p, w.s_cnt.p, rel_fixed ? nullptr : w.s_rel.p};
+      const int wd[3] = {wide ? 1 : 0, wide ? 1 : 0, 0};
+      const int am[3] = {fused ? 1 : 0, fused ? 2 : 0, 0};
+      launch_decode_streams(3, secs, h.si, ht, outs, wd, am, w.scan_tmp.p, err, sms, s);
       CK(cudaGetLastError());
     }
     prof_end(c, s);
     if (M > 0) {
-      TRY(grow(w.scan_tmp, block_bases_bytes(M)));
       prof_begin(c, "d.block_scans", s);
-      launch_block_bases(P<unsigned long long>(w.s_id), P<unsigned long long>(w.s_cnt), M,
-                         w.scan_tmp.p, s);
+      if (!fused) launch_block_sums(w.s_id.p, w.s_cnt.p, wide ? 1 : 0, M, w.scan_tmp.p, s);
+      launch_block_bases(M, agg_log2, w.scan_tmp.p, s);
+      if (lut) launch_recon_lut(P<Plan>(w.plan), h.d, lo, P<float>(w.lut), sms, s);
       CK(cudaGetLastError());
       prof_end(c, s);
+      ExpandArgs ea;
+      ea.plan = P<Plan>(w.plan);
+      ea.sid = w.s_id.p;
+      ea.scnt = w.s_cnt.p;
+      ea.wide = wide ? 1 : 0;
+      ea.M = M;
+      ea.tiles = (M + 1023) / 1024;
+      ea.agg = w.scan_tmp.p;
+      ea.agg_log2 = agg_log2;
+      ea.rel = rel_fixed ? nullptr : P<uint32_t>(w.s_rel);
+      ea.rel_pl = reinterpret_cast<const uint32_t *>(in + h.off[2] + 32);
+      ea.rel_w = h.si[2].width;
+      ea.rel_words = words_of(h.si[2].payload_bits);
+      ea.nb = nb;
+      ea.n = n;
+      ea.log2_chunk = h.log2_chunk;
+      ea.lut = lut ? P<float>(w.lut) : nullptr;
+      ea.lut_off = lo;
+      for (uint32_t f = 0; f < kMaxD; ++f) ea.qmax[f] = f < h.d ? h.qmax[f] : 0u;
+      ea.lp = h.lp;
+      ea.out = out;
+      ea.qout = qout;
+      ea.err = err;
       prof_begin(c, "d.expand", s);
-      launch_expand_blocks(h.d, P<Plan>(w.plan), P<unsigned long long>(w.s_id),
-                           P<unsigned long long>(w.s_cnt), M, w.scan_tmp.p,
-                           P<uint32_t>(w.s_rel), nb, n, h.log2_chunk, out, qout, err, s);
+      launch_expand(h.d, ea, lut, sms, s);
+      CK(cudaGetLastError());
       prof_end(c, s);
     }
     launch_outliers_decode(P<Plan>(w.plan), reinterpret_cast<const float *>(in + h.off[3]), h.K,
@@ -1293,7 +1336,7 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
       const uint8_t *secs[1] = {in + h.off[0]};
       void *outs[1] = {w.sym.p};
       const int wide[1] = {0};
-      launch_decode_streams(1, secs, h.si, ht, outs, wide, err, sms, s);
+      launch_decode_streams(1, secs, h.si, ht, outs, wide, nullptr, nullptr, err, sms, s);
     }
     prof_end(c, s);
     const int32_t *qref = ra ? P<int32_t>(t->anc_q) : P<int32_t>(t->prev_q);
@@ -1308,7 +1351,7 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
     prof_begin(c, "t.recon", s);
     launch_recon_t(P<Plan>(w.plan), n, h.d, P<uint32_t>(w.sym), qref, out, qout, err, sms, s);
     prof_end(c, s);
-    launch_patches_apply(in + h.off[1], h.K, n * h.d, out, err, sms, s);
+    if (out) launch_patches_apply(in + h.off[1], h.K, n * h.d, out, err, sms, s);
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(c->h_err, w.err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1346,6 +1389,143 @@ lcp_status lcp_decompress(lcp_ctx *c, lcp_traj *traj, const void *d_in, size_t i
   prof_reset(c);
   return (lcp_status)decompress_impl(c, traj, (const uint8_t *)d_in, in_size, d_out, n_cap, n_out,
                                      d_fields, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+namespace {
+
+// method (0 S, 1 T) and flags of container i, read in rounds of up to 64
+// headers per synchronization, newest first
+struct ChainPeek {
+  lcp_ctx *c;
+  const void *const *ins;
+  const size_t *sizes;
+  cudaStream_t s;
+  std::vector<int> method;  // -1: not read yet
+  std::vector<uint32_t> flags;
+  int get(uint64_t i, int &m, uint32_t &f) {
+    if (method[i] < 0) {
+      const uint64_t lo = i >= 63 ? i - 63 : 0;
+      uint8_t *st = c->h_stage;
+      for (uint64_t k = lo; k <= i; ++k) {
+        if (!ins[k] || sizes[k] < 48) continue;
+        CK(cudaMemcpyAsync(st + 16 * (k - lo), ins[k], 16, cudaMemcpyDeviceToHost, s));
+      }
+      CK(cudaStreamSynchronize(s));
+      for (uint64_t k = lo; k <= i; ++k) {
+        if (method[k] >= 0) continue;
+        const uint8_t *h = st + 16 * (k - lo);
+        if (!ins[k] || sizes[k] < 48) {
+          method[k] = 2;  // absent
+          continue;
+        }
+        if (h[0] != 'L' || h[1] != 'C' || h[2] != 'P' || h[3] != '1' || h[5] > 1)
+          return ERR_FORMAT;
+        method[k] = h[5];
+        flags[k] = rd32(h + 8);
+      }
+    }
+    m = method[i];
+    f = flags[i];
+    return OK;
+  }
+};
+
+// Frames first..last of one trajectory (Algorithm 1 stream order) through
+// the recursive rule of Sec. "Spatial-Anchor-Frame-Based Batch Compression":
+// a frame depends on the frames of its batch before it and, when its batch
+// opens with an LCP-T frame, on the batch's anchor (the latest earlier batch
+// opening coded LCP-S; frame t opens a batch when t % batch = 0, batch
+// being the decoder trajectory's).  Decoding starts at the latest LCP-S
+// frame of first's batch at or before first, else at the anchor; frames
+// before first are decoded to codes only.
+int decompress_range(lcp_ctx *c, lcp_traj *t, const void *const *ins, const size_t *sizes,
+                     uint64_t count, uint64_t first, uint64_t last, float *const *outs,
+                     uint64_t n_cap, uint64_t *n_out, uint32_t *d_out, cudaStream_t s) {
+  if (!t || !ins || !sizes || !outs || first > last || last >= count) return ERR_ARG;
+  for (uint64_t i = first; i <= last; ++i)
+    if (!ins[i] || !outs[i - first]) return ERR_ARG;
+  ChainPeek pk{c, ins, sizes, s, std::vector<int>(last + 1, -1),
+               std::vector<uint32_t>(last + 1, 0u)};
+  const uint64_t B = t->batch;
+  int m;
+  uint32_t f;
+  // back from `first` to the latest LCP-S frame, or to a batch opening coded
+  // LCP-T (which needs the anchor)
+  uint64_t start = first;
+  bool need_anchor = false;
+  for (;;) {
+    TRY(pk.get(start, m, f));
+    if (m == 2) return ERR_STATE;  // a frame the chain needs is absent
+    if (((f & kFlagFirst) != 0) != (start % B == 0)) return ERR_ARG;  // batch size differs
+    if (m == 0) break;
+    if (f & kFlagFirst) {
+      need_anchor = true;
+      break;
+    }
+    if (start == 0) return ERR_FORMAT;
+    --start;
+  }
+  std::vector<uint64_t> chain;
+  if (need_anchor) {  // the latest earlier batch opening coded LCP-S
+    uint64_t a = start;
+    bool found = false;
+    while (a >= B) {
+      a -= B;
+      TRY(pk.get(a, m, f));
+      if (m == 2) return ERR_STATE;  // cannot tell whether it was the anchor
+      if (!(f & kFlagFirst)) return ERR_ARG;
+      if (m == 0) {
+        found = true;
+        break;
+      }
+    }
+    if (!found) return ERR_STATE;
+    chain.push_back(a);
+  }
+  for (uint64_t i = start; i <= last; ++i) chain.push_back(i);
+  // a fresh decoder state
+  t->has_prev = t->has_anchor = false;
+  t->prev_scaled = t->anc_scaled = false;
+  t->t = 0;
+  for (uint64_t i : chain) {
+    const bool want = i >= first;
+    uint64_t no = 0;
+    uint32_t dd = 0;
+    TRY(decompress_impl(c, t, reinterpret_cast<const uint8_t *>(ins[i]), sizes[i],
+                        want ? outs[i - first] : nullptr, n_cap, &no, &dd, s, !want));
+    if (want) {
+      if (n_out) *n_out = no;
+      if (d_out) *d_out = dd;
+    }
+  }
+  return OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lcp_status lcp_decompress_frames(lcp_ctx *c, lcp_traj *dec, const void *const *d_containers,
+                                 const size_t *sizes, uint64_t count, uint64_t first,
+                                 uint64_t last, float *const *d_outs, uint64_t n_cap,
+                                 uint64_t *n_out, uint32_t *d_fields, void *stream) {
+  if (!c) return LCP_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  prof_reset(c);
+  return (lcp_status)decompress_range(c, dec, d_containers, sizes, count, first, last, d_outs,
+                                      n_cap, n_out, d_fields, (cudaStream_t)stream);
+}
+
+lcp_status lcp_decompress_frame(lcp_ctx *c, lcp_traj *dec, const void *const *d_containers,
+                                const size_t *sizes, uint64_t count, uint64_t target,
+                                float *d_out, uint64_t n_cap, uint64_t *n_out,
+                                uint32_t *d_fields, void *stream) {
+  float *outs[1] = {d_out};
+  return lcp_decompress_frames(c, dec, d_containers, sizes, count, target, target, outs, n_cap,
+                               n_out, d_fields, stream);
 }
 
 lcp_status lcp_peek(const void *d_in, size_t in_size, uint64_t *n, uint32_t *d,
@@ -1391,14 +1571,14 @@ lcp_status lcp_quantize(const float *d_x, uint64_t n, float m, float e, float ma
   } else if (hst != OK) {
     r = (lcp_status)hst;
   } else {
-    // every q must stay below 2^30
-    double qest = ((double)max_abs + fabs((double)m)) / (2.0 * (double)e);
-    if (!(qest < 1073741824.0)) r = LCP_ERR_RANGE;
-    else {
-      launch_element_rules(d_x, n, fp, d_q, d_xr, d_viol, s);
-      if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
-        r = LCP_ERR_CUDA;
-    }
+    // every q must stay below 2^30: checked by the kernel on every value
+    launch_element_rules(d_x, n, fp, d_q, d_xr, d_viol, stp, s);
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(&hst, stp, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      r = LCP_ERR_CUDA;
+    else if (hst != OK)
+      r = (lcp_status)hst;
   }
   cudaFreeAsync(fp, s);
   cudaStreamSynchronize(s);

@@ -48,7 +48,8 @@ struct FieldPlan {
   uint32_t c8;          // mantissa of e, times 8
   long long mb;         // floor(m / 2^(g1 + 1))
   uint32_t sticky;      // m has bits below 2^(g1 + 1)
-  uint32_t pad0;
+  uint32_t wide;        // |value| can reach 2^32 * 2e: c8, mb and sticky are
+                        // unused and Q2 takes the 320-bit path
   unsigned long long bn;      // blocks along this axis
   unsigned long long stride;  // block-id stride of this axis
   unsigned long long bmagic;  // r / bn = umulhi(r, bmagic) >> bshift (r < 2^63, bn >= 2)
@@ -380,6 +381,7 @@ static __device__ __noinline__ float recon_wide(long long q, const FieldPlan &F)
 // because |2V| >= 2^26 whenever m has bits below the grid.  Falls back when
 // the result is subnormal (a second rounding would be needed).
 __device__ __forceinline__ float reconstruct(long long q, const FieldPlan &F) {
+  if (F.wide) return recon_wide(q, F);
   long long V = (2 * q + 1) * (long long)F.c8 + F.mb;
   long long W = 2 * V + (long long)F.sticky;
   float r = __ll2float_rn(W);
@@ -430,6 +432,7 @@ static __device__ __noinline__ float recon_slow(long long q, const FieldPlan &F)
 __device__ __forceinline__ float reconstruct_c(long long q, uint32_t c8, long long mb,
                                                uint32_t sticky, int32_t g1,
                                                const FieldPlan &Fs) {
+  if (Fs.wide) return recon_wide(q, Fs);
   long long V = (2 * q + 1) * (long long)c8 + mb;
   long long W = 2 * V + (long long)sticky;
   float r = __ll2float_rn(W);
@@ -454,8 +457,12 @@ __device__ __forceinline__ bool violates(float x, float xr, float e) {
 
 // ---------------------------------------------------------------------------
 // field plan from min, max and the requested bound (domain rules in order:
-// bound outside [2^-100, 2^100] -> ERR_ARG; 2^30 bins or more -> ERR_RANGE;
-// |value| >= 2^32 * 2e -> ERR_RANGE)
+// bound outside [2^-100, 2^100] -> ERR_ARG; 2^30 bins or more -> ERR_RANGE).
+// A field whose minimum reaches 2^32 * 2e in magnitude is marked wide: its
+// centre no longer fits the 64-bit form of reconstruct(), so Q2 runs on the
+// exact 320-bit path there (Q1 and Q3 need no change).  W = 2 ((2q + 1) c8
+// + mb) + sticky stays below 2^62 when |m| < 2^33 e: (2q + 1) c8 < 2^58 and
+// |mb| <= |m| 2^27 / e < 2^60.
 // ---------------------------------------------------------------------------
 __device__ inline int plan_field(float mn, float mx, double eb, int mode, uint32_t lp, FieldPlan &F) {
   double range = (double)mx - (double)mn;
@@ -480,8 +487,8 @@ __device__ inline int plan_field(float mn, float mx, double eb, int mode, uint32
   bool chk;
   int32_t qmax = quantize(mx, F, chk);
   if (qmax >= (1 << 30) || qmax < 0) return ERR_RANGE;
-  if (!(amax < ldexp(2.0 * (double)e, 32))) return ERR_RANGE;
   F.qmax = (uint32_t)qmax;
+  F.wide = (fabs((double)mn) < ldexp(2.0 * (double)e, 32)) ? 0u : 1u;
   // reconstruction constants: grid 2^G, G = (lsb exponent of e) - 3
   int eneg, Ee, mneg, Em;
   uint32_t Me, Mm;
@@ -492,7 +499,7 @@ __device__ inline int plan_field(float mn, float mx, double eb, int mode, uint32
   F.c8 = Me << 3;
   long long mb = 0;
   uint32_t st = 0;
-  if (Mm != 0) {
+  if (Mm != 0 && !F.wide) {
     if (Em >= G) {
       mb = (long long)((unsigned long long)Mm << (Em - G));
       if (mneg) mb = -mb;

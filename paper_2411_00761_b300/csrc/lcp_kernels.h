@@ -47,8 +47,9 @@ void launch_quantize_s(const float *fields, uint64_t n, uint32_t d, const Plan *
                        int32_t *q, cudaStream_t s);
 void launch_field_plan(float m, float e, float max_abs, FieldPlan *fp, int *status,
                        cudaStream_t s);
+// status: set to ERR_RANGE when a code falls outside [0, 2^30)
 void launch_element_rules(const float *x, uint64_t n, FieldPlan *fp_dev, int32_t *q, float *xr,
-                          uint8_t *viol, cudaStream_t s);
+                          uint8_t *viol, int *status, cudaStream_t s);
 
 // --- partition and segmentation (k_sort.cu) -----------------------------
 // exclusive scan, out[n] = total; skipped when gate is given and *gate != 1
@@ -204,26 +205,59 @@ void launch_requant(const Plan *plan, uint64_t n, uint32_t d, const int32_t *qre
 void launch_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan, cudaStream_t s);
 void launch_huff_table(const uint8_t *sec, HuffTable *T, cudaStream_t s);
 // decodes ns streams (secs[k], infos[k]) into outs[k] (8-byte values when
-// wide[k], else 4-byte); Huffman streams share one launch (tables ht[k])
+// wide[k], else 4-byte; a null outs[k] skips the stream); Huffman streams
+// share one launch (tables ht[k]).  agg_mode[k] (optional): 1 = the stream
+// holds LCP-S block-id deltas, 2 = count deltas; its Huffman lanes then also
+// write one block-scan aggregate per chunk into agg
 void launch_decode_streams(int ns, const uint8_t *const *secs, const StreamInfo *infos,
-                           HuffTable *ht, void *const *outs, const int *wide, int *err, int sms,
-                           cudaStream_t s);
-// mode 1: values are zigzag codes, scanned after unzigzag
-void launch_scan_u64(const unsigned long long *in, uint64_t n, int mode, bool inclusive,
-                     unsigned long long *out, unsigned long long *tile_tmp,
-                     unsigned long long *tile_base, cudaStream_t s);
-void launch_check_counts(const unsigned long long *counts, uint64_t m,
-                         const unsigned long long *starts_total, uint64_t nb, int *err, int sms,
-                         cudaStream_t s);
-// block-tile bases (agg: block_bases_bytes(M)) and the fused expand over
-// block tiles
-uint64_t block_bases_bytes(uint64_t M);
-void launch_block_bases(const unsigned long long *sid, const unsigned long long *scnt, uint64_t M,
-                        void *agg, cudaStream_t s);
-void launch_expand_blocks(uint32_t d, const Plan *plan, const unsigned long long *sid,
-                          const unsigned long long *scnt, uint64_t M, const void *agg,
-                          const uint32_t *s_rel, uint64_t nb, uint64_t n, uint32_t log2_chunk,
-                          float *out, int32_t *qout, int *err, cudaStream_t s);
+                           HuffTable *ht, void *const *outs, const int *wide, const int *agg_mode,
+                           void *agg, int *err, int sms, cudaStream_t s);
+// LCP-S block scans: aggregates of 2^agg_log2 blocks each (agg:
+// block_bases_bytes(M, agg_log2) bytes), their sums when the decode did not
+// write them (agg_log2 = 10), and their bases
+uint64_t block_bases_bytes(uint64_t M, uint32_t agg_log2);
+void launch_block_sums(const void *sid, const void *scnt, int wide, uint64_t M, void *agg,
+                       cudaStream_t s);
+void launch_block_bases(uint64_t M, uint32_t agg_log2, void *agg, cudaStream_t s);
+// reconstruction table of every code of every field: field f's codes
+// 0..qmax_f at off[f]; off[d] entries in all
+struct LutOffsets {
+  uint32_t off[kMaxD + 1];
+};
+constexpr uint32_t kLutMax = 16384;  // largest table the expand keeps in shared memory
+void launch_recon_lut(const Plan *plan, uint32_t d, const LutOffsets &lo, float *lut, int sms,
+                      cudaStream_t s);
+// the LCP-S expand over block tiles (see k_decode.cu)
+struct ExpandArgs {
+  const Plan *plan;
+  const void *sid, *scnt;  // id deltas, zigzag count deltas: u64 when wide, else u32
+  int wide;
+  uint64_t M, tiles;       // tiles = ceil(M / 1024)
+  const void *agg;         // block_bases_bytes(M, agg_log2) bytes, bases formed
+  uint32_t agg_log2;       // blocks per aggregate = 2^agg_log2 (<= 10)
+  const uint32_t *rel;     // decoded relative-location deltas [nb], or null:
+  const uint32_t *rel_pl;  // then the fixed-width payload (rel_w <= 32 bits per value)
+  uint32_t rel_w;
+  uint64_t rel_words;
+  uint64_t nb, n;
+  uint32_t log2_chunk;
+  const float *lut;        // with a table: its values and offsets
+  LutOffsets lut_off;
+  uint32_t qmax[kMaxD];    // largest code of each field (host copy)
+  uint32_t lp;             // log2 p
+  // filled by launch_expand: blocks per axis, floor(r / bn) = umulhi(r,
+  // bmagic) >> bshift (bshift 255 when bn = 1), whether block ids need 64
+  // bits, and the pairs (qmax_2i | qmax_2i+1 << 16)
+  uint32_t bn[kMaxD];
+  unsigned long long bmagic[kMaxD];
+  uint32_t bshift[kMaxD];
+  int div0_64;
+  uint32_t qmax2[kMaxD / 2];
+  float *out;              // [d][n], or null (codes only)
+  int32_t *qout;           // [d][n] codes, or null
+  int *err;
+};
+void launch_expand(uint32_t d, const ExpandArgs &a, bool lut, int sms, cudaStream_t s);
 void launch_outliers_decode(const Plan *plan, const float *raw, uint64_t K, uint64_t n, uint32_t d,
                             float *out, int32_t *qout, int sms, cudaStream_t s);
 

@@ -62,6 +62,11 @@ SIGNATURES = {
     "lcp_server_destroy": (C.c_int, [_vp]),
     "lcp_compress_batch": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp, C.c_int]),
     "lcp_decompress_batch": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp, C.c_int]),
+    "lcp_decompress_frames": (C.c_int, [_vp, _vp, C.POINTER(_vp), C.POINTER(_sz), _u64, _u64, _u64,
+                                        C.POINTER(_vp), _u64, C.POINTER(_u64), C.POINTER(_u32),
+                                        _vp]),
+    "lcp_decompress_frame": (C.c_int, [_vp, _vp, C.POINTER(_vp), C.POINTER(_sz), _u64, _u64, _vp,
+                                       _u64, C.POINTER(_u64), C.POINTER(_u32), _vp]),
 }
 
 
@@ -234,6 +239,47 @@ class Context:
                                  _stream(stream))
         _check(st, "lcp_decompress")
         return out.view(-1)[: d * n].view(d, n)
+
+    def decompress_frames(self, containers: list, first: int, last: int | None = None,
+                          batch: int | None = None, traj: "Trajectory | None" = None,
+                          stream=None) -> list[torch.Tensor]:
+        """lcp_decompress_frames: frames first..last (default: first only) of
+        one trajectory whose containers (uint8 CUDA tensors, frame i at index
+        i; None where absent) are given in stream order.  The decoder state is
+        traj, else a fresh trajectory of the stream's batch size `batch`.
+        Returns float32 [d, n] frames in slot order."""
+        last = first if last is None else last
+        n, d, _, _ = self.peek(containers[first], None, stream)
+        outs = [torch.empty((d, n), dtype=torch.float32, device=containers[first].device)
+                for _ in range(first, last + 1)]
+        cnt = len(containers)
+        ptrs = (_vp * cnt)(*[_ptr(b) if b is not None else None for b in containers])
+        sizes = (_sz * cnt)(*[b.numel() if b is not None else 0 for b in containers])
+        op = (_vp * len(outs))(*[_ptr(o) for o in outs])
+        dec = traj if traj is not None else Trajectory(self, batch, 8)
+        nn = C.c_uint64(0)
+        dd = C.c_uint32(0)
+        _check(_lib.lcp_decompress_frames(self.h, dec.h, ptrs, sizes, cnt, first, last, op, n,
+                                          C.byref(nn), C.byref(dd), _stream(stream)),
+               "lcp_decompress_frames")
+        return outs
+
+    def decompress_frame(self, containers: list, target: int, batch: int | None = None,
+                         traj: "Trajectory | None" = None, stream=None) -> torch.Tensor:
+        """lcp_decompress_frame: one frame of a trajectory by random access
+        (decoder state as in decompress_frames)."""
+        n, d, _, _ = self.peek(containers[target], None, stream)
+        out = torch.empty((d, n), dtype=torch.float32, device=containers[target].device)
+        cnt = len(containers)
+        ptrs = (_vp * cnt)(*[_ptr(b) if b is not None else None for b in containers])
+        sizes = (_sz * cnt)(*[b.numel() if b is not None else 0 for b in containers])
+        dec = traj if traj is not None else Trajectory(self, batch, 8)
+        nn = C.c_uint64(0)
+        dd = C.c_uint32(0)
+        _check(_lib.lcp_decompress_frame(self.h, dec.h, ptrs, sizes, cnt, target, _ptr(out), n,
+                                         C.byref(nn), C.byref(dd), _stream(stream)),
+               "lcp_decompress_frame")
+        return out
 
     def peek(self, buf: torch.Tensor, size: int | None = None, stream=None):
         n = C.c_uint64(0)
@@ -453,7 +499,7 @@ def quantize(x: torch.Tensor, m: float, e: float, max_abs: float | None = None, 
     xr = torch.empty(n, dtype=torch.float32, device=x.device)
     v = torch.empty(n, dtype=torch.uint8, device=x.device)
     if max_abs is None:
-        max_abs = float(x.abs().max()) if n else 0.0
+        max_abs = 0.0  # unused by the library (kept in the C signature)
     _check(_lib.lcp_quantize(_ptr(x), n, m, e, max_abs, _ptr(q), _ptr(xr), _ptr(v),
                              _stream(stream)), "lcp_quantize")
     return q, xr, v.bool()

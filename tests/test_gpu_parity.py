@@ -40,7 +40,8 @@ def gpu_bytes(res):
 # element rules
 # ---------------------------------------------------------------------------
 ELEM_CASES = [(0.0, 1e-3, 1.0), (-0.5, 3.7e-4, 1.0), (1000.0, 0.25, 50.0), (-2000.0, 3.6, 4000.0),
-              (1.0e-6, 1e-3, 1.0), (0.0, 1e-7, 1e-3), (123.456, 1e-5, 0.01), (-3.0, 0.7, 6.0)]
+              (1.0e-6, 1e-3, 1.0), (0.0, 1e-7, 1e-3), (123.456, 1e-5, 0.01), (-3.0, 0.7, 6.0),
+              (1.0e6, 1e-5, 1.0), (-3.0e7, 3e-6, 8.0)]  # the last two: |x| >= 2^32 * 2e
 
 
 @pytest.mark.parametrize("m,eb,scale", ELEM_CASES)
@@ -216,6 +217,8 @@ Q2_FRAMES = [
     ((-0.75, 123.456, -9.9e3), (1.0, 1.0, 1.0), 3.3e-6, "abs"),
     ((0.0, 50.0, -100.0), (1.0, 1e-4, 1e-4), 2e-8, "abs"),  # 2.5e7 bins in the first field
     ((5.0e4, -5.0e4, 1.0), (1.0e4, 1.0e4, 1.0e4), 1e-4, "rel"),
+    # minima 2^33 bins or more away from zero: Q2 on the exact wide path
+    ((1.0e6, -3.0e7, 2.0e5), (1.0, 1.0, 1.0), 1e-5, "abs"),
 ]
 
 
@@ -301,6 +304,55 @@ def test_anchor_scaling_matches_oracle(ctx, orc, lcp, scale):
         assert np.array_equal(Y.view(np.uint32), dec[t].view(np.uint32)), t
 
 
+@pytest.mark.parametrize("scale", [1, 5])
+def test_random_access_matches_oracle(ctx, orc, lcp, scale):
+    """Random-access retrieval (Sec. "Spatial-Anchor-Frame-Based Batch
+    Compression", recursive decompression) through lcp_decompress_frame and
+    lcp_decompress_frames: every frame fetched alone, in a shuffled order, and
+    every batch fetched at once equal the oracle's sequential decode of the
+    whole stream bit for bit; frames the chain does not need may be absent,
+    and a missing anchor is reported."""
+    from oracle import hybrid
+    batch = 4
+    frames = list(synth.brownian_trajectory(20011, 17, 5, sigma=0.02))
+    enc = hybrid.encode_trajectory(frames, 1e-3, "abs", 8, batch=batch, anchor_scale=scale)
+    dec = hybrid.decode_trajectory([b for b, _ in enc])
+    methods = [m for _, m in enc]
+    # some batch opens with an LCP-T frame, so its anchor must be fetched
+    assert any(methods[b0] == "T" for b0 in range(batch, len(frames), batch))
+    bufs = [to_dev(np.frombuffer(b, np.uint8)) for b, _ in enc]
+    dt = lcp.Trajectory(ctx, batch=batch, p=8)
+    for t in np.random.default_rng(1).permutation(len(frames)):
+        Y = ctx.decompress_frame(bufs, int(t), traj=dt).cpu().numpy()
+        assert np.array_equal(ctx.decompress_frame(bufs, int(t), batch=batch).cpu().numpy().view(
+            np.uint32), Y.view(np.uint32))
+        assert np.array_equal(Y.view(np.uint32), dec[t].view(np.uint32)), t
+    for b0 in range(0, len(frames), batch):
+        last = min(b0 + batch - 1, len(frames) - 1)
+        Ys = ctx.decompress_frames(bufs, b0, last, traj=dt)
+        for k, Y in enumerate(Ys):
+            assert np.array_equal(Y.cpu().numpy().view(np.uint32),
+                                  dec[b0 + k].view(np.uint32)), (b0, k)
+    # only the chain of frame t present (and the batch openings back to its
+    # anchor, whose headers show which opening is the anchor)
+    for t in range(len(frames)):
+        b0 = t - t % batch
+        s = max([i for i in range(b0, t + 1) if methods[i] == "S"], default=None)
+        if s is None:
+            a = max(i for i in range(0, b0, batch) if methods[i] == "S")
+            need = [a] + list(range(a + batch, b0, batch)) + list(range(b0, t + 1))
+        else:
+            need = list(range(s, t + 1))
+        part = [bufs[i] if i in need else None for i in range(t + 1)]
+        Y = ctx.decompress_frame(part, t, traj=dt).cpu().numpy()
+        assert np.array_equal(Y.view(np.uint32), dec[t].view(np.uint32)), t
+        if need[0] < b0:  # without the anchor the chain cannot start
+            part[need[0]] = None
+            with pytest.raises(lcp.LcpError) as ei:
+                ctx.decompress_frame(part, t, traj=dt)
+            assert ei.value.status == lcp.ERR_STATE
+
+
 def test_select_is_a_query(ctx, lcp):
     frames = list(synth.brownian_trajectory(5000, 4, 2))
     tr = lcp.Trajectory(ctx, batch=10, p=8)
@@ -333,16 +385,58 @@ def test_full_size_plain_frame_bytes(ctx, orc):
     check_s(ctx, orc, Xf, 1e-3, "abs", 8)
 
 
-@pytest.mark.parametrize("which", ["md", "cosmology"])
-def test_full_size_sampled(ctx, orc, lcp, which):
-    """16M-particle MD and 64M-particle 6-field frames: every decoded value is
+def test_bench_config_bytes_16M(ctx, orc):
+    """The benchmarked configuration -- the cosmology-like 6-field frame, eb =
+    1e-3 of each field's range, p = 8 -- at 2^24 particles: the whole
+    container equals the oracle's byte for byte (with and without the slot
+    permutation) and the decoded frame equals the oracle's decode bit for
+    bit.  At this size dense halo buckets exceed 32K keys, so the multi-task
+    level-2 split runs."""
+    Xf = synth.cosmology(1 << 24, 2)
+    r, o = check_s(ctx, orc, Xf, 1e-3, "rel", 8)
+    assert o["M"] > 1 << 22
+
+
+def test_bench_config_full_frame_64M(ctx, orc):
+    """The benchmarked frame itself (2^26 particles x 6 fields, p = 8), in the
+    bench's launch configuration: the container the bench times is decoded by
+    the oracle, and every decoded value equals the GPU's decode bit for bit;
+    the slot permutation is a permutation, every particle is within its bound,
+    and on 2^21 sampled slots the decoded code equals the oracle's own Q1 of
+    the particle's value."""
+    Xf = synth.cosmology(1 << 26, 2)
+    d, n = Xf.shape
+    Xd = to_dev(Xf)
+    r0 = ctx.compress(Xd, 1e-3, "rel", 8)  # the bench's call
+    r = ctx.compress(Xd, 1e-3, "rel", 8, perm=True)
+    assert torch.equal(r0["bytes"], r["bytes"])
+    Y = ctx.decompress(r0["bytes"])
+    buf = gpu_bytes(r0)
+    Yo, qo = orc.decompress(buf)
+    Yg = Y.cpu().numpy()
+    assert np.array_equal(Yg.view(np.uint32), Yo.view(np.uint32))
+    perm = r["perm"].long()
+    assert torch.equal(torch.sort(perm).values, torch.arange(n, device="cuda"))
+    hdr = np.frombuffer(buf[:48 + 16 * d], np.uint8)
+    e = hdr[48:48 + 16 * d].view(np.float32).reshape(d, 4)[:, 1]
+    m = hdr[48:48 + 16 * d].view(np.float32).reshape(d, 4)[:, 0]
+    err = (Xd[:, perm].double() - Y.double()).abs().max(dim=1).values.cpu().numpy()
+    assert (err <= e.astype(np.float64)).all()
+    K = int(np.frombuffer(buf[24:32], np.uint64)[0])
+    rng = np.random.default_rng(0)
+    slots = np.sort(rng.choice(n - K, 1 << 21, replace=False))
+    pi = perm.cpu().numpy()[slots]
+    for f in range(d):
+        q = orc.q1(Xf[f, pi], float(m[f]), float(e[f]))
+        assert np.array_equal(q, qo[f, slots].astype(np.int64))
+
+
+def test_full_size_md_sampled(ctx, orc, lcp):
+    """The 16M-particle MD frame at the bench's p = 2: every decoded value is
     within the bound of its particle; on a sample of particles the decoded
-    value equals the oracle's reconstruction of the oracle's code bit for bit;
-    the decoded frame holds every particle once."""
-    if which == "md":
-        Xf, eb, mode, p = synth.md_fcc(1 << 24, 1), 1e-4, "rel", 16
-    else:
-        Xf, eb, mode, p = synth.cosmology(1 << 26, 2), 1e-3, "rel", 4
+    value equals the oracle's reconstruction of the oracle's code bit for
+    bit; the decoded frame holds every particle once."""
+    Xf, eb, mode, p = synth.md_fcc(1 << 24, 1), 1e-4, "rel", 2
     Xd = to_dev(Xf)
     r = ctx.compress(Xd, eb, mode, p, perm=True)
     Y = ctx.decompress(r["bytes"])

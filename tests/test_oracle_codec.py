@@ -98,6 +98,32 @@ def test_bruteforce_tiny_frames(orc, seed):
     check_bound(Xf, r, Y)
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_bruteforce_far_from_zero(orc, seed):
+    """Eq. quantization holds for every real value: frames whose values sit
+    2^33 bins or more away from zero (bounds far below the f32 spacing of the
+    data, and negative offsets) are coded, and their streams equal the exact
+    rational restatement."""
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(2, 40))
+    d = int(rng.integers(1, 4))
+    p = int(2 ** rng.integers(0, 3))
+    off = float(rng.choice([1.0e6, -3.0e7, 2.0e5]))
+    eb = float(rng.choice([1e-5, 3e-6]))
+    Xf = (off + rng.normal(size=(d, n)) * 0.5).astype(np.float32)
+    e_list = [X.round_down_f32(eb)] * d
+    assert max(abs(float(v)) for v in Xf.ravel()) >= 2 ** 32 * 2 * e_list[0]
+    r = orc.compress_s(Xf, eb, "abs", p, 5, streams=True)
+    ids, cnts, rels, outl, slots = CP.streams_s_bruteforce(Xf, e_list, p, 5)
+    assert list(r["ids"]) == ids and list(r["cnts"]) == cnts and list(r["rels"]) == rels
+    assert r["K"] == len(outl) and list(r["pi"]) == slots
+    Y, q = orc.decompress(r["bytes"])
+    check_bound(Xf, r, Y)
+    # the bins are finer than the data's spacing: every value decodes exactly
+    pi = r["pi"]
+    assert np.array_equal(Y.view(np.uint32), Xf[:, pi].view(np.uint32))
+
+
 def _frames():
     yield "uniform_clusters", synth.uniform_clusters(20000, 0), 1e-3, "abs", 8
     yield "md_fcc", synth.md_fcc(20000, 1, cells=20), 1e-4, "rel", 16
