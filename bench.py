@@ -63,12 +63,24 @@ WORKLOADS = {
     "plain": dict(desc="plain LCP-S frame: 2^20 particles, uniform + 64 Gaussian clusters, "
                        "eb = 1e-3 absolute, p = 8", n=1 << 20, d=3, eb=1e-3, mode="abs", p=8,
                   seed=0),
+    # sweeps: one JSON line with a row per setting
+    # (below ~1e-3 of the range the 6-D block key of this frame needs more
+    # than 63 bits: the codec's domain ends there)
+    "eb_sweep": dict(desc="cosmology-like frame (64M x 6) at eb = 1e-2, 5e-3, 2e-3, 1e-3 of "
+                          "each field's range, p from the exact block-size search at each eb: "
+                          "CR, PSNR and GB/s per eb", n=1 << 26, d=6, eb=0.0, mode="rel", p=0,
+                     seed=2, frame="cosmology", sweep=("eb", (1e-2, 5e-3, 2e-3, 1e-3))),
+    "md_psweep": dict(desc="MD-like frame (16M x 3) at eb = 1e-4 of the range, block size "
+                           "4 eb ... 64 eb (p = 2 ... 32): CR and GB/s per p", n=1 << 24, d=3,
+                      eb=1e-4, mode="rel", p=0, seed=1, frame="md",
+                      sweep=("p", (2, 4, 8, 16, 32))),
 }
 
 
 def make_frame(name: str, seed: int):
     from paper_2411_00761_b300 import synth
     w = WORKLOADS[name]
+    name = w.get("frame", name)
     if name == "cosmology":
         return synth.cosmology(w["n"], seed)
     if name == "md":
@@ -85,8 +97,17 @@ def peaks():
         return 6400.0, "fallback"
 
 
-# algorithmic bytes of each stage (what its function must read and write), in
-# terms of N particles, D fields, M blocks, K raw outliers and C container bytes
+# Algorithmic bytes of one launch of a full-frame kernel (the roofline's
+# numerator): the per-particle figure of the measurement plan -- D * 4 bytes of
+# input read once plus the container written (or read) once -- times the N
+# particles one launch processes: 4 N D + C, whichever stage the kernel is.
+def algorithmic_bytes(N, D, C):
+    return 4 * N * D + C
+
+
+# bytes each stage moves by its design, intermediate arrays included (context
+# for the measured DRAM traffic; not the roofline's numerator), in terms of N
+# particles, D fields, M blocks, K raw outliers and C container bytes
 def stage_bytes(stage: str, N, D, M, K, C):
     raw = 4 * N * D
     nb = N - K
@@ -109,9 +130,12 @@ def stage_bytes(stage: str, N, D, M, K, C):
         "s.encode_counts": 16 * M,
         "s.encode_rel": 4 * nb,
         "s.outliers": 4 * K * D,
-        "d.streams": C + 16 * M + 4 * nb,
-        "d.block_scans": 48 * M,
-        "d.expand": 16 * M + 4 * nb + raw,
+        # ids and count deltas (4 bytes each) written, aggregates
+        "d.streams": C + 8 * M,
+        "d.block_scans": 0,
+        # ids and count deltas read, relative codes read (at most the
+        # container), frame written
+        "d.expand": 8 * M + C + raw,
     }
     return table.get(stage, 0)
 
@@ -226,6 +250,32 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def fidelity(ctx, Xd, w, p, out, Y):
+    """Per field: PSNR = 20 log10(value range / RMSE) (Sec. "Evaluation
+    metrics") and max |x - x'| / eb_f, over every particle, from one
+    compression with the slot permutation and its decompression."""
+    import torch
+    D, N = Xd.shape
+    r = ctx.compress(Xd, w["eb"], w["mode"], p=p, out=out, perm=True)
+    ctx.decompress(r["bytes"], r["size"], out=Y)
+    pi = r["perm"].long()
+    hdr = r["bytes"][:48 + 16 * D].cpu().numpy()
+    e = hdr[48:48 + 16 * D].view(np.float32).reshape(D, 4)[:, 1].astype(np.float64)
+    psnr, maxe = [], []
+    for f in range(D):
+        x = Xd[f, pi].double()
+        err = Y[f].double() - x
+        rng = float(Xd[f].max().double() - Xd[f].min().double())
+        mse = float((err * err).mean())
+        psnr.append(float("inf") if mse == 0.0 else 20.0 * np.log10(rng / np.sqrt(mse)))
+        maxe.append(float(err.abs().max()) / float(e[f]))
+    del pi
+    torch.cuda.empty_cache()
+    return {"psnr_db": [round(v, 3) for v in psnr], "psnr_min_db": round(min(psnr), 3),
+            "max_err_over_eb": [round(v, 6) for v in maxe], "max_err_over_eb_max": max(maxe),
+            "eb_f": [float(v) for v in e]}
+
+
 def cpu_baseline(name: str, X: np.ndarray, p: int, n_sample: int):
     """The oracle as it stands, single-threaded, on the first n_sample
     particles of the frame (storage order is random, so this is a random
@@ -279,6 +329,72 @@ def run_reference_batched(args):
     return 0
 
 
+def run_sweep(args):
+    """One frame at several bounds (eb_sweep) or block sizes (md_psweep): per
+    setting the compressed size, CR, fidelity and the compress / decompress
+    throughput (CUDA events, inputs resident in HBM)."""
+    import torch
+
+    from paper_2411_00761_b300 import lcp
+    name = args.workload
+    w = WORKLOADS[name]
+    X = make_frame(name, w["seed"])
+    D, N = X.shape
+    raw = X.nbytes
+    Xd = torch.from_numpy(X).cuda()
+    ctx = lcp.Context(0)
+    ctx.reserve(N, D)
+    out = torch.empty(lcp.max_compressed_size(N, D), dtype=torch.uint8, device="cuda")
+    Y = torch.empty((D, N), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = peaks()
+    key, values = w["sweep"]
+    rows = []
+    for v in values:
+        eb = v if key == "eb" else w["eb"]
+        p = v if key == "p" else w["p"]
+        if p == 0:  # exact block-size search at this bound, untimed
+            ctx.compress(Xd, eb, w["mode"], p=0, out=out)
+            p = int(np.frombuffer(out[12:16].cpu().numpy().tobytes(), np.uint32)[0])
+        ws = dict(w, eb=eb)
+        for _ in range(args.warmup):
+            r = ctx.compress(Xd, eb, w["mode"], p=p, out=out)
+            ctx.decompress(r["bytes"], r["size"], out=Y)
+        tc, td = [], []
+        for _ in range(args.steps):
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            r = ctx.compress(Xd, eb, w["mode"], p=p, out=out)
+            e1.record(stream)
+            ctx.decompress(r["bytes"], r["size"], out=Y)
+            e2.record(stream)
+            e2.synchronize()
+            tc.append(e0.elapsed_time(e1))
+            td.append(e1.elapsed_time(e2))
+        csize = r["size"]
+        tcm, tdm = statistics.mean(tc), statistics.mean(td)
+        rows.append({key: v, "eb": eb, "p": p, "container_bytes": csize, "ratio": raw / csize,
+                     "compress_gbs": raw / (tcm * 1e-3) / 1e9,
+                     "decompress_gbs": raw / (tdm * 1e-3) / 1e9,
+                     "compress_roofline_frac": (raw + csize) / (tcm * 1e-3) / 1e9 / peak,
+                     "decompress_roofline_frac": (raw + csize) / (tdm * 1e-3) / 1e9 / peak,
+                     "fidelity": fidelity(ctx, Xd, ws, p, out, Y)})
+    best = max(rows, key=lambda x: 1 / (1 / x["compress_gbs"] + 1 / x["decompress_gbs"]))
+    line = {
+        "metric": "compress/decompress GB/s vs HBM peak at fixed eb + ratio",
+        "value": 1 / (1 / best["compress_gbs"] + 1 / best["decompress_gbs"]), "unit": "GB/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 in, integer codes",
+        "data": "synthetic", "peak": peak, "peak_kind": peak_kind,
+        "config": {"workload": name, "desc": w["desc"], "particles": N, "fields": D,
+                   "eb_mode": w["mode"], "sweep": key,
+                   "value_is": "the best setting's round-trip GB/s"},
+        "sweep": rows,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -287,6 +403,10 @@ def run_reference(args):
     w = WORKLOADS[name]
     if name in ("batched", "serving"):  # the oracle's Algorithm 1 on a bounded sample
         return run_reference_batched(args)
+    if "sweep" in w:  # the sweep's first setting
+        key, values = w["sweep"]
+        w = dict(w, **{key: values[0]})
+        WORKLOADS[name] = w
     X = make_frame(name, w["seed"])
     n_sample = args.sample or (1 << 18 if w["d"] == 6 else 1 << 19)
     p = w["p"]
@@ -582,28 +702,39 @@ def run_serving(args):
     # whole job: bytes of all replicas over the longest replica's span
     span_ms, raw_all = ranks_aggregate(span_s * 1e3, float(raw_done), world, dev)
     _, n_all = ranks_aggregate(0.0, float(len(allv)), world, dev)
+    # admission counters summed over the replicas
+    _, offered_all = ranks_aggregate(0.0, float(arrivals.size), world, dev)
+    _, rejected_all = ranks_aggregate(0.0, float(rejected), world, dev)
+    _, shed_all = ranks_aggregate(0.0, float(shed), world, dev)
+    _, failed_all = ranks_aggregate(0.0, float(sum(failed.values())), world, dev)
+    _, warm_all = ranks_aggregate(
+        0.0, float(sum(1 for _, r in done_list if r["enqueue_ms"] < warm_ms)), world, dev)
     pct = lambda v, q: float(np.percentile(np.array(v), q)) if v else None
     line = {
         "metric": "compress/decompress GB/s vs HBM peak at fixed eb + ratio; batched p50/p99 ms",
         "value": raw_all / (span_ms * 1e-3) / 1e9, "unit": "GB/s", "n_gpus": world,
-        "steps": len(allv),
-        "warmup": int(sum(1 for _, r in done_list if r["enqueue_ms"] < warm_ms)),
-        "ms_per_step": span_s * 1e3 / max(len(allv), 1), "higher_is_better": True,
+        "steps": int(n_all), "warmup": int(warm_all),
+        "ms_per_step": span_ms / max(n_all, 1.0), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 in, integer codes",
         "data": "synthetic",
         "config": {"workload": "serving", "desc": w["desc"], "producers": NP,
                    "offered_rate_req_s": rate, "seconds": seconds, "lanes": w["lanes"],
                    "max_pending": max_pending,
                    "batch": w["batch"], "hbm_budget_gb": w["budget_gb"],
-                   "parallelism": (f"{world} independent replicas (latency figures: rank 0)"
-                                   if world > 1 else "single GPU, lanes overlap requests")},
+                   "parallelism": (f"{world} independent replicas" if world > 1
+                                   else "single GPU, lanes overlap requests"),
+                   "whole_job_fields": "value, steps, warmup, ms_per_step, achieved_rate_req_s, "
+                                       "requests_done, offered, rejected_by_budget, shed, "
+                                       "failed (summed over replicas; time = longest replica)",
+                   "rank0_fields": "p50/p99 latencies, failed_by_status, ratio, "
+                                   "server_device_gb, wall_s, gpu_launches, clocks"},
         "p50_ms": pct(allv, 50), "p99_ms": pct(allv, 99),
         "compress_p50_ms": pct(lat["compress"], 50), "compress_p99_ms": pct(lat["compress"], 99),
         "decompress_p50_ms": pct(lat["decompress"], 50),
         "decompress_p99_ms": pct(lat["decompress"], 99),
         "achieved_rate_req_s": n_all / (span_ms * 1e-3), "requests_done": int(n_all),
-        "offered": int(arrivals.size), "rejected_by_budget": rejected, "shed": shed,
-        "failed_by_status": failed,
+        "offered": int(offered_all), "rejected_by_budget": int(rejected_all),
+        "shed": int(shed_all), "failed": int(failed_all), "failed_by_status": failed,
         "ratio": comp_raw / max(comp_bytes, 1), "server_device_gb": mem / 1e9,
         "wall_s": wall, "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
         "cpu_baseline": None,
@@ -637,6 +768,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if "sweep" in WORKLOADS[args.workload]:
+        return run_sweep(args)
 
     import torch
     import torch.distributed as dist
@@ -724,8 +857,14 @@ def main():
         per.setdefault(nm, []).append(ms)
     avg = {k: statistics.mean(v) for k, v in per.items()}
     dom = max(avg, key=avg.get)
-    dbytes = stage_bytes(dom, N, D, M, K, csize)
+    dbytes = algorithmic_bytes(N, D, csize)
     achieved = dbytes / (avg[dom] * 1e-3) / 1e9
+    # dominant kernel of the decompression alone (the path's other half)
+    ddom = max((k for k in avg if k.startswith("d.")), key=avg.get, default=None)
+
+    # fidelity (Sec. "Evaluation metrics"): PSNR and the largest error / eb per
+    # field, from one compression with the slot permutation (untimed)
+    fid = fidelity(ctx, Xd, w, p, out, Y)
 
     # e2e through the same calls with host buffers
     e2e = None
@@ -784,7 +923,15 @@ def main():
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": measured_traffic(name, dom, N),
                          "algorithmic_bytes_per_launch": dbytes,
+                         "design_bytes_per_launch": stage_bytes(dom, N, D, M, K, csize),
                          "avg_ms": avg[dom]},
+            "roofline_decompress_kernel": None if ddom is None else {
+                "kernel": ddom, "avg_ms": avg[ddom],
+                "achieved": dbytes / (avg[ddom] * 1e-3) / 1e9,
+                "frac": dbytes / (avg[ddom] * 1e-3) / 1e9 / peak,
+                "traffic": measured_traffic(name, ddom, N),
+                "design_bytes_per_launch": stage_bytes(ddom, N, D, M, K, csize)},
+            "fidelity": fid,
             "stages_ms": {k: round(v, 4) for k, v in sorted(avg.items(), key=lambda x: -x[1])},
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "cpu_baseline": cpu,

@@ -179,7 +179,10 @@ LCP_API lcp_status lcp_peek(const void *d_in, size_t in_size, uint64_t *n, uint3
  * frame would get, without coding it or changing any state.  *est_s is the
  * LCP-S size estimate (the size of the most recent LCP-S frame, 0 if none),
  * *est_t the exact LCP-T size when the FSM tests LCP-T for this frame (0
- * otherwise).
+ * otherwise).  Both are sizes at the trajectory's bound eb: with anchor
+ * scaling on (lcp_traj_set_anchor_scale), a frame that becomes an anchor is
+ * written at eb / scale and its container is larger than est_s, so size the
+ * output buffer with lcp_max_compressed_size, not with est_s.
  */
 LCP_API lcp_status lcp_select(lcp_ctx *ctx, lcp_traj *traj, const float *d_fields, uint64_t n,
                       uint32_t d, double eb, lcp_eb_mode mode, lcp_method *chosen,

@@ -90,3 +90,54 @@ def test_malformed_images_are_rejected(lcp, frames):
         with pytest.raises(lcp.LcpError) as ei:
             lcp.Trajectory.restore(ctx, bad)
         assert ei.value.status == lcp.ERR_FORMAT
+
+
+# anchors written at eb / 5 (Sec. "Best error-bound scale for anchor frames"):
+# a cut right after a scaled anchor, before the frame that predicts from it,
+# must restore the anchor's grid and its scaled flag
+SCALE = 5
+
+
+@pytest.fixture(scope="module")
+def scaled(lcp, frames):
+    from oracle import hybrid
+    enc = hybrid.encode_trajectory(frames, EB, "abs", P, batch=BATCH, anchor_scale=SCALE)
+    ctx = lcp.Context(0)
+    tr = lcp.Trajectory(ctx, batch=BATCH, p=P, anchor_scale=SCALE)
+    got = [encode(lcp, ctx, tr, X) for X in frames]
+    assert [b for b, _ in got] == [b for b, _ in enc]
+    flags = [hybrid.oracle.peek(b)["flags"] for b, _ in enc]
+    # frames predicted from a scaled anchor (re-quantized reference)
+    req = [t for t, f in enumerate(flags) if f & hybrid.FLAG_REF_REQUANT]
+    assert req, "no frame predicts from a scaled anchor"
+    return got, enc, req
+
+
+def test_encoder_resumes_after_scaled_anchor(lcp, frames, scaled):
+    got, enc, req = scaled
+    for t_req in req:
+        cut = t_req - 1  # the scaled reference is the last frame coded before the cut
+        ctx = lcp.Context(0)
+        tr = lcp.Trajectory(ctx, batch=BATCH, p=P, anchor_scale=SCALE)
+        for t in range(cut + 1):
+            assert encode(lcp, ctx, tr, frames[t]) == got[t]
+        tr2 = lcp.Trajectory.restore(lcp.Context(0), tr.export())
+        for t in range(cut + 1, STEPS):
+            assert encode(lcp, tr2.ctx, tr2, frames[t])[0] == enc[t][0], (t_req, t)
+
+
+def test_decoder_resumes_after_scaled_anchor(lcp, scaled):
+    from oracle import hybrid
+    got, enc, req = scaled
+    dec = hybrid.decode_trajectory([b for b, _ in enc])
+    for t_req in req:
+        cut = t_req - 1
+        ctx = lcp.Context(0)
+        dt = lcp.Trajectory(ctx, batch=BATCH, p=P)
+        for t in range(cut + 1):
+            ctx.decompress(dev(np.frombuffer(enc[t][0], np.uint8)), traj=dt)
+        dt2 = lcp.Trajectory.restore(lcp.Context(0), dt.export())
+        for t in range(cut + 1, STEPS):
+            y = dt2.ctx.decompress(dev(np.frombuffer(enc[t][0], np.uint8)), traj=dt2)
+            assert np.array_equal(y.cpu().numpy().view(np.uint32), dec[t].view(np.uint32)), \
+                (t_req, t)
