@@ -635,6 +635,7 @@ def run_serving(args):
     gen_stream = torch.cuda.Stream(device=dev)
     rejected = 0
     shed = 0
+    not_decodable = 0
     launches0 = lcp.kernel_launches()
     t_start = time.perf_counter()
     with ClockSampler(local) as clk:
@@ -645,14 +646,19 @@ def run_serving(args):
             P = prods[int(k)]
             with lock:
                 backlog = len(pending)
+            measured = a >= w["warm_seconds"]  # counters cover the measured window
             if backlog >= max_pending:
-                shed += 1
+                shed += measured
                 continue
             first, nxt = srv.frames(int(k))
             if not is_c and nxt > first:
                 f = int(rng.integers(first, nxt))
                 Y = torch.empty((3, P["n"]), dtype=torch.float32, device=dev)
-                tk = srv.submit_decompress(int(k), f, Y)
+                try:
+                    tk = srv.submit_decompress(int(k), f, Y)
+                except lcp.LcpError:  # evicted since frames() was read: refused
+                    not_decodable += measured
+                    continue
                 keep = (Y,)
                 op = "decompress"
             else:
@@ -665,7 +671,7 @@ def run_serving(args):
                 keep = (X,)
                 op = "compress"
             if tk is None:
-                rejected += 1
+                rejected += measured
                 continue
             with lock:
                 pending.append((tk, op, 12 * P["n"], a, keep))
@@ -723,6 +729,8 @@ def run_serving(args):
                    "batch": w["batch"], "hbm_budget_gb": w["budget_gb"],
                    "parallelism": (f"{world} independent replicas" if world > 1
                                    else "single GPU, lanes overlap requests"),
+                   "counters": "shed, rejected_by_budget and refused_not_decodable count "
+                               "requests that arrived after the warm-up; failed counts all",
                    "whole_job_fields": "value, steps, warmup, ms_per_step, achieved_rate_req_s, "
                                        "requests_done, offered, rejected_by_budget, shed, "
                                        "failed (summed over replicas; time = longest replica)",
@@ -735,6 +743,7 @@ def run_serving(args):
         "achieved_rate_req_s": n_all / (span_ms * 1e-3), "requests_done": int(n_all),
         "offered": int(offered_all), "rejected_by_budget": int(rejected_all),
         "shed": int(shed_all), "failed": int(failed_all), "failed_by_status": failed,
+        "refused_not_decodable": not_decodable,
         "ratio": comp_raw / max(comp_bytes, 1), "server_device_gb": mem / 1e9,
         "wall_s": wall, "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
         "cpu_baseline": None,

@@ -326,10 +326,16 @@ LCP_API lcp_status lcp_decompress_batch(lcp_ctx *const *ctxs, void *const *strea
  *     when given); the response gives its frame index, size and method.  A
  *     producer's frames all have one shape.
  *   - LCP_REQ_DECOMPRESS decodes the producer's frame `frame` into d_out
- *     [d][n_cap] (device): its batch from the batch's first frame, preceded
- *     by the batch's anchor when that first frame is LCP-T.  Containers older
- *     than the last 2 * batch frames are freed (anchors still needed are
- *     kept); lcp_server_frames gives the decodable range [first, next).
+ *     [d][n_cap] (device): from the latest LCP-S frame of its batch, or from
+ *     the batch's anchor when the batch opens with LCP-T, the frames before
+ *     `frame` to codes only.  Containers older than the last 2 * batch frames
+ *     are freed (anchors still needed are kept); lcp_server_frames gives the
+ *     decodable range [first, next).  A frame that is not decodable when the
+ *     request is submitted is refused then (ERR_STATE); otherwise the frames
+ *     the request needs are pinned until it completes, so it cannot fail for
+ *     want of them.  Containers use stream-ordered device memory from the
+ *     device's default pool (freed memory is kept for reuse), so requests
+ *     never synchronize the device to allocate.
  *   - Admission: lcp_server_submit returns LCP_ERR_NOMEM when the device
  *     memory the server holds (workspaces, reference states, containers, and
  *     what admitted requests may still add) plus this request's worst case

@@ -1505,6 +1505,28 @@ int decompress_range(lcp_ctx *c, lcp_traj *t, const void *const *ins, const size
 
 }  // namespace
 
+namespace lcp {
+// The frames of a chain the caller has already determined (the serving
+// loop's own bookkeeping), in stream order: all but the last decoded to
+// codes only, the last into out.  t is reset first.
+int decode_chain(lcp_ctx *c, lcp_traj *t, const void *const *ins, const size_t *sizes, int k,
+                 float *out, uint64_t n_cap, uint64_t *n_out, uint32_t *d_out, cudaStream_t s) {
+  if (!c || !t || !ins || !sizes || k < 1) return ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok) return ERR_CUDA;
+  prof_reset(c);
+  t->has_prev = t->has_anchor = false;
+  t->prev_scaled = t->anc_scaled = false;
+  t->t = 0;
+  for (int i = 0; i < k; ++i) {
+    const bool last = i == k - 1;
+    TRY(decompress_impl(c, t, reinterpret_cast<const uint8_t *>(ins[i]), sizes[i],
+                        last ? out : nullptr, n_cap, n_out, d_out, s, !last));
+  }
+  return OK;
+}
+}  // namespace lcp
+
 extern "C" {
 
 lcp_status lcp_decompress_frames(lcp_ctx *c, lcp_traj *dec, const void *const *d_containers,

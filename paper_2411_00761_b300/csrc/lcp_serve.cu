@@ -7,10 +7,14 @@
 // against a device-memory budget, and runs them on lanes: host threads with
 // their own context and CUDA stream, so requests of different producers
 // overlap on the GPU.  A producer's requests run one at a time in arrival
-// order.  Decompressing an earlier frame replays what its decoding needs:
-// the batch's anchor frame if the batch opens with an LCP-T frame, then the
-// batch's frames up to the requested one (Sec. "Batch compression": a frame
-// depends on its batch and the batch's anchor only).
+// order.  Decompressing an earlier frame replays what its decoding needs
+// (Sec. "Spatial-Anchor-Frame-Based Batch Compression": a frame depends on
+// its batch and the batch's anchor only): from the latest LCP-S frame of its
+// batch up to it, or from the batch's anchor when the batch opens with LCP-T,
+// the frames before the requested one to codes only.  The frames a request
+// needs are pinned from its admission to its completion, so eviction never
+// takes them.  Containers live in stream-ordered device memory (a pool that
+// keeps freed memory), so no request synchronizes the device to allocate.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +30,11 @@
 
 #include "../../include/lcp.h"
 
+namespace lcp {
+int decode_chain(lcp_ctx *c, lcp_traj *t, const void *const *ins, const size_t *sizes, int k,
+                 float *out, uint64_t n_cap, uint64_t *n_out, uint32_t *d_out, cudaStream_t s);
+}
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -37,12 +46,14 @@ struct Frame {
   lcp_method method = LCP_SPATIAL;
   uint64_t anchor = 0;  // the anchor frame in force when this frame was coded
   bool has_anchor = false;
+  int pins = 0;         // admitted requests that need this container
 };
 
 struct Pending {
   uint64_t ticket;
   lcp_request req;
   double enqueue_ms;
+  std::vector<uint64_t> chain;  // decompress: the frames to decode, pinned
 };
 
 struct Producer {
@@ -69,6 +80,7 @@ struct lcp_server {
   std::vector<cudaStream_t> streams;
   std::vector<void *> scratch;  // per lane: compress output / decode buffers
   std::vector<size_t> scratch_cap;
+  std::vector<lcp_traj *> dec;  // per lane: decoder state, reused by every decompress
   std::vector<std::thread> threads;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -92,6 +104,7 @@ struct lcp_server {
     for (lcp_ctx *c : ctxs) b += lcp_ctx_device_bytes(c);
     for (size_t i = 0; i < scratch_cap.size(); ++i) b += scratch_cap[i];
     for (const auto &kv : prods) b += lcp_traj_device_bytes(kv.second.traj);
+    for (lcp_traj *t : dec) b += lcp_traj_device_bytes(t);
     return b;
   }
 };
@@ -99,8 +112,10 @@ struct lcp_server {
 namespace {
 
 // frees containers older than the retention window, keeping the anchors the
-// retained frames need
-void evict_locked(lcp_server *S, Producer &P) {
+// retained frames need and every frame an admitted request has pinned
+// (stream-ordered free on the evicting lane's stream: nothing else uses an
+// unpinned container)
+void evict_locked(lcp_server *S, Producer &P, cudaStream_t st) {
   if (P.next <= S->retain) return;
   const uint64_t keep_from = P.next - S->retain;
   std::vector<uint64_t> anchors;  // anchors of retained frames
@@ -110,8 +125,8 @@ void evict_locked(lcp_server *S, Producer &P) {
     return std::find(anchors.begin(), anchors.end(), g) != anchors.end();
   };
   for (auto it = P.frames.begin(); it != P.frames.end();) {
-    if (it->first < keep_from && !needed(it->first)) {
-      cudaFree(it->second.buf);
+    if (it->first < keep_from && !needed(it->first) && it->second.pins == 0) {
+      cudaFreeAsync(it->second.buf, st);
       S->stored -= it->second.size;
       it = P.frames.erase(it);
     } else {
@@ -122,10 +137,11 @@ void evict_locked(lcp_server *S, Producer &P) {
 
 bool grow_scratch(lcp_server *S, int lane, size_t bytes) {
   if (S->scratch_cap[lane] >= bytes) return true;
-  if (S->scratch[lane]) cudaFree(S->scratch[lane]);
+  cudaStream_t st = S->streams[lane];
+  if (S->scratch[lane]) cudaFreeAsync(S->scratch[lane], st);
   S->scratch[lane] = nullptr;
   S->scratch_cap[lane] = 0;
-  if (cudaMalloc(&S->scratch[lane], bytes) != cudaSuccess) {
+  if (cudaMallocAsync(&S->scratch[lane], bytes, st) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -153,7 +169,7 @@ lcp_status run_compress(lcp_server *S, int lane, Producer &P, const lcp_request 
   f.index = P.next;
   f.size = size;
   f.method = chosen;
-  if (cudaMalloc(&f.buf, std::max<size_t>(size, 16)) != cudaSuccess) {
+  if (cudaMallocAsync(&f.buf, std::max<size_t>(size, 16), st) != cudaSuccess) {
     cudaGetLastError();
     return LCP_ERR_NOMEM;
   }
@@ -164,7 +180,7 @@ lcp_status run_compress(lcp_server *S, int lane, Producer &P, const lcp_request 
                                    st) != cudaSuccess) ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(f.buf);
+    cudaFreeAsync(f.buf, st);
     return LCP_ERR_CUDA;
   }
   // Algorithm 1 bookkeeping: an LCP-S frame that opens a batch is the anchor
@@ -182,47 +198,58 @@ lcp_status run_compress(lcp_server *S, int lane, Producer &P, const lcp_request 
   P.frames[f.index] = f;
   S->stored += size;
   P.next += 1;
-  evict_locked(S, P);
+  evict_locked(S, P, st);
   return (r.d_bytes != nullptr && !copy_out) ? LCP_ERR_CAPACITY : LCP_OK;
 }
 
-lcp_status run_decompress(lcp_server *S, int lane, Producer &P, const lcp_request &r,
+// the frames decoding `frame` needs, in stream order (empty: not decodable)
+std::vector<uint64_t> chain_locked(const lcp_server *S, const Producer &P, uint64_t frame) {
+  std::vector<uint64_t> chain;
+  auto it = P.frames.find(frame);
+  if (it == P.frames.end()) return chain;  // never coded, or no longer retained
+  const uint64_t b0 = frame - frame % S->batch;
+  uint64_t start = frame;
+  for (;; --start) {  // the latest LCP-S frame of the batch at or before `frame`
+    auto jt = P.frames.find(start);
+    if (jt == P.frames.end()) return {};
+    if (jt->second.method == LCP_SPATIAL || start == b0) break;
+  }
+  const Frame &s0 = P.frames.at(start);
+  if (s0.method == LCP_TEMPORAL) {  // the batch opens with LCP-T: its anchor first
+    if (!s0.has_anchor || !P.frames.count(s0.anchor)) return {};
+    chain.push_back(s0.anchor);
+  }
+  for (uint64_t g = start; g <= frame; ++g) chain.push_back(g);
+  return chain;
+}
+
+lcp_status run_decompress(lcp_server *S, int lane, Producer &P, const Pending &job,
                           lcp_response &out) {
+  const lcp_request &r = job.req;
   lcp_ctx *ctx = S->ctxs[lane];
   cudaStream_t st = S->streams[lane];
-  // the frames to decode, in order: (the anchor,) the batch start .. frame
-  std::vector<Frame> chain;
+  std::vector<const void *> ins;
+  std::vector<size_t> sizes;
   {
     std::lock_guard<std::mutex> lk(S->mu);
-    auto it = P.frames.find(r.frame);
-    if (it == P.frames.end()) return LCP_ERR_STATE;  // never coded, or no longer retained
-    const uint64_t b0 = r.frame - r.frame % S->batch;
-    for (uint64_t g = b0; g <= r.frame; ++g) {
-      auto jt = P.frames.find(g);
-      if (jt == P.frames.end()) return LCP_ERR_STATE;
-      chain.push_back(jt->second);
+    for (uint64_t g : job.chain) {
+      const Frame &f = P.frames.at(g);  // pinned: still retained
+      ins.push_back(f.buf);
+      sizes.push_back(f.size);
     }
-    if (chain.front().method == LCP_TEMPORAL) {
-      if (!chain.front().has_anchor) return LCP_ERR_STATE;
-      auto at = P.frames.find(chain.front().anchor);
-      if (at == P.frames.end()) return LCP_ERR_STATE;
-      chain.insert(chain.begin(), at->second);
-    }
+    const Frame &f = P.frames.at(job.chain.back());
+    out.frame = f.index;
+    out.size = f.size;
+    out.method = f.method;
   }
-  lcp_traj *dec = nullptr;
-  lcp_status s = lcp_traj_create(ctx, S->batch, 8, &dec);
-  if (s != LCP_OK) return s;
-  for (size_t k = 0; k < chain.size() && s == LCP_OK; ++k) {
-    uint64_t n_out = 0;
-    uint32_t d_out = 0;
-    s = lcp_decompress(ctx, dec, chain[k].buf, chain[k].size, r.d_out, r.n_cap, &n_out, &d_out,
-                       st);
-    out.frame = chain[k].index;
-    out.size = chain[k].size;
-    out.method = chain[k].method;
+  if (!S->dec[lane]) {
+    lcp_status s = lcp_traj_create(ctx, S->batch, 8, &S->dec[lane]);
+    if (s != LCP_OK) return s;
   }
-  lcp_traj_destroy(dec);
-  return s;
+  uint64_t n_out = 0;
+  uint32_t d_out = 0;
+  return (lcp_status)lcp::decode_chain(ctx, S->dec[lane], ins.data(), sizes.data(),
+                                       (int)ins.size(), r.d_out, r.n_cap, &n_out, &d_out, st);
 }
 
 void lane_loop(lcp_server *S, int lane) {
@@ -248,7 +275,7 @@ void lane_loop(lcp_server *S, int lane) {
     out.enqueue_ms = job.enqueue_ms;
     out.start_ms = S->now_ms();
     out.status = job.req.op == LCP_REQ_COMPRESS ? run_compress(S, lane, P, job.req, out)
-                                                : run_decompress(S, lane, P, job.req, out);
+                                                : run_decompress(S, lane, P, job, out);
     out.done_ms = S->now_ms();
     {
       std::lock_guard<std::mutex> lk(S->mu);
@@ -256,6 +283,10 @@ void lane_loop(lcp_server *S, int lane) {
       if (pr != S->promised.end()) {
         S->reserved -= pr->second;
         S->promised.erase(pr);
+      }
+      for (uint64_t g : job.chain) {  // unpin
+        auto it = P.frames.find(g);
+        if (it != P.frames.end()) it->second.pins -= 1;
       }
       S->done[job.ticket] = out;
       P.busy = false;
@@ -287,6 +318,14 @@ lcp_status lcp_server_create(int device, int lanes, uint32_t batch, uint64_t hbm
   S->budget = hbm_budget;
   S->retain = 2 * batch;
   S->t0 = Clock::now();
+  {  // freed container memory stays in the device's default pool for reuse
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+  }
   for (int k = 0; k < lanes; ++k) {
     lcp_ctx *c = nullptr;
     cudaStream_t st = nullptr;
@@ -301,6 +340,7 @@ lcp_status lcp_server_create(int device, int lanes, uint32_t batch, uint64_t hbm
     S->streams.push_back(st);
     S->scratch.push_back(nullptr);
     S->scratch_cap.push_back(0);
+    S->dec.push_back(nullptr);
   }
   for (int k = 0; k < lanes; ++k) S->threads.emplace_back(lane_loop, S, k);
   *out = S;
@@ -328,11 +368,17 @@ lcp_status lcp_server_submit(lcp_server *S, const lcp_request *r, uint64_t *tick
     P.n = r->n;
     P.d = r->d;
   }
+  std::vector<uint64_t> chain;
+  if (r->op == LCP_REQ_DECOMPRESS) {  // refused now when not decodable; else pinned
+    chain = chain_locked(S, P, r->frame);
+    if (chain.empty()) return LCP_ERR_STATE;
+    for (uint64_t g : chain) P.frames.at(g).pins += 1;
+  }
   const uint64_t t = S->next_ticket++;
   S->outstanding.insert(t);
   S->reserved += need;
   S->promised[t] = need;
-  P.queue.push_back(Pending{t, *r, S->now_ms()});
+  P.queue.push_back(Pending{t, *r, S->now_ms(), std::move(chain)});
   if (!P.queued && !P.busy) {
     P.queued = true;
     S->ready.push_back(r->producer);
@@ -392,10 +438,13 @@ lcp_status lcp_server_destroy(lcp_server *S) {
   S->cv_work.notify_all();
   for (auto &t : S->threads) t.join();
   cudaSetDevice(S->device);
+  for (size_t k = 0; k < S->streams.size(); ++k) cudaStreamSynchronize(S->streams[k]);
   for (auto &kv : S->prods) {
     for (auto &f : kv.second.frames) cudaFree(f.second.buf);
     if (kv.second.traj) lcp_traj_destroy(kv.second.traj);
   }
+  for (lcp_traj *t : S->dec)
+    if (t) lcp_traj_destroy(t);
   for (size_t k = 0; k < S->ctxs.size(); ++k) {
     if (S->scratch[k]) cudaFree(S->scratch[k]);
     cudaStreamDestroy(S->streams[k]);
