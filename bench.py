@@ -765,6 +765,7 @@ def main():
     ap.add_argument("--sample", type=int, default=0, help="CPU-baseline sample particles")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="default schedule, no autotuning")
     ap.add_argument("--n", type=int, default=0, help="override the particle count (small cases)")
     ap.add_argument("--seconds", type=float, default=0.0, help="serving: measured seconds")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: offered requests/s")
@@ -806,6 +807,12 @@ def main():
     if p == 0:  # exact block-size search (Sec. "Best block size"), once per frame
         r = ctx.compress(Xd, w["eb"], w["mode"], p=0, out=out)
         p = int(np.frombuffer(out[12:16].cpu().numpy().tobytes(), np.uint32)[0])
+    # schedule autotuner (chunk size within 1% of the default's bytes, sort
+    # partition width), once per frame shape, untimed
+    sched = {"log2_chunk": 10, "bucket_delta": 0, "tuned": False}
+    if not args.no_tune:
+        sched = dict(ctx.tune(Xd, w["eb"], w["mode"], p, max_growth=0.01), tuned=True)
+        ctx.set_schedule(sched["log2_chunk"], sched["bucket_delta"])
     stream = torch.cuda.current_stream(dev)
 
     def step(profile=None):
@@ -919,7 +926,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 in, integer codes",
             "data": "synthetic",
             "config": {"workload": name, "desc": w["desc"], "particles": N, "fields": D,
-                       "eb": w["eb"], "eb_mode": w["mode"], "p": p,
+                       "eb": w["eb"], "eb_mode": w["mode"], "p": p, "schedule": sched,
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"input {raw / 1e9:.2f} GB > 126 MB L2 every step (no flush)"},
             "compress_gbs": raw / (tcm * 1e-3) / 1e9,

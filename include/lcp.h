@@ -170,6 +170,44 @@ LCP_API lcp_status lcp_decompress_frame(lcp_ctx *ctx, lcp_traj *dec,
                                 uint64_t count, uint64_t target, float *d_out, uint64_t n_cap,
                                 uint64_t *n_out, uint32_t *d_fields, void *stream);
 
+/*
+ * Schedule of a context: knobs of how its compressions run.
+ *   log2_chunk   5..10 (default 10): every stream is cut into chunks of
+ *                2^log2_chunk symbols that decode independently (Sec. "Block
+ *                coding" names the coders; the chunking is this library's).
+ *                Recorded in each container's header, so it is part of the
+ *                bytes like p: smaller chunks cost chunk-table bytes and buy
+ *                decoding parallelism.  Decoders accept every value.
+ *   bucket_delta -4..1 (default 0): shift of the width of the first sort
+ *                partition (up to 2^15 buckets).  Never changes the bytes.
+ * The paper's own tuning is its block-size choice (lcp_choose_block_size);
+ * these knobs are GPU schedule parameters with no counterpart there.
+ */
+typedef struct {
+  uint32_t log2_chunk;
+  int32_t bucket_delta;
+  uint32_t reserved[6]; /* zero */
+} lcp_schedule;
+/* Applies a schedule to the context's later compressions (NULL: defaults);
+ * ERR_ARG outside the ranges above. */
+LCP_API lcp_status lcp_ctx_set_schedule(lcp_ctx *ctx, const lcp_schedule *schedule);
+LCP_API lcp_status lcp_ctx_get_schedule(const lcp_ctx *ctx, lcp_schedule *out);
+/*
+ * Autotuner of the schedule for one frame shape: LCP-S round trips
+ * (compress then decompress) of d_fields at bound eb and block multiplier p
+ * (0: the exact block-size search first, Sec. "Best block size"), for
+ * log2_chunk in {8, 9, 10} and bucket_delta in {-2, -1, 0, 1}, each timed
+ * with CUDA events over `reps` round trips after one untimed.  The fastest
+ * schedule whose container is at most (1 + max_growth) times the default
+ * schedule's size is returned in *best (and its mean round-trip ms in
+ * *best_ms, optional); the context's own schedule is left as it was.
+ * Allocates a worst-case container and an [d][n] output buffer for the
+ * duration of the call (stream-ordered).  Synchronizes `stream`.
+ */
+LCP_API lcp_status lcp_tune_schedule(lcp_ctx *ctx, const float *d_fields, uint64_t n, uint32_t d,
+                             double eb, lcp_eb_mode mode, uint32_t p, double max_growth,
+                             int reps, lcp_schedule *best, float *best_ms, void *stream);
+
 /* Reads n, d, method and flags from a container's header (device memory). */
 LCP_API lcp_status lcp_peek(const void *d_in, size_t in_size, uint64_t *n, uint32_t *d,
                     lcp_method *method, uint32_t *flags, void *stream);

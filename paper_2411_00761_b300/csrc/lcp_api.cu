@@ -16,7 +16,6 @@ unsigned long long lcp::g_launches = 0;
 
 namespace {
 
-constexpr uint32_t kLog2Chunk = 10;  // chunk of 1024 symbols
 constexpr uint32_t kFlagFirst = 1u, kFlagRefAnchor = 2u;
 constexpr uint32_t kFlagRequant = 4u;  // reference codes re-quantized on the frame's grid
 
@@ -99,10 +98,13 @@ void note_cuda_error(cudaError_t e, const char *what, int line) {
     if (_s != OK) return _s; \
   } while (0)
 
-uint32_t bits_target(uint64_t n) {
+// level-1 partition bits: about 2048 keys per bucket at most, up to 2^14
+// buckets, shifted by the schedule's delta (0 .. 15)
+uint32_t bits_target(uint64_t n, int delta = 0) {
   uint32_t b = 0;
   while (b < 14 && ((2048ull << b) < n)) ++b;
-  return b;
+  const int t = (int)b + delta;
+  return (uint32_t)(t < 0 ? 0 : (t > 15 ? 15 : t));
 }
 
 bool aligned16(const void *p) { return (((uintptr_t)p) & 15u) == 0; }
@@ -128,6 +130,11 @@ struct Profile {
 struct lcp_ctx {
   int device = 0;
   int sms = 148;
+  // schedule (lcp_ctx_set_schedule): chunk size of the streams (recorded in
+  // every container), shift of the level-1 partition bits (never changes the
+  // bytes)
+  uint32_t log2_chunk = 10;
+  int bucket_delta = 0;
   Workspace ws;
   Profile prof;
   Plan *h_plan = nullptr;
@@ -230,7 +237,8 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   prof_begin(c, "s.minmax", s);
   launch_minmax(X, n, d, P<MinMax>(w.mm), sms, s);
   prof_end(c, s);
-  launch_plan(P<MinMax>(w.mm), n, d, eb, mode, p, bits_target(n), 0, P<Plan>(w.plan), s);
+  launch_plan(P<MinMax>(w.mm), n, d, eb, mode, p, bits_target(n, c->bucket_delta), 0,
+              P<Plan>(w.plan), s);
   CK(cudaGetLastError());
   int st = read_plan(c, s);
   if (st != OK) return st;
@@ -338,7 +346,7 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   sa.perm = want_perm ? perm_out : nullptr;
   sa.q_in = want_q ? P<int32_t>(w.q_in) : nullptr;
   sa.q_slot = want_q ? q_slot_out : nullptr;
-  sa.log2_chunk = kLog2Chunk;
+  sa.log2_chunk = c->log2_chunk;
   sa.n = n;
   prof_begin(c, "s.subsort", s);
   launch_subsort(sa, sms, s);
@@ -362,7 +370,7 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   la.q_in = want_q ? P<int32_t>(w.q_in) : nullptr;
   la.q_slot = want_q ? q_slot_out : nullptr;
   la.outl_idx = P<uint32_t>(w.outl_idx);
-  la.log2_chunk = kLog2Chunk;
+  la.log2_chunk = c->log2_chunk;
   la.n = n;
   prof_begin(c, "s.local_sort", s);
   launch_local(la, 4 * sms, s);
@@ -382,13 +390,13 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   // 8. codebooks and the container layout
   prof_begin(c, "s.codebook", s);
   launch_codebook(3, P<uint32_t>(w.hist), P<unsigned long long>(w.maxv),
-                  P<unsigned long long>(w.nvals), kLog2Chunk, P<uint8_t>(w.cbwork),
+                  P<unsigned long long>(w.nvals), c->log2_chunk, P<uint8_t>(w.cbwork),
                   P<StreamDesc>(w.desc),
                   P<uint32_t>(w.codes), P<uint8_t>(w.lens), P<uint16_t>(w.tables), s);
   LayoutArgs L;
   L.method = 0;
   L.d = d;
-  L.log2_chunk = kLog2Chunk;
+  L.log2_chunk = c->log2_chunk;
   L.flags = flags;
   L.p = p;
   L.n = n;
@@ -408,19 +416,19 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
     StreamDesc *D = P<StreamDesc>(w.desc);
     prof_begin(c, "s.encode_ids", s);
     launch_encode_u64(P<unsigned long long>(w.s_id), n, D + 0, P<uint32_t>(w.codes),
-                      P<uint8_t>(w.lens), kLog2Chunk, out, P<Summary>(w.summary),
+                      P<uint8_t>(w.lens), c->log2_chunk, out, P<Summary>(w.summary),
                       P<unsigned long long>(w.chunk_bits), P<unsigned long long>(w.chunk_off), sms,
                       s);
     prof_end(c, s);
     prof_begin(c, "s.encode_counts", s);
     launch_encode_u64(P<unsigned long long>(w.s_cnt), n, D + 1, P<uint32_t>(w.codes) + kAlpha,
-                      P<uint8_t>(w.lens) + kAlpha, kLog2Chunk, out, P<Summary>(w.summary),
+                      P<uint8_t>(w.lens) + kAlpha, c->log2_chunk, out, P<Summary>(w.summary),
                       P<unsigned long long>(w.chunk_bits), P<unsigned long long>(w.chunk_off), sms,
                       s);
     prof_end(c, s);
     prof_begin(c, "s.encode_rel", s);
     launch_encode_u32(P<uint32_t>(w.s_rel), n, D + 2, P<uint32_t>(w.codes) + 2 * kAlpha,
-                      P<uint8_t>(w.lens) + 2 * kAlpha, kLog2Chunk, out, P<Summary>(w.summary),
+                      P<uint8_t>(w.lens) + 2 * kAlpha, c->log2_chunk, out, P<Summary>(w.summary),
                       P<unsigned long long>(w.chunk_bits), P<unsigned long long>(w.chunk_off), sms,
                       s);
     prof_end(c, s);
@@ -474,13 +482,13 @@ int compress_t_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   note_launch();
   k_set_u64<<<1, 1, 0, s>>>(P<unsigned long long>(w.nvals), (unsigned long long)(n * d));
   launch_codebook(1, P<uint32_t>(w.hist), P<unsigned long long>(w.maxv),
-                  P<unsigned long long>(w.nvals), kLog2Chunk, P<uint8_t>(w.cbwork),
+                  P<unsigned long long>(w.nvals), c->log2_chunk, P<uint8_t>(w.cbwork),
                   P<StreamDesc>(w.desc),
                   P<uint32_t>(w.codes), P<uint8_t>(w.lens), P<uint16_t>(w.tables), s);
   LayoutArgs L;
   L.method = 1;
   L.d = d;
-  L.log2_chunk = kLog2Chunk;
+  L.log2_chunk = c->log2_chunk;
   L.flags = flags;
   L.p = 0;
   L.n = n;
@@ -497,7 +505,7 @@ int compress_t_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   if (!size_only) {
     StreamDesc *D = P<StreamDesc>(w.desc);
     launch_encode_u32(P<uint32_t>(w.sym), n * d, D + 0, P<uint32_t>(w.codes), P<uint8_t>(w.lens),
-                      kLog2Chunk, out, P<Summary>(w.summary),
+                      c->log2_chunk, out, P<Summary>(w.summary),
                       P<unsigned long long>(w.chunk_bits), P<unsigned long long>(w.chunk_off), sms,
                       s);
     // patches in increasing symbol index
@@ -540,6 +548,12 @@ int check_p(uint32_t p, uint32_t d) {
 }
 
 // p == 0: exact size for each candidate, smallest wins, ties to the smaller p
+// one container (below, with the decompression entry points); codes_only: a
+// frame decoded only as the reference of later frames
+int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, float *out,
+                    uint64_t n_cap, uint64_t *n_out, uint32_t *d_out, cudaStream_t s,
+                    bool codes_only = false);
+
 int choose_p(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double eb, int mode,
              uint32_t *best, cudaStream_t s) {
   const uint32_t cands[5] = {2, 4, 8, 16, 32};
@@ -1039,6 +1053,128 @@ lcp_status lcp_compress(lcp_ctx *c, lcp_traj *traj, const float *d_fields, uint6
   return (lcp_status)st;
 }
 
+lcp_status lcp_ctx_set_schedule(lcp_ctx *c, const lcp_schedule *sc) {
+  if (!c) return LCP_ERR_ARG;
+  if (!sc) {
+    c->log2_chunk = 10;
+    c->bucket_delta = 0;
+    return LCP_OK;
+  }
+  if (sc->log2_chunk < 5 || sc->log2_chunk > 10 || sc->bucket_delta < -4 ||
+      sc->bucket_delta > 1)
+    return LCP_ERR_ARG;
+  c->log2_chunk = sc->log2_chunk;
+  c->bucket_delta = sc->bucket_delta;
+  return LCP_OK;
+}
+
+lcp_status lcp_ctx_get_schedule(const lcp_ctx *c, lcp_schedule *out) {
+  if (!c || !out) return LCP_ERR_ARG;
+  memset(out, 0, sizeof(*out));
+  out->log2_chunk = c->log2_chunk;
+  out->bucket_delta = c->bucket_delta;
+  return LCP_OK;
+}
+
+lcp_status lcp_tune_schedule(lcp_ctx *c, const float *d_fields, uint64_t n, uint32_t d, double eb,
+                             lcp_eb_mode mode, uint32_t p, double max_growth, int reps,
+                             lcp_schedule *best, float *best_ms, void *stream) {
+  if (!c || !best) return LCP_ERR_ARG;
+  int st = check_frame_args(d_fields, n, d, eb, mode);
+  if (st != OK) return (lcp_status)st;
+  if (!(max_growth >= 0.0) || reps < 1 || reps > 100 || n == 0) return LCP_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint32_t keep_lc = c->log2_chunk;
+  const int keep_bd = c->bucket_delta;
+  if (p == 0) {  // the exact block-size search, once
+    c->log2_chunk = 10;
+    c->bucket_delta = 0;
+    st = choose_p(c, d_fields, n, d, eb, mode, &p, s);
+    if (st != OK) {
+      c->log2_chunk = keep_lc;
+      c->bucket_delta = keep_bd;
+      return (lcp_status)st;
+    }
+  } else if (check_p(p, d) != OK) {
+    return LCP_ERR_ARG;
+  }
+  const size_t cap = lcp_max_compressed_size(n, d);
+  void *buf = nullptr;
+  float *y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaMallocAsync(&buf, cap, s) != cudaSuccess ||
+      cudaMallocAsync((void **)&y, (size_t)n * d * 4, s) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    if (buf) cudaFreeAsync(buf, s);
+    if (y) cudaFreeAsync(y, s);
+    if (e0) cudaEventDestroy(e0);
+    return LCP_ERR_NOMEM;
+  }
+  // candidates: chunk sizes 2^8 .. 2^10 (smaller chunks decode with more
+  // lanes but cost table bytes), level-1 partition widths around the default
+  const uint32_t lcs[3] = {10, 9, 8};
+  const int bds[4] = {0, -1, -2, 1};
+  uint64_t base_size = 0;
+  float best_t = 0.0f;
+  bool have = false;
+  for (uint32_t lc : lcs) {
+    for (int bd : bds) {
+      c->log2_chunk = lc;
+      c->bucket_delta = bd;
+      float tsum = 0.0f;
+      uint64_t size = 0;
+      for (int r = 0; r <= reps && st == OK; ++r) {  // the first round warms up
+        size_t sz = 0;
+        uint64_t total = 0;
+        st = cudaEventRecord(e0, s) == cudaSuccess ? OK : ERR_CUDA;
+        if (st == OK)
+          st = compress_s_impl(c, d_fields, n, d, eb, mode, p, 0, (uint8_t *)buf, cap, false,
+                               nullptr, nullptr, &total, s);
+        if (st == OK) {
+          sz = (size_t)total;
+          uint64_t no = 0;
+          uint32_t dd = 0;
+          st = decompress_impl(c, nullptr, (const uint8_t *)buf, sz, y, n, &no, &dd, s);
+        }
+        if (st == OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                         cudaEventSynchronize(e1) != cudaSuccess))
+          st = ERR_CUDA;
+        if (st == OK && r > 0) {
+          float ms = 0.0f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          tsum += ms;
+        }
+        size = sz;
+      }
+      if (st != OK) break;
+      if (lc == 10 && bd == 0) base_size = size;
+      const float t = tsum / (float)reps;
+      const bool fits = (double)size <= (1.0 + max_growth) * (double)base_size;
+      if (fits && (!have || t < best_t)) {
+        have = true;
+        best_t = t;
+        memset(best, 0, sizeof(*best));
+        best->log2_chunk = lc;
+        best->bucket_delta = bd;
+      }
+    }
+    if (st != OK) break;
+  }
+  cudaFreeAsync(buf, s);
+  cudaFreeAsync(y, s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  c->log2_chunk = keep_lc;
+  c->bucket_delta = keep_bd;
+  if (st != OK) return (lcp_status)st;
+  if (best_ms) *best_ms = best_t;
+  return LCP_OK;
+}
+
 lcp_status lcp_choose_block_size(lcp_ctx *c, const float *d_fields, uint64_t n, uint32_t d,
                                  double eb, lcp_eb_mode mode, uint64_t sample, uint32_t *p_best,
                                  uint64_t *sizes, void *stream) {
@@ -1217,7 +1353,7 @@ int read_header(lcp_ctx *c, const uint8_t *in, size_t in_size, Header &h, cudaSt
 // codes into the trajectory, no values; out is ignored)
 int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, float *out,
                     uint64_t n_cap, uint64_t *n_out, uint32_t *d_out, cudaStream_t s,
-                    bool codes_only = false) {
+                    bool codes_only) {
   Header h;
   TRY(read_header(c, in, in_size, h, s));
   if (n_out) *n_out = h.n;

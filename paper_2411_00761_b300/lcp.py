@@ -62,6 +62,10 @@ SIGNATURES = {
     "lcp_server_destroy": (C.c_int, [_vp]),
     "lcp_compress_batch": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp, C.c_int]),
     "lcp_decompress_batch": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp, C.c_int]),
+    "lcp_ctx_set_schedule": (C.c_int, [_vp, _vp]),
+    "lcp_ctx_get_schedule": (C.c_int, [_vp, _vp]),
+    "lcp_tune_schedule": (C.c_int, [_vp, _vp, _u64, _u32, C.c_double, C.c_int, _u32, C.c_double,
+                                    C.c_int, _vp, C.POINTER(C.c_float), _vp]),
     "lcp_decompress_frames": (C.c_int, [_vp, _vp, C.POINTER(_vp), C.POINTER(_sz), _u64, _u64, _u64,
                                         C.POINTER(_vp), _u64, C.POINTER(_u64), C.POINTER(_u32),
                                         _vp]),
@@ -76,6 +80,11 @@ class CompressJob(C.Structure):
                 ("mode", C.c_int), ("p", _u32), ("method", C.c_int), ("d_out", _vp),
                 ("out_cap", _sz), ("out_size", _sz), ("chosen", C.c_int), ("status", C.c_int),
                 ("ms", C.c_float)]
+
+
+class Schedule(C.Structure):
+    """lcp_schedule (include/lcp.h)."""
+    _fields_ = [("log2_chunk", _u32), ("bucket_delta", C.c_int32), ("reserved", _u32 * 6)]
 
 
 class Request(C.Structure):
@@ -239,6 +248,28 @@ class Context:
                                  _stream(stream))
         _check(st, "lcp_decompress")
         return out.view(-1)[: d * n].view(d, n)
+
+    def set_schedule(self, log2_chunk: int = 10, bucket_delta: int = 0):
+        """lcp_ctx_set_schedule."""
+        sc = Schedule(log2_chunk, bucket_delta)
+        _check(_lib.lcp_ctx_set_schedule(self.h, C.byref(sc)), "lcp_ctx_set_schedule")
+
+    def schedule(self) -> dict:
+        sc = Schedule()
+        _check(_lib.lcp_ctx_get_schedule(self.h, C.byref(sc)), "lcp_ctx_get_schedule")
+        return dict(log2_chunk=sc.log2_chunk, bucket_delta=sc.bucket_delta)
+
+    def tune(self, X: torch.Tensor, eb: float, mode="abs", p: int = 0, max_growth: float = 0.01,
+             reps: int = 2, stream=None) -> dict:
+        """lcp_tune_schedule: the fastest schedule for this frame shape (the
+        context's own schedule is unchanged)."""
+        d, n = X.shape
+        sc = Schedule()
+        ms = C.c_float(0.0)
+        _check(_lib.lcp_tune_schedule(self.h, _ptr(X), n, d, float(eb), _mode(mode), p,
+                                      float(max_growth), reps, C.byref(sc), C.byref(ms),
+                                      _stream(stream)), "lcp_tune_schedule")
+        return dict(log2_chunk=sc.log2_chunk, bucket_delta=sc.bucket_delta, ms=ms.value)
 
     def decompress_frames(self, containers: list, first: int, last: int | None = None,
                           batch: int | None = None, traj: "Trajectory | None" = None,

@@ -397,16 +397,20 @@ def test_bench_config_bytes_16M(ctx, orc):
     assert o["M"] > 1 << 22
 
 
-def test_bench_config_full_frame_64M(ctx, orc):
+def test_bench_config_full_frame_64M(lcp, orc):
     """The benchmarked frame itself (2^26 particles x 6 fields, p = 8), in the
-    bench's launch configuration: the container the bench times is decoded by
-    the oracle, and every decoded value equals the GPU's decode bit for bit;
-    the slot permutation is a permutation, every particle is within its bound,
-    and on 2^21 sampled slots the decoded code equals the oracle's own Q1 of
-    the particle's value."""
+    bench's launch configuration (the schedule chosen by the autotuner, as the
+    bench does): the container the bench times is decoded by the oracle, and
+    every decoded value equals the GPU's decode bit for bit; the slot
+    permutation is a permutation, every particle is within its bound, and on
+    2^21 sampled slots the decoded code equals the oracle's own Q1 of the
+    particle's value."""
     Xf = synth.cosmology(1 << 26, 2)
     d, n = Xf.shape
     Xd = to_dev(Xf)
+    ctx = lcp.Context(0)
+    sc = ctx.tune(Xd, 1e-3, "rel", 8, max_growth=0.01)
+    ctx.set_schedule(sc["log2_chunk"], sc["bucket_delta"])
     r0 = ctx.compress(Xd, 1e-3, "rel", 8)  # the bench's call
     r = ctx.compress(Xd, 1e-3, "rel", 8, perm=True)
     assert torch.equal(r0["bytes"], r["bytes"])
@@ -429,6 +433,46 @@ def test_bench_config_full_frame_64M(ctx, orc):
     for f in range(d):
         q = orc.q1(Xf[f, pi], float(m[f]), float(e[f]))
         assert np.array_equal(q, qo[f, slots].astype(np.int64))
+
+
+@pytest.mark.parametrize("lc", [5, 8, 9])
+def test_schedule_chunks_match_oracle(lcp, orc, lc):
+    """Chunks of 2^lc symbols (a schedule knob recorded in the container):
+    LCP-S containers of the benchmarked configuration (2^22 particles) and an
+    LCP-T frame equal the oracle's at the same chunk size byte for byte, and
+    decode bit for bit."""
+    ctx = lcp.Context(0)
+    ctx.set_schedule(lc, 0)
+    assert ctx.schedule()["log2_chunk"] == lc
+    Xf = synth.cosmology(1 << 22, 2)
+    o = orc.compress_s(Xf, 1e-3, "rel", 8, log2_chunk=lc)
+    r = ctx.compress(to_dev(Xf), 1e-3, "rel", 8)
+    assert gpu_bytes(r) == o["bytes"]
+    Y = ctx.decompress(r["bytes"]).cpu().numpy()
+    Yo, _ = orc.decompress(o["bytes"])
+    assert np.array_equal(Y.view(np.uint32), Yo.view(np.uint32))
+    frames = list(synth.brownian_trajectory(30011, 2, 5))
+    tr = lcp.Trajectory(ctx, batch=10, p=8)
+    r0 = ctx.compress(to_dev(frames[0]), 1e-3, "abs", traj=tr, method="spatial")
+    o0 = orc.compress_s(frames[0], 1e-3, "abs", 8, log2_chunk=lc, flags=1)
+    assert gpu_bytes(r0) == o0["bytes"]
+    r1 = ctx.compress(to_dev(frames[1]), 1e-3, "abs", traj=tr, method="temporal")
+    o1 = orc.compress_t(frames[1], 1e-3, "abs", o0["q"], o0["pi"], log2_chunk=lc)
+    assert gpu_bytes(r1) == o1["bytes"]
+
+
+def test_schedule_bucket_width_keeps_bytes(lcp, orc):
+    """The width of the first sort partition changes no byte."""
+    Xf = synth.cosmology(300007, 4)
+    ref = orc.compress_s(Xf, 1e-3, "rel", 8)["bytes"]
+    ctx = lcp.Context(0)
+    for bd in (-4, -2, -1, 1):
+        ctx.set_schedule(10, bd)
+        assert gpu_bytes(ctx.compress(to_dev(Xf), 1e-3, "rel", 8)) == ref, bd
+    with pytest.raises(lcp.LcpError):
+        ctx.set_schedule(11, 0)
+    with pytest.raises(lcp.LcpError):
+        ctx.set_schedule(10, 2)
 
 
 def test_full_size_md_sampled(ctx, orc, lcp):
