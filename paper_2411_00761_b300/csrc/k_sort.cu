@@ -175,17 +175,24 @@ void launch_scan_small(const unsigned long long *in, uint32_t n, unsigned long l
 }
 
 // ---------------------------------------------------------------------------
-// scatter: same tiles as the quantize pass; shared-memory cursors per bucket
+// scatter: same tiles as the quantize pass; shared-memory cursors per bucket.
+// One launch serves the buckets [blo, bhi) only: every 8-byte key write
+// opens or extends a partially written 32-byte sector at its bucket's write
+// front in this tile, and all tiles x buckets fronts of a frame exceed L2 at
+// 64M keys, so partial sectors would be evicted and rewritten.  Passes over
+// bucket ranges keep each pass's fronts L2-resident; keys outside the range
+// are read and skipped.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_scatter(const unsigned long long *__restrict__ keys,
                                                  uint64_t n, const Plan *__restrict__ plan,
                                                  uint32_t nb1, uint64_t span,
                                                  const uint32_t *__restrict__ tile_off,
                                                  unsigned long long *__restrict__ keys_out,
-                                                 uint32_t *__restrict__ idx_out) {
+                                                 uint32_t *__restrict__ idx_out, uint32_t blo,
+                                                 uint32_t bhi) {
   extern __shared__ uint32_t s_cur[];
   const uint32_t *to = tile_off + (uint64_t)blockIdx.x * nb1;
-  for (uint32_t b = threadIdx.x; b < nb1; b += blockDim.x) s_cur[b] = to[b];
+  for (uint32_t b = threadIdx.x + blo; b < bhi; b += blockDim.x) s_cur[b - blo] = to[b];
   __syncthreads();
   if (plan->status != OK) return;
   const uint32_t shift = plan->part_shift, nb = nb1 - 1;
@@ -211,22 +218,26 @@ __global__ void __launch_bounds__(512) k_scatter(const unsigned long long *__res
     }
     // one cursor update per run of lanes with the same bucket
     uint32_t pos[kIlp];
+    bool in[kIlp];
 #pragma unroll
     for (int r = 0; r < kIlp; ++r) {
       const uint64_t i = i0 + (uint64_t)r * blockDim.x + threadIdx.x;
-      const bool valid = i < hi;
       const uint32_t b = (k[r] & kOutlierBit) ? nb : (uint32_t)(k[r] >> shift);
+      const bool valid = i < hi && b >= blo && b < bhi;
+      in[r] = valid;
+      pos[r] = 0u;
+      if (!__any_sync(0xffffffffu, valid)) continue;
       int leader;
       uint32_t rank, len;
       lane_runs(b, valid, leader, rank, len);
       uint32_t base = 0u;
-      if (valid && rank == 0u) base = atomicAdd(&s_cur[b], len);
+      if (valid && rank == 0u) base = atomicAdd(&s_cur[b - blo], len);
       pos[r] = __shfl_sync(0xffffffffu, base, leader) + rank;
     }
 #pragma unroll
     for (int r = 0; r < kIlp; ++r) {
       const uint64_t i = i0 + (uint64_t)r * blockDim.x + threadIdx.x;
-      if (i < hi) {
+      if (in[r]) {
         keys_out[pos[r]] = k[r];
         if (idx_out) idx_out[pos[r]] = (uint32_t)i;
       }
@@ -243,9 +254,19 @@ void launch_scatter(const unsigned long long *keys, uint64_t n, const Plan *plan
       cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
       cudaSuccess;
   (void)attr;
-  note_launch();
-  k_scatter<<<tiles, 512, sizeof(uint32_t) * nb1, s>>>(keys, n, plan, nb1, span, tile_off,
-                                                      keys_out, idx_out);
+  // passes: about 40 MB of 32-byte write fronts (tiles x buckets) each
+  const uint64_t fronts = (uint64_t)tiles * nb1 * 32ull;
+  const uint64_t budget = 40ull << 20;
+  const uint32_t passes =
+      (uint32_t)std::min<uint64_t>(16, std::max<uint64_t>(1, (fronts + budget - 1) / budget));
+  const uint32_t per = (nb1 + passes - 1) / passes;
+  for (uint32_t lo = 0; lo < nb1; lo += per) {
+    const uint32_t hi = std::min(nb1, lo + per);
+    note_launch();
+    k_scatter<<<tiles, 512, sizeof(uint32_t) * (hi - lo), s>>>(keys, n, plan, nb1, span,
+                                                               tile_off, keys_out, idx_out, lo,
+                                                               hi);
+  }
 }
 
 // ---------------------------------------------------------------------------
