@@ -188,9 +188,11 @@ __global__ void __launch_bounds__(512) k_scatter(const unsigned long long *__res
                                                  uint32_t nb1, uint64_t span,
                                                  const uint32_t *__restrict__ tile_off,
                                                  unsigned long long *__restrict__ keys_out,
-                                                 uint32_t *__restrict__ idx_out, uint32_t blo,
-                                                 uint32_t bhi) {
+                                                 uint32_t *__restrict__ idx_out,
+                                                 const uint32_t *__restrict__ bounds,
+                                                 uint32_t pass) {
   extern __shared__ uint32_t s_cur[];
+  const uint32_t blo = bounds[pass], bhi = bounds[pass + 1];
   const uint32_t *to = tile_off + (uint64_t)blockIdx.x * nb1;
   for (uint32_t b = threadIdx.x + blo; b < bhi; b += blockDim.x) s_cur[b - blo] = to[b];
   __syncthreads();
@@ -245,27 +247,50 @@ __global__ void __launch_bounds__(512) k_scatter(const unsigned long long *__res
   }
 }
 
+// bucket bounds of the scatter passes: pass r takes the buckets whose keys
+// start in [r n / passes, (r + 1) n / passes) of the partitioned order
+// (bstart: exclusive bucket starts, bstart[nb1] = n), so passes move about
+// the same number of keys
+__global__ void k_scatter_bounds(const unsigned long long *__restrict__ bstart, uint32_t nb1,
+                                 uint64_t n, uint32_t passes, uint32_t *__restrict__ bounds) {
+  const uint32_t r = threadIdx.x;
+  if (r > passes) return;
+  if (r == passes) {
+    bounds[r] = nb1;
+    return;
+  }
+  const unsigned long long target = (unsigned long long)((n * (uint64_t)r) / passes);
+  uint32_t lo = 0, hi = nb1;  // first bucket with bstart >= target
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (bstart[mid] < target) lo = mid + 1;
+    else hi = mid;
+  }
+  bounds[r] = r == 0 ? 0u : lo;
+}
+
 void launch_scatter(const unsigned long long *keys, uint64_t n, const Plan *plan, uint32_t nb1,
-                    int tiles, const uint32_t *tile_off, unsigned long long *keys_out,
-                    uint32_t *idx_out, cudaStream_t s) {
+                    int tiles, const uint32_t *tile_off, const unsigned long long *bstart,
+                    uint32_t *bounds, unsigned long long *keys_out, uint32_t *idx_out,
+                    cudaStream_t s) {
   uint64_t span = (n + tiles - 1) / tiles;
   span = (span + 3) & ~3ull;
   static const bool attr =  // once per process, thread-safe
       cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
       cudaSuccess;
   (void)attr;
-  // passes: about 40 MB of 32-byte write fronts (tiles x buckets) each
+  // passes: about 40 MB of 32-byte write fronts (tiles x buckets) in all,
+  // split by key count
   const uint64_t fronts = (uint64_t)tiles * nb1 * 32ull;
   const uint64_t budget = 40ull << 20;
-  const uint32_t passes =
-      (uint32_t)std::min<uint64_t>(16, std::max<uint64_t>(1, (fronts + budget - 1) / budget));
-  const uint32_t per = (nb1 + passes - 1) / passes;
-  for (uint32_t lo = 0; lo < nb1; lo += per) {
-    const uint32_t hi = std::min(nb1, lo + per);
+  const uint32_t passes = (uint32_t)std::min<uint64_t>(
+      kScatterPassesMax, std::max<uint64_t>(1, (fronts + budget - 1) / budget));
+  note_launch();
+  k_scatter_bounds<<<1, 32, 0, s>>>(bstart, nb1, n, passes, bounds);
+  for (uint32_t r = 0; r < passes; ++r) {
     note_launch();
-    k_scatter<<<tiles, 512, sizeof(uint32_t) * (hi - lo), s>>>(keys, n, plan, nb1, span,
-                                                               tile_off, keys_out, idx_out, lo,
-                                                               hi);
+    k_scatter<<<tiles, 512, sizeof(uint32_t) * nb1, s>>>(keys, n, plan, nb1, span, tile_off,
+                                                         keys_out, idx_out, bounds, r);
   }
 }
 

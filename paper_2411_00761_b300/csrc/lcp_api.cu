@@ -50,7 +50,7 @@ struct Workspace {
       s_id, s_cnt, hist, maxv, nvals, mcount, kcount, desc, codes, lens,
       tables, chunk_bits, chunk_off, outl_idx, summary, q_in, q_slot, perm, sym, patch_s,
       patch_i, patch_x, patch_s2, patch_i2, patch_so, patch_io, dec_fields, hufft, err,
-      scan_tmp, cand, tq, fplan, fstatus, cbwork, sample, rq, lut;
+      scan_tmp, cand, tq, fplan, fstatus, cbwork, sample, rq, lut, sbounds;
 };
 
 __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
@@ -218,7 +218,9 @@ int ws_common(lcp_ctx *c, uint64_t n, uint32_t d) {
   TRY(grow(w.summary, sizeof(Summary)));
   TRY(grow(w.cbwork, codebook_work_size(3)));
   const uint64_t nd = n * d;
-  const uint64_t chunks = std::max<uint64_t>(nd, n) / 1024 + 2;
+  // per-chunk bit counts and offsets of the longest stream (n d values in
+  // LCP-T) at the context's chunk size
+  const uint64_t chunks = (std::max<uint64_t>(nd, n) >> c->log2_chunk) + 2;
   TRY(grow(w.chunk_bits, chunks * 8));
   TRY(grow(w.chunk_off, (chunks + 1) * 8));
   return OK;
@@ -252,6 +254,7 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   TRY(grow(w.tile_hist, (size_t)tiles * nb1 * 4));
   TRY(grow(w.btot, (size_t)nb1 * 8));
   TRY(grow(w.bstart, (size_t)(nb1 + 1) * 8));
+  TRY(grow(w.sbounds, (size_t)(kScatterPassesMax + 1) * 4));
   TRY(grow(w.s_rel, nn * 4));
   TRY(grow(w.tmp_bid, nn * 8));
   TRY(grow(w.tmp_pos, (nn + 1) * 4));  // block start slots
@@ -297,7 +300,8 @@ int compress_s_impl(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double e
   prof_end(c, s);
   prof_begin(c, "s.scatter", s);
   launch_scatter(P<unsigned long long>(w.keys), n, P<Plan>(w.plan), nb1, tiles,
-                 P<uint32_t>(w.tile_hist), P<unsigned long long>(w.keys2),
+                 P<uint32_t>(w.tile_hist), P<unsigned long long>(w.bstart),
+                 P<uint32_t>(w.sbounds), P<unsigned long long>(w.keys2),
                  want_perm ? P<uint32_t>(w.idx2) : nullptr, s);
   prof_end(c, s);
   CK(cudaGetLastError());

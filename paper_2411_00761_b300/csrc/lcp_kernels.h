@@ -58,9 +58,12 @@ void launch_scan_small(const unsigned long long *in, uint32_t n, unsigned long l
 void launch_bucket_offsets(uint32_t *tile_hist, int tiles, uint32_t nb1,
                            unsigned long long *bucket_start, unsigned long long *totals,
                            cudaStream_t s);
+// bounds: kScatterPassesMax + 1 entries (device scratch)
+constexpr uint32_t kScatterPassesMax = 16;
 void launch_scatter(const unsigned long long *keys, uint64_t n, const Plan *plan, uint32_t nb1,
-                    int tiles, const uint32_t *tile_off, unsigned long long *keys_out,
-                    uint32_t *idx_out, cudaStream_t s);
+                    int tiles, const uint32_t *tile_off, const unsigned long long *bstart,
+                    uint32_t *bounds, unsigned long long *keys_out, uint32_t *idx_out,
+                    cudaStream_t s);
 // level-2 split of the buckets above the split threshold (sub_off: per
 // split bucket, the offset of each sub-bucket) and the unit list of the
 // unsplit buckets and the outlier bucket
