@@ -145,13 +145,16 @@ def stage_bytes(stage: str, N, D, M, K, C):
 # scaled by the particle count; None unless every listed source file still
 # has the hash recorded at capture
 _SORT = ("paper_2411_00761_b300/csrc/k_sort.cu",)
+_DEC = ("paper_2411_00761_b300/csrc/k_decode.cu", "paper_2411_00761_b300/csrc/lcp_kernels.h")
 TRAFFIC_PROFILES = {
+    # s.split: the dominant kernel of the stage, k_split_big (k_split_hist and
+    # k_split_scan add ~7% of the stage's time)
+    ("cosmology", "s.split"): ("profiles/k_split_big_cosmology_16M.md", _SORT, 16777216),
     ("cosmology", "s.subsort"): ("profiles/k_subsort_cosmology_16M.md", _SORT, 16777216),
-    ("cosmology", "s.split"): ("profiles/k_split_cosmology_16M.md", _SORT, 16777216),
-    ("cosmology", "s.scatter"): ("profiles/k_scatter_cosmology_16M.md", _SORT, 16777216),
-    ("cosmology", "d.expand"): ("profiles/k_expand_blocks_cosmology_16M.md",
-                                ("paper_2411_00761_b300/csrc/k_decode.cu",
-                                 "paper_2411_00761_b300/csrc/lcp_common.cuh"), 16777216),
+    # every pass of the stage at 2^25 keys (the same number of passes as at 2^26)
+    ("cosmology", "s.scatter"): ("profiles/k_scatter_cosmology_32M.md", _SORT, 33554432),
+    ("cosmology", "d.expand"): ("profiles/k_expand_fast_cosmology_16M.md", _DEC, 16777216),
+    ("cosmology", "d.streams"): ("profiles/k_huff_decode_cosmology_16M.md", _DEC, 16777216),
 }
 
 
@@ -449,10 +452,19 @@ def batched_start(sizes, seed):
     return out
 
 
+def summary(ms_list, nbytes):
+    """Mean / p50 / p99 of per-step times (ms) and the throughput of the mean."""
+    a = np.array(ms_list)
+    return {"mean_ms": float(a.mean()), "p50_ms": float(np.percentile(a, 50)),
+            "p99_ms": float(np.percentile(a, 99)), "gbs": nbytes / (a.mean() * 1e-3) / 1e9}
+
+
 def run_batched(args):
-    """Config 4: per time step, every trajectory's frame in one batched
-    compress call and one batched decompress call (lanes = contexts with their
-    own streams), against one frame per call."""
+    """Config 4: per time step, every trajectory's frame compressed in one
+    batched call (lanes = contexts with their own streams) and decoded in one
+    fused step (lcp_decompress_step: the LCP-T frames in one persistent launch
+    replayed as a CUDA graph); timed beside the same containers decoded by the
+    lanes, and beside one frame per call for both directions."""
     import torch
     import torch.distributed as dist
 
@@ -490,45 +502,64 @@ def run_batched(args):
         for p in pos:
             p.add_(torch.randn(p.shape, generator=gen, device=dev, dtype=torch.float64) * 0.02)
 
-    launches0 = lcp.kernel_launches()
-    t_step, t_c, t_d, csize, nT = [], [], [], 0, 0
+    # the same time steps one frame per call on one context, for comparison
+    seq_ctx = lcp.Context(local)
+    seq_enc = [lcp.Trajectory(seq_ctx, batch=w["batch"], p=w["p"]) for _ in sizes]
+    seq_dec = [lcp.Trajectory(seq_ctx, batch=w["batch"], p=w["p"]) for _ in sizes]
+    seq_outs = [torch.empty_like(o) for o in outs]
+    # and decoded through the fused time-step decoder and through the lanes
+    step_dec = lcp.Step(lcp.Context(local), max_frames=T, lanes=lanes)  # lanes: S frames
+    lane_dec = [lcp.Trajectory(lanes.ctxs[0], batch=w["batch"], p=w["p"]) for _ in sizes]
+    lane_Ys = [torch.empty_like(y) for y in Ys]
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize(dev)
+        return r, (time.perf_counter() - t0) * 1e3
+
+    launches = 0
+    t_step, t_c, t_d, t_dl, t_cs, t_ds, csize, nT = [], [], [], [], [], [], 0, 0
     with ClockSampler(local) as clk:
         for step in range(steps_total):
             Xs = frames()
             torch.cuda.synchronize(dev)
             if world > 1:
                 dist.barrier()
-            t0 = time.perf_counter()
-            res = lanes.compress([dict(X=Xs[k], eb=w["eb"], mode=w["mode"], p=w["p"],
-                                       method="auto", traj=enc[k], out=outs[k])
-                                  for k in range(T)])
-            t1 = time.perf_counter()
-            lanes.decompress([dict(buf=outs[k], size=res[k]["size"], traj=decs[k], out=Ys[k])
-                              for k in range(T)])
-            torch.cuda.synchronize(dev)
-            t2 = time.perf_counter()
+            l0 = lcp.kernel_launches()
+            # the batched round trip: every frame of the time step compressed
+            # in one call, then decoded in one fused step
+            res, tc = timed(lambda: lanes.compress(
+                [dict(X=Xs[k], eb=w["eb"], mode=w["mode"], p=w["p"], method="auto",
+                      traj=enc[k], out=outs[k]) for k in range(T)]))
+            dres, td = timed(lambda: step_dec.decompress(
+                [dict(buf=outs[k], size=res[k]["size"], traj=decs[k], out=Ys[k])
+                 for k in range(T)]))
+            l1 = lcp.kernel_launches()
+            # the same containers decoded by the lanes
+            _, tdl = timed(lambda: lanes.decompress(
+                [dict(buf=outs[k], size=res[k]["size"], traj=lane_dec[k], out=lane_Ys[k])
+                 for k in range(T)]))
+            # one frame per call: compress, then decompress
+            sres, tcs = timed(lambda: [seq_ctx.compress(Xs[k], w["eb"], w["mode"], w["p"],
+                                                        method="auto", traj=seq_enc[k],
+                                                        out=seq_outs[k]) for k in range(T)])
+            _, tds = timed(lambda: [seq_ctx.decompress(seq_outs[k], sres[k]["size"],
+                                                       traj=seq_dec[k], out=lane_Ys[k])
+                                    for k in range(T)])
             if step >= args.warmup:
-                t_step.append((t2 - t0) * 1e3)
-                t_c.append((t1 - t0) * 1e3)
-                t_d.append((t2 - t1) * 1e3)
+                launches += l1 - l0
+                t_step.append(tc + td)
+                t_c.append(tc)
+                t_d.append(td)
+                t_dl.append(tdl)
+                t_cs.append(tcs)
+                t_ds.append(tds)
                 csize += sum(r["size"] for r in res)
                 nT += sum(1 for r in res if r["method"] == "temporal")
             advance()
-    launches = lcp.kernel_launches() - launches0
-    # the same frames one per call on one context (fresh trajectories, a few steps)
-    seq_ctx = lcp.Context(local)
-    seq_tr = [lcp.Trajectory(seq_ctx, batch=w["batch"], p=w["p"]) for _ in sizes]
-    seq_ms = []
-    for step in range(min(5, args.steps)):
-        Xs = frames()
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for k in range(T):
-            seq_ctx.compress(Xs[k], w["eb"], w["mode"], w["p"], method="auto", traj=seq_tr[k],
-                             out=outs[k])
-        torch.cuda.synchronize(dev)
-        seq_ms.append((time.perf_counter() - t0) * 1e3)
-        advance()
+    step_dec.close()
     ms, units = ranks_aggregate(statistics.mean(t_step), float(raw), world, dev)
     value = units / (ms * 1e-3) / 1e9
     pct = lambda v, q: float(np.percentile(np.array(v), q))
@@ -560,7 +591,15 @@ def run_batched(args):
             "p50_ms": pct(t_step, 50), "p99_ms": pct(t_step, 99),
             "compress_p50_ms": pct(t_c, 50), "compress_p99_ms": pct(t_c, 99),
             "decompress_p50_ms": pct(t_d, 50), "decompress_p99_ms": pct(t_d, 99),
-            "one_frame_per_call_compress_ms": statistics.mean(seq_ms),
+            "decompress_path": "lcp_decompress_step (LCP-T frames fused, graph replay; "
+                               "LCP-S frames over the lanes)",
+            "per_path": {
+                "compress_batched": summary(t_c, raw),
+                "compress_one_frame_per_call": summary(t_cs, raw),
+                "decompress_step_fused": summary(t_d, raw),
+                "decompress_lanes": summary(t_dl, raw),
+                "decompress_one_frame_per_call": summary(t_ds, raw),
+            },
             "ratio": raw * len(t_step) / max(csize, 1),
             "temporal_frames_fraction": nT / (T * len(t_step)),
             "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
@@ -646,7 +685,7 @@ def run_serving(args):
             P = prods[int(k)]
             with lock:
                 backlog = len(pending)
-            measured = a >= w["warm_seconds"]  # counters cover the measured window
+            measured = int(a >= w["warm_seconds"])  # counters cover the measured window
             if backlog >= max_pending:
                 shed += measured
                 continue
@@ -743,7 +782,7 @@ def run_serving(args):
         "achieved_rate_req_s": n_all / (span_ms * 1e-3), "requests_done": int(n_all),
         "offered": int(offered_all), "rejected_by_budget": int(rejected_all),
         "shed": int(shed_all), "failed": int(failed_all), "failed_by_status": failed,
-        "refused_not_decodable": not_decodable,
+        "refused_not_decodable": int(not_decodable),
         "ratio": comp_raw / max(comp_bytes, 1), "server_device_gb": mem / 1e9,
         "wall_s": wall, "e2e": None, "gpu_launches": launches, "clocks": clk.summary(),
         "cpu_baseline": None,
@@ -766,6 +805,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default schedule, no autotuning")
+    ap.add_argument("--schedule", default="", help="LOG2_CHUNK,BUCKET_DELTA instead of tuning")
     ap.add_argument("--n", type=int, default=0, help="override the particle count (small cases)")
     ap.add_argument("--seconds", type=float, default=0.0, help="serving: measured seconds")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: offered requests/s")
@@ -810,8 +850,12 @@ def main():
     # schedule autotuner (chunk size within 1% of the default's bytes, sort
     # partition width), once per frame shape, untimed
     sched = {"log2_chunk": 10, "bucket_delta": 0, "tuned": False}
-    if not args.no_tune:
-        sched = dict(ctx.tune(Xd, w["eb"], w["mode"], p, max_growth=0.01), tuned=True)
+    if args.schedule:  # given explicitly (e.g. to profile the tuned configuration)
+        lc, bd = (int(v) for v in args.schedule.split(","))
+        sched = {"log2_chunk": lc, "bucket_delta": bd, "tuned": False}
+        ctx.set_schedule(lc, bd)
+    elif not args.no_tune:
+        sched = dict(ctx.tune(Xd, w["eb"], w["mode"], p, max_growth=0.01, reps=5), tuned=True)
         ctx.set_schedule(sched["log2_chunk"], sched["bucket_delta"])
     stream = torch.cuda.current_stream(dev)
 
@@ -831,9 +875,9 @@ def main():
     K = int(np.frombuffer(hdr[24:32], np.uint64)[0])
     M = int(np.frombuffer(hdr[32:40], np.uint64)[0])
 
-    # timed region: compress and decompress timed separately with events
-    ctx.profile(True)
-    prof = []
+    # timed region: compress and decompress timed separately with events; the
+    # library's stage events accumulate and are read after the region
+    ctx.profile(True, accumulate=True)
     tc, td = [], []
     launches0 = lcp.kernel_launches()
     if world > 1:
@@ -848,10 +892,8 @@ def main():
             e0.record(stream)
             r = ctx.compress(Xd, w["eb"], w["mode"], p=p, out=out)
             e1.record(stream)
-            prof.extend(ctx.profile_read())
             ctx.decompress(r["bytes"], r["size"], out=Y)
             e2.record(stream)
-            prof.extend(ctx.profile_read())
             e2.synchronize()
             tc.append(e0.elapsed_time(e1))
             td.append(e1.elapsed_time(e2))
@@ -860,6 +902,7 @@ def main():
         if world > 1:
             dist.barrier()
     launches = lcp.kernel_launches() - launches0
+    prof = ctx.profile_read(4096)
     ctx.profile(False)
     total_ms, units = ranks_aggregate(t_start.elapsed_time(t_end), float(raw), world, dev)
     ms_step = total_ms / args.steps

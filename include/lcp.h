@@ -197,10 +197,11 @@ LCP_API lcp_status lcp_ctx_get_schedule(const lcp_ctx *ctx, lcp_schedule *out);
  * (compress then decompress) of d_fields at bound eb and block multiplier p
  * (0: the exact block-size search first, Sec. "Best block size"), for
  * log2_chunk in {8, 9, 10} and bucket_delta in {-2, -1, 0, 1}, each timed
- * with CUDA events over `reps` round trips after one untimed.  The fastest
- * schedule whose container is at most (1 + max_growth) times the default
- * schedule's size is returned in *best (and its mean round-trip ms in
- * *best_ms, optional); the context's own schedule is left as it was.
+ * with CUDA events over `reps` round trips after one untimed; a candidate's
+ * time is its fastest round (the least disturbed).  The fastest schedule
+ * whose container is at most (1 + max_growth) times the default schedule's
+ * size is returned in *best (and that round-trip ms in *best_ms, optional);
+ * the context's own schedule is left as it was.
  * Allocates a worst-case container and an [d][n] output buffer for the
  * duration of the call (stream-ordered).  Synchronizes `stream`.
  */
@@ -347,10 +348,42 @@ typedef struct {
   float ms;               /* out */
 } lcp_decompress_job;
 
+/*
+ * One time step of many trajectories (config 4; Algorithm 1 per trajectory)
+ * decoded together.  Every LCP-T job whose reference is on its own grid is
+ * planned on the device (one CTA per frame reads its header and stream
+ * section, builds its field plans and Huffman tables) and decoded by one
+ * persistent kernel over the chunks of all these frames, each symbol
+ * finished on the spot (code, range check, Eq. quantization reversed); the
+ * step's device work is recorded once as a CUDA graph on the step's own
+ * stream and replayed there, ordered after the work already queued on
+ * `stream` and before anything queued on it later.  Other jobs (LCP-S frames, references
+ * re-quantized from a scaled anchor, a second frame of one trajectory) are
+ * decoded one by one after the fused ones, in job order.
+ *   - A job's traj is its trajectory's decoder state (as for
+ *     lcp_decompress); each job's status, n_out and d_fields are set; the
+ *     call returns LCP_OK when every job succeeded, else LCP_ERR_STATE.
+ *   - One host synchronization for the headers, one after the graph.
+ *   - A step serves at most max_frames fused frames per call (<= 256).
+ *   - A step object is not thread-safe (one caller at a time).
+ *   - lcp_step_set_lanes gives the step lanes (contexts and streams, as for
+ *     lcp_decompress_batch; the arrays are copied, the contexts must outlive
+ *     the step and be used by nothing else during its calls): the frames it
+ *     does not fuse are then spread over them, unless a trajectory comes
+ *     twice among those frames (then one at a time).  0 lanes: none.
+ */
+typedef struct lcp_step lcp_step;
+LCP_API lcp_status lcp_step_create(lcp_ctx *ctx, int max_frames, lcp_step **out);
+LCP_API lcp_status lcp_step_destroy(lcp_step *step);
+LCP_API lcp_status lcp_step_set_lanes(lcp_step *step, lcp_ctx *const *ctxs,
+                                      void *const *streams, int lanes);
+
 LCP_API lcp_status lcp_compress_batch(lcp_ctx *const *ctxs, void *const *streams, int lanes,
                                       lcp_compress_job *jobs, int njobs);
 LCP_API lcp_status lcp_decompress_batch(lcp_ctx *const *ctxs, void *const *streams, int lanes,
                                         lcp_decompress_job *jobs, int njobs);
+LCP_API lcp_status lcp_decompress_step(lcp_step *step, lcp_decompress_job *jobs, int njobs,
+                                       void *stream);
 
 /*
  * Serving: a request loop around the codec.  Producers submit requests as
@@ -420,10 +453,15 @@ LCP_API lcp_status lcp_server_destroy(lcp_server *srv);
 /*
  * Per-kernel timing (tracing).  With profiling on, every entry point records
  * a CUDA event pair on its stream around each major kernel (stage names such
- * as "s.quantize", "s.local_sort", "d.expand").  lcp_ctx_profile_read returns
- * the number of stages of the most recent call (at most cap), their names in
- * names[32 * k] (NUL-terminated) and durations in ms[k]; it waits for those
- * events.  The paper has no counterpart: this is measurement plumbing.
+ * as "s.quantize", "s.local_sort", "d.expand").
+ *   - enable 1: each call's stages replace the previous call's (up to 32).
+ *   - enable 2: stages accumulate over calls (up to 4096) until read, so a
+ *     timed loop needs no read between its calls; the read empties the list.
+ *   - enable 0: off.  Enabling makes the events (outside any timed region).
+ * lcp_ctx_profile_read returns the number of stages listed (at most cap),
+ * their names in names[32 * k] (NUL-terminated) and durations in ms[k]; it
+ * waits for those events.  The paper has no counterpart: this is measurement
+ * plumbing.
  */
 LCP_API lcp_status lcp_ctx_profile(lcp_ctx *ctx, int enable);
 /* Description of the last failed CUDA runtime call on this thread (empty if

@@ -84,38 +84,42 @@ __global__ void __launch_bounds__(kCbThreads) k_cb_build(const uint32_t *__restr
   if (threadIdx.x == 0) {
     // leaves nodew[0..U) ascending; internal node j (id U + j) has weight
     // nodew[U + j], created in non-decreasing order.  Branch-free picks: the
-    // next four leaves and three internal nodes are kept in registers, the
-    // refills loaded unconditionally (clamped in range) and selected.  An
-    // internal entry not yet created is filled in when its node is made.
+    // next four leaves and three internal nodes are kept in registers; the
+    // refill of each window is loaded right after a pick (clamped in range)
+    // and used at the next one, so its latency overlaps that pick.  An
+    // internal entry not yet created when it is loaded is filled in when its
+    // node is made.
     const uint32_t *lw = nodew;
     uint32_t *iw = nodew + U;
     int nl = 0, ni = 0;
     uint32_t L0 = lw[0], L1 = lw[1], L2 = lw[min(2, U - 1)], L3 = lw[min(3, U - 1)];
     uint32_t I0 = 0u, I1 = 0u, I2 = 0u;
+    uint32_t pL = lw[min(4, U - 1)], pI = 0u;  // lw[nl + 4], iw[ni + 3]
     for (int nn = 0; nn < U - 1; ++nn) {
       uint32_t sum = 0u;
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        const uint32_t nextL = lw[min(nl + 4, U - 1)];
-        const uint32_t nextI = iw[min(ni + 3, U - 2)];
         const bool leaf = nl < U && (ni == nn || L0 <= I0);
         sum += leaf ? L0 : I0;
         parent[leaf ? nl : U + ni] = (uint16_t)(U + nn);
         L0 = leaf ? L1 : L0;
         L1 = leaf ? L2 : L1;
         L2 = leaf ? L3 : L2;
-        L3 = leaf ? nextL : L3;
+        L3 = leaf ? pL : L3;
         I0 = leaf ? I0 : I1;
         I1 = leaf ? I1 : I2;
-        I2 = leaf ? I2 : nextI;
+        I2 = leaf ? I2 : pI;
         nl += leaf ? 1 : 0;
         ni += leaf ? 0 : 1;
+        pL = lw[min(nl + 4, U - 1)];
+        pI = iw[min(ni + 3, U - 2)];
       }
       iw[nn] = sum;
       const int q = nn - ni;  // queue length before this node joins
       I0 = q == 0 ? sum : I0;
       I1 = q == 1 ? sum : I1;
       I2 = q == 2 ? sum : I2;
+      pI = q == 3 ? sum : pI;  // loaded before this store
     }
     parent[2 * U - 2] = (uint16_t)(2 * U - 2);
   }
@@ -448,8 +452,11 @@ void launch_layout(const LayoutArgs &a, int sms, bool size_only, cudaStream_t s)
 }
 
 // ---------------------------------------------------------------------------
-// fixed-length payload: a warp packs 32 consecutive values (32 * w bits, w
-// whole words) in shared memory and writes the w words out
+// fixed-length payload, groups of 32 consecutive values (32 * w bits, w whole
+// words).  Widths up to 32: lane k assembles word k of the group from the
+// values it overlaps, fetched by shuffles, and the w words go out in one
+// coalesced store.  Wider values (8-byte streams): the lanes OR their bits
+// into a shared-memory stage.
 // ---------------------------------------------------------------------------
 constexpr int kFixWarps = 8;
 constexpr int kFixGroups = 4;  // groups per warp iteration (their loads issued together)
@@ -469,6 +476,12 @@ __global__ void __launch_bounds__(32 * kFixWarps) k_encode_fixed(
   const unsigned long long words = words_of(D.payload_bits);
   const unsigned long long groups = (D.n + 31) >> 5;
   const unsigned long long nw = (unsigned long long)gridDim.x * kFixWarps;
+  // word `lane` of a group spans bits [32 lane, 32 lane + 32): values
+  // i_lo = floor(32 lane / w) onwards, value i shifted left by
+  // 32 lane + 64 - (i + 1) w within a 64-bit accumulator whose high word is
+  // the output (bits of neighbouring words fall off either end)
+  const uint32_t i_lo = w <= 32u ? (32u * (uint32_t)lane) / w : 0u;
+  const int nj = w <= 32u ? (int)((32u + w - 1u) / w) + 1 : 0;  // values a word can touch
   for (unsigned long long g0 = ((unsigned long long)blockIdx.x * kFixWarps + wl) * kFixGroups;
        g0 < groups; g0 += nw * kFixGroups) {
     unsigned long long v[kFixGroups];
@@ -481,35 +494,48 @@ __global__ void __launch_bounds__(32 * kFixWarps) k_encode_fixed(
     for (int q = 0; q < kFixGroups; ++q) {
       const unsigned long long g = g0 + q;
       if (g >= groups) break;
-      buf[lane] = 0u;
-      buf[lane + 32] = 0u;
-      __syncwarp();
-      const unsigned long long i = g * 32ull + lane;
-      if (i < D.n) {
-        // bits [lane*w, lane*w + w) of the group, MSB first
-        uint32_t left = w, pos = (uint32_t)lane * w;
-        while (left) {
-          const uint32_t wi = pos >> 5, off = pos & 31u;
-          const uint32_t take = min(left, 32u - off);
-          const unsigned long long part = (v[q] >> (left - take)) & ((1ull << take) - 1ull);
-          atomicOr(&buf[wi], (uint32_t)part << (32u - off - take));
-          pos += take;
-          left -= take;
-        }
-      }
-      __syncwarp();
       const unsigned long long wbase = g * (unsigned long long)w;
-      for (uint32_t k = lane; k < w; k += 32)
-        if (wbase + k < words) pl[wbase + k] = buf[k];
-      __syncwarp();
+      if (w <= 32u) {
+        const uint32_t x32 = (uint32_t)v[q];
+        unsigned long long acc = 0ull;
+        for (int j = 0; j < nj; ++j) {
+          const uint32_t i = i_lo + (uint32_t)j;
+          const uint32_t x = __shfl_sync(0xffffffffu, x32, (int)(i & 31u));
+          const int sh = 32 * lane + 64 - (int)((i + 1u) * w);
+          if (i < 32u && (int)(i * w) < 32 * lane + 32 && sh < 64)
+            acc |= (unsigned long long)x << sh;
+        }
+        if ((uint32_t)lane < w && wbase + lane < words) pl[wbase + lane] = (uint32_t)(acc >> 32);
+      } else {
+        buf[lane] = 0u;
+        buf[lane + 32] = 0u;
+        __syncwarp();
+        const unsigned long long i = g * 32ull + lane;
+        if (i < D.n) {
+          // bits [lane*w, lane*w + w) of the group, MSB first
+          uint32_t left = w, pos = (uint32_t)lane * w;
+          while (left) {
+            const uint32_t wi = pos >> 5, off = pos & 31u;
+            const uint32_t take = min(left, 32u - off);
+            const unsigned long long part = (v[q] >> (left - take)) & ((1ull << take) - 1ull);
+            atomicOr(&buf[wi], (uint32_t)part << (32u - off - take));
+            pos += take;
+            left -= take;
+          }
+        }
+        __syncwarp();
+        for (uint32_t k = lane; k < w; k += 32)
+          if (wbase + k < words) pl[wbase + k] = buf[k];
+        __syncwarp();
+      }
     }
   }
 }
 
 // ---------------------------------------------------------------------------
 // Huffman payload: per-chunk bit counts, their scan (the chunk table), then
-// one warp per chunk: rounds of 32 consecutive symbols (one per lane), bit
-// positions from a warp scan, codes assembled in a shared-memory stage
+// one warp per chunk, each lane a run of consecutive symbols, the chunk's
+// words assembled in a shared-memory stage
 // ---------------------------------------------------------------------------
 constexpr int kEncWarps = 8;
 constexpr int kStageWords = 2848;  // >= (1024 * (24 + 64)) / 32 + 2
@@ -574,16 +600,47 @@ __global__ void k_chunk_table(const unsigned long long *__restrict__ chunk_off,
     st_u64(ct + 8 * c, chunk_off[c]);
 }
 
-// ORs nbits (<= 64) of v, MSB first, at bit position pos of a u32 word array
-__device__ __forceinline__ void put_bits_smem(uint32_t *buf, uint32_t pos, unsigned long long v,
-                                              uint32_t nbits) {
-  while (nbits) {
-    const uint32_t wi = pos >> 5, off = pos & 31u;
-    const uint32_t take = min(nbits, 32u - off);
-    const uint32_t part = (uint32_t)((v >> (nbits - take)) & ((1ull << take) - 1ull));
-    atomicOr(&buf[wi], part << (32u - off - take));
-    pos += take;
-    nbits -= take;
+// Rounds of 128 consecutive symbols of the chunk, four per lane (loaded
+// together, so a warp's loads stay contiguous): the lane's bit count, a warp
+// scan for its start, then its codes shifted through a 64-bit accumulator
+// whose full words go to the warp's stage.  A lane's first and last words
+// may be shared with its neighbours and are ORed in; the words between are
+// the lane's alone.
+constexpr int kEncPer = 4;
+
+template <typename T>
+__device__ __forceinline__ void enc_load4(const T *vals, unsigned long long i,
+                                          unsigned long long hi, unsigned long long (&v)[kEncPer]);
+template <>
+__device__ __forceinline__ void enc_load4<unsigned long long>(const unsigned long long *vals,
+                                                              unsigned long long i,
+                                                              unsigned long long hi,
+                                                              unsigned long long (&v)[kEncPer]) {
+  if (i + kEncPer <= hi) {
+    const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(vals + i);
+    const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(vals + i + 2);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+  } else {
+#pragma unroll
+    for (int j = 0; j < kEncPer; ++j) v[j] = i + j < hi ? vals[i + j] : 0ull;
+  }
+}
+template <>
+__device__ __forceinline__ void enc_load4<uint32_t>(const uint32_t *vals, unsigned long long i,
+                                                    unsigned long long hi,
+                                                    unsigned long long (&v)[kEncPer]) {
+  if (i + kEncPer <= hi) {
+    const uint4 a = *reinterpret_cast<const uint4 *>(vals + i);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+  } else {
+#pragma unroll
+    for (int j = 0; j < kEncPer; ++j) v[j] = i + j < hi ? vals[i + j] : 0ull;
   }
 }
 
@@ -602,6 +659,7 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_huff_encode(
   __syncthreads();
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const unsigned long long cs = 1ull << log2_chunk;
+  const uint32_t width = D.width;
   uint32_t *buf = enc_smem + (size_t)wl * kStageWords;
   uint32_t *pl = reinterpret_cast<uint32_t *>(out + D.offset + pad16(80ull + 2ull * D.used) +
                                               pad16(8ull * D.n_chunks));
@@ -618,37 +676,75 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_huff_encode(
     for (uint32_t i = lane; i < nwords; i += 32) buf[i] = 0u;
     __syncwarp();
     uint32_t base = (uint32_t)(start & 31ull);  // bit position relative to word w0
-    for (unsigned long long b0 = lo; b0 < hi; b0 += 32 * 8) {
-      unsigned long long vv[8];
+    for (unsigned long long b0 = lo; b0 < hi; b0 += 32 * kEncPer) {
+      const unsigned long long i0 = b0 + (unsigned long long)lane * kEncPer;
+      unsigned long long v[kEncPer];
+      enc_load4<T>(vals, i0, hi, v);
+      uint32_t e[kEncPer], bits = 0u, em = 0u;  // em: escapes with raw bits
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const unsigned long long i = b0 + 32ull * q + lane;
-        vv[q] = i < hi ? (unsigned long long)vals[i] : 0ull;
+      for (int j = 0; j < kEncPer; ++j) {
+        const bool on = i0 + j < hi;
+        const uint32_t sym = v[j] < (unsigned long long)kEsc ? (uint32_t)v[j] : (uint32_t)kEsc;
+        e[j] = on ? tab[sym] : 0u;
+        const bool esc = on && sym == (uint32_t)kEsc && width;
+        em |= esc ? (1u << j) : 0u;
+        bits += (e[j] & 31u) + (esc ? width : 0u);
       }
+      uint32_t x = bits;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const unsigned long long r0 = b0 + 32ull * q;
-        if (r0 >= hi) break;
-        const unsigned long long i = r0 + lane;
-        const unsigned long long v = vv[q];
-        uint32_t sym = 0u, L = 0u, nb = 0u;
-        if (i < hi) {
-          sym = v < (unsigned long long)kEsc ? (uint32_t)v : (uint32_t)kEsc;
-          L = tab[sym] & 31u;
-          nb = L + (sym == kEsc ? D.width : 0u);
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      const uint32_t pos0 = base + x - bits;
+      base += __shfl_sync(0xffffffffu, x, 31);
+      if (bits == 0u) continue;
+      uint32_t wp = pos0 >> 5, nacc = pos0 & 31u;  // next word; bits held (the
+      unsigned long long acc = 0ull;                 // first nacc are a neighbour's)
+      bool first = true;
+      auto emit = [&](uint32_t word) {
+        if (first) {
+          if (word) atomicOr(&buf[wp], word);
+          first = false;
+        } else {
+          buf[wp] = word;
         }
-        uint32_t x = nb;
+        ++wp;
+      };
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-          if (lane >= o) x += y;
+      for (int j = 0; j < kEncPer; ++j) {
+        const uint32_t L = e[j] & 31u;
+        acc = (acc << L) | (unsigned long long)(e[j] >> 5);
+        nacc += L;  // < 56
+        if (nacc >= 32u) {
+          nacc -= 32u;
+          emit((uint32_t)(acc >> nacc));
         }
-        const uint32_t pos = base + x - nb;
-        if (nb) {
-          put_bits_smem(buf, pos, tab[sym] >> 5, L);
-          if (sym == kEsc) put_bits_smem(buf, pos + L, v, D.width);
+        if ((em >> j) & 1u) {
+          const unsigned long long w = v[j];  // the raw value, MSB first
+          if (width > 32u) {
+            const uint32_t hw = width - 32u;
+            acc = (acc << hw) | ((w >> 32) & ((1ull << hw) - 1ull));
+            nacc += hw;
+            if (nacc >= 32u) {
+              nacc -= 32u;
+              emit((uint32_t)(acc >> nacc));
+            }
+            acc = (acc << 32) | (w & 0xffffffffull);
+            nacc += 32u;
+          } else {
+            acc = (acc << width) | (w & ((1ull << width) - 1ull));
+            nacc += width;
+          }
+          if (nacc >= 32u) {
+            nacc -= 32u;
+            emit((uint32_t)(acc >> nacc));
+          }
         }
-        base += __shfl_sync(0xffffffffu, x, 31);
+      }
+      if (nacc) {  // the last partial word, shared with the next lane
+        const uint32_t word = (uint32_t)(acc << (32u - nacc));
+        if (word) atomicOr(&buf[wp], word);
       }
     }
     __syncwarp();

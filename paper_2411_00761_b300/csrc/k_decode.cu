@@ -20,7 +20,7 @@ __global__ void k_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan) {
     FieldPlan F;
     int st = plan_field(df->m[f], df->m[f], (double)df->e[f], 0, df->lp, F);
     F.qmax = df->qmax[f];
-    F.bn = ((unsigned long long)df->qmax[f] >> df->lp) + 1ull;
+    field_block_grid(F, df->lp);
     plan->f[f] = F;
     if (st != OK) atomicCAS(&plan->status, OK, ERR_FORMAT);
   }
@@ -35,31 +35,6 @@ __global__ void k_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan) {
     for (uint32_t k = 0; k < d; ++k) {
       plan->f[k].stride = stride;
       stride *= plan->f[k].bn;
-    }
-  }
-  if (f < (int)d) {
-    // floor(r / bn) for r < 2^63: m = ceil(2^(63+l) / bn), l = ceil(log2 bn), then
-    // floor(r m / 2^(63+l)) = floor(r / bn) (Granlund-Montgomery, division by
-    // invariant integers using multiplication, Thm. 4.2)
-    const unsigned long long bn = plan->f[f].bn;
-    if (bn <= 1) {
-      plan->f[f].bmagic = 0;
-      plan->f[f].bshift = 255;
-    } else {
-      uint32_t l = 0;
-      while ((1ull << l) < bn) ++l;
-      // binary long division of 2^(63+l) by bn; the quotient fits 64 bits
-      unsigned long long q = 0, rem = 0;
-      for (int bit = 63 + (int)l; bit >= 0; --bit) {
-        rem = (rem << 1) | (bit == 63 + (int)l ? 1ull : 0ull);
-        q <<= 1;
-        if (rem >= bn) {
-          rem -= bn;
-          q |= 1ull;
-        }
-      }
-      plan->f[f].bmagic = q + (rem != 0 ? 1ull : 0ull);
-      plan->f[f].bshift = l - 1;
     }
   }
 }
@@ -96,19 +71,9 @@ __global__ void k_huff_table(const uint8_t *__restrict__ sec, HuffTable *__restr
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < U && i < (uint32_t)kAlpha; i += blockDim.x)
     T->syms[i] = (uint16_t)((uint32_t)sec[80 + 2 * i] | ((uint32_t)sec[81 + 2 * i] << 8));
-  // first-level table: codes of up to kFastBits bits, entry = sym << 5 | len
-  for (uint32_t e = threadIdx.x; e < (1u << kFastBits); e += blockDim.x) T->fast[e] = 0u;
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < U && i < (uint32_t)kAlpha; i += blockDim.x) {
-    // length of the i-th symbol in canonical order
-    int L = 1;
-    while (L < kLmax && i >= index[L] + cnt[L]) ++L;
-    if (L > kFastBits) continue;
-    uint32_t code = first[L] + (i - index[L]);
-    uint32_t sym = (uint32_t)sec[80 + 2 * i] | ((uint32_t)sec[81 + 2 * i] << 8);
-    uint32_t lo = code << (kFastBits - L), hi = (code + 1) << (kFastBits - L);
-    for (uint32_t e = lo; e < hi && e < (1u << kFastBits); ++e) T->fast[e] = (sym << 5) | (uint32_t)L;
-  }
+  // first-level table: codes of up to kFastBits bits, entry = sym << 5 | len
+  huff_fill_fast(first, cnt, index, T->syms, min(U, (uint32_t)kAlpha), T->fast);
 }
 
 void launch_huff_table(const uint8_t *sec, HuffTable *T, cudaStream_t s) {
@@ -168,21 +133,6 @@ struct HuffJobs {
 constexpr int kRing = kRingWords;
 static_assert(kDecR * (kLmax + 64) <= 32 * (kRing / 2 - 2), "ring covers two rounds");
 
-__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src, bool valid) {
-  const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
-  const int n = valid ? 4 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sdst), "l"(src), "r"(n)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait1() {
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait0() {
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
 
 // WIDE: 8-byte values (streams whose largest value needs them); otherwise
 // 4-byte values, and escapes are at most 32 bits wide.  A round's kDecR
@@ -262,6 +212,7 @@ __global__ void __launch_bounds__(32 * kDecWarps) k_huff_decode(HuffJobs jobs,
     return __funnelshift_l(y, x, b & 31);
   };
   const uint32_t width = info.width;
+  const uint32_t esc_shift = (width && width <= 32u) ? 32u - width : 0u;
   const int amode = J.agg_mode;
   bool bad = act && !ok;
   unsigned long long s1 = 0ull, s2 = 0ull;  // aggregate sums (a; or b and p)
@@ -277,50 +228,85 @@ __global__ void __launch_bounds__(32 * kDecWarps) k_huff_decode(HuffJobs jobs,
     cp_async_wait1();
     const uint32_t todo = min(mine - r0, (uint32_t)kDecR);
     V v[kDecR];
+    if (!WIDE && todo == (uint32_t)kDecR) {
+      // a full round of 4-byte values: one 64-bit window per symbol (three
+      // ring words) gives the code and the escape bits after it
 #pragma unroll
-    for (uint32_t k = 0; k < (uint32_t)kDecR; ++k) {
-      const bool on = k < todo;
-      const uint32_t win = peek32(bp);
-      const uint32_t e = fast[win >> (32 - kFastBits)];
-      uint32_t sym = e >> 4;
-      uint32_t len = e & 15u;
-      const bool longc = on && e == 0u;
-      if (__any_sync(__activemask(), longc)) {
-        if (longc) {  // a code longer than the first-level table
-          int L = kFastBits + 1;
-          while (L <= kLmax && (unsigned long long)win >= lim[L]) ++L;
-          if (L > kLmax) {
-            bad = true;
-            sym = 0;
-            len = 1;
-          } else {
-            sym = syms[index[L] + ((win >> (32 - L)) - first[L])];
-            len = (uint32_t)L;
-          }
-        }
-      }
-      // the raw bits after an escape code, read by every lane (off the
-      // dependency chain of the bit position: no branch on the escape)
-      const bool esc = on && sym == (uint32_t)kEsc && width > 0;
-      const uint32_t hw = peek32(bp + len);
-      V x;
-      if (!WIDE) {
-        x = esc ? (hw >> (32u - width)) : sym;
-      } else {
-        x = sym;
-        if (__any_sync(__activemask(), esc)) {
-          if (esc) {
-            if (width <= 32) {
-              x = hw >> (32 - width);
+      for (int k = 0; k < kDecR; ++k) {
+        const uint32_t wi = bp >> 5, sh = bp & 31u;
+        const uint32_t a0 = myring[(wi & (kRing - 1)) * 32];
+        const uint32_t a1 = myring[((wi + 1) & (kRing - 1)) * 32];
+        const uint32_t a2 = myring[((wi + 2) & (kRing - 1)) * 32];
+        const uint32_t hi = __funnelshift_l(a1, a0, sh);  // bits [bp, bp + 32)
+        const uint32_t lo = __funnelshift_l(a2, a1, sh);  // bits [bp + 32, bp + 64)
+        const uint32_t e = fast[hi >> (32 - kFastBits)];
+        uint32_t sym = e >> 4;
+        uint32_t len = e & 15u;
+        if (__any_sync(__activemask(), e == 0u)) {
+          if (e == 0u) {  // a code longer than the first-level table
+            int L = kFastBits + 1;
+            while (L <= kLmax && (unsigned long long)hi >= lim[L]) ++L;
+            if (L > kLmax) {
+              bad = true;
+              sym = 0;
+              len = 1;
             } else {
-              const uint32_t lw = peek32(bp + len + 32);
-              x = (V)((((unsigned long long)hw << 32) | lw) >> (64 - width));
+              sym = syms[index[L] + ((hi >> (32 - L)) - first[L])];
+              len = (uint32_t)L;
             }
           }
         }
+        const uint32_t after = __funnelshift_l(lo, hi, len);  // bits [bp + len, +32)
+        const bool esc = sym == (uint32_t)kEsc && width > 0;
+        v[k] = esc ? (V)(after >> esc_shift) : (V)sym;
+        bp += len + (esc ? width : 0u);
       }
-      bp += on ? len + (esc ? width : 0u) : 0u;
-      v[k] = on ? x : (V)0;
+    } else {
+#pragma unroll
+      for (uint32_t k = 0; k < (uint32_t)kDecR; ++k) {
+        const bool on = k < todo;
+        const uint32_t win = peek32(bp);
+        const uint32_t e = fast[win >> (32 - kFastBits)];
+        uint32_t sym = e >> 4;
+        uint32_t len = e & 15u;
+        const bool longc = on && e == 0u;
+        if (__any_sync(__activemask(), longc)) {
+          if (longc) {  // a code longer than the first-level table
+            int L = kFastBits + 1;
+            while (L <= kLmax && (unsigned long long)win >= lim[L]) ++L;
+            if (L > kLmax) {
+              bad = true;
+              sym = 0;
+              len = 1;
+            } else {
+              sym = syms[index[L] + ((win >> (32 - L)) - first[L])];
+              len = (uint32_t)L;
+            }
+          }
+        }
+        // the raw bits after an escape code, read by every lane (off the
+        // dependency chain of the bit position: no branch on the escape)
+        const bool esc = on && sym == (uint32_t)kEsc && width > 0;
+        const uint32_t hw = peek32(bp + len);
+        V x;
+        if (!WIDE) {
+          x = esc ? (hw >> (32u - width)) : sym;
+        } else {
+          x = sym;
+          if (__any_sync(__activemask(), esc)) {
+            if (esc) {
+              if (width <= 32) {
+                x = hw >> (32 - width);
+              } else {
+                const uint32_t lw = peek32(bp + len + 32);
+                x = (V)((((unsigned long long)hw << 32) | lw) >> (64 - width));
+              }
+            }
+          }
+        }
+        bp += on ? len + (esc ? width : 0u) : 0u;
+        v[k] = on ? x : (V)0;
+      }
     }
     if (amode == 1) {
 #pragma unroll
@@ -972,7 +958,7 @@ constexpr int kFper = 8;                      // slots per thread
 constexpr int kFwin = kXThreads * kFper;      // slots per window
 constexpr int kFrel = kFwin + 4;              // staged words of a window (w <= 32)
 
-template <int D>
+template <int D, bool DIV32>
 __global__ void __launch_bounds__(kXThreads, 4) k_expand_fast(const ExpandArgs a) {
   constexpr int NP = (D + 1) / 2;  // field pairs
   extern __shared__ __align__(16) float s_lut[];
@@ -1082,6 +1068,8 @@ __global__ void __launch_bounds__(kXThreads, 4) k_expand_fast(const ExpandArgs a
         uint32_t q;
         if (a.bshift[f] == 255u) {
           q = r32;
+        } else if (DIV32) {  // below the first axis the block space is < 2^31
+          q = __umulhi(r32, a.bmagic32[f]) >> a.bshift[f];
         } else {
           const unsigned long long x = (unsigned long long)r32 * (uint32_t)a.bmagic[f];
           const unsigned long long y =
@@ -1318,21 +1306,21 @@ static void expand_t(const ExpandArgs &a, bool lut, int sms, cudaStream_t s) {
   kern<<<(unsigned)grid, kXThreads, dyn, s>>>(a);
 }
 
-template <int D>
+template <int D, bool DIV32>
 static void expand_fast_t(const ExpandArgs &a, int sms, cudaStream_t s) {
   const size_t dyn = sizeof(float) * (size_t)a.lut_off.off[D];
   static const bool attr =
-      cudaFuncSetAttribute(k_expand_fast<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(k_expand_fast<D, DIV32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)(sizeof(float) * kLutMax)) == cudaSuccess;
   (void)attr;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand_fast<D>, kXThreads, dyn) !=
-          cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_expand_fast<D, DIV32>, kXThreads,
+                                                    dyn) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   const uint64_t grid = std::min<uint64_t>(a.tiles, (uint64_t)sms * per_sm);
   note_launch();
-  k_expand_fast<D><<<(unsigned)grid, kXThreads, dyn, s>>>(a);
+  k_expand_fast<D, DIV32><<<(unsigned)grid, kXThreads, dyn, s>>>(a);
 }
 
 // floor(r / bn) for r < 2^63: m = ceil(2^(63+l) / bn), l = ceil(log2 bn), then
@@ -1363,6 +1351,11 @@ static void expand_d(ExpandArgs a, bool lut, int sms, cudaStream_t s) {
     fast = fast && (bn << a.lp) <= 65536ull;  // corner + digit never carries past 16 bits
     a.bn[f] = (uint32_t)bn;
     block_magic(bn, a.bmagic[f], a.bshift[f]);
+    a.bmagic32[f] = 0u;
+    if (bn > 1 && bn <= 65536ull) {  // ceil(2^(31 + l) / bn) < 2^32
+      const unsigned long long num = 1ull << (a.bshift[f] + 32u);  // l = bshift + 1
+      a.bmagic32[f] = (uint32_t)(num / bn + ((num % bn) != 0 ? 1ull : 0ull));
+    }
     space *= bn;
     if (f > 0) rest *= bn;
   }
@@ -1372,7 +1365,9 @@ static void expand_d(ExpandArgs a, bool lut, int sms, cudaStream_t s) {
   }
   a.div0_64 = space > ((unsigned __int128)1 << 32) ? 1 : 0;
   fast = fast && rest <= ((unsigned __int128)1 << 32);
-  if (fast) expand_fast_t<D>(a, sms, s);
+  const bool div32 = rest <= ((unsigned __int128)1 << 31);
+  if (fast && div32) expand_fast_t<D, true>(a, sms, s);
+  else if (fast) expand_fast_t<D, false>(a, sms, s);
   else if (c16) expand_t<D, true>(a, lut, sms, s);
   else expand_t<D, false>(a, lut, sms, s);
 }

@@ -289,7 +289,7 @@ __global__ void k_field_plan(float m, float e, float max_abs, FieldPlan *fp, int
   FieldPlan F;
   double ebf = (double)e;
   int st = plan_field(m, m, ebf, 0, 0, F);
-  (void)max_abs;  // bounds q on the host (q < 2^30); no rule on |x| here
+  (void)max_abs;  // unused: k_element_rules checks every q < 2^30; no rule on |x|
   *fp = F;
   *status = st;
 }

@@ -80,57 +80,55 @@ __global__ void k_bucket_colsum(const uint32_t *__restrict__ tile_hist, int tile
 }
 
 // exclusive scan of n values (one CTA); out[n] = total.  Tiles of
-// kScanTileS values: loaded coalesced (the next tile's loads issued before
-// the current one is scanned), four consecutive values per thread.
-constexpr int kScanTileS = 4096;
+// kScanTileS values, kScanPer consecutive values per thread read with 16-byte
+// loads (all of a tile's loads in flight at once), so a 2^17-value scan takes
+// eight tiles.
+constexpr int kScanPer = 16;
+constexpr int kScanTileS = 1024 * kScanPer;
 
 __global__ void __launch_bounds__(1024) k_scan_small(const unsigned long long *__restrict__ in,
                                                      uint32_t n,
                                                      unsigned long long *__restrict__ out,
                                                      const uint32_t *__restrict__ gate) {
-  __shared__ unsigned long long t[kScanTileS];
   __shared__ unsigned long long s_warp[32];
   if (gate && *gate != 1u) return;  // the stream this scan serves is not Huffman coded
-  constexpr int per = kScanTileS / 1024;
-  unsigned long long cur[per], nxt[per];
-#pragma unroll
-  for (int k = 0; k < per; ++k) {
-    const uint32_t i = threadIdx.x + 1024u * k;
-    cur[k] = i < n ? in[i] : 0ull;
-  }
+  const bool vec = ((((uintptr_t)in) | ((uintptr_t)out)) & 15u) == 0;
   unsigned long long carry = 0;
-  for (uint32_t base = 0; base < n; base += kScanTileS) {
+  for (uint64_t base = 0; base < n; base += kScanTileS) {
+    const uint64_t i0 = base + (uint64_t)threadIdx.x * kScanPer;
+    unsigned long long v[kScanPer];
+    if (vec && i0 + kScanPer <= n) {
 #pragma unroll
-    for (int k = 0; k < per; ++k) {
-      const uint32_t i = base + kScanTileS + threadIdx.x + 1024u * k;
-      nxt[k] = i < n ? in[i] : 0ull;
+      for (int j = 0; j < kScanPer; j += 2) {
+        const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(in + i0 + j);
+        v[j] = x.x;
+        v[j + 1] = x.y;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < kScanPer; ++j) v[j] = i0 + j < n ? in[i0 + j] : 0ull;
     }
+    unsigned long long sum = 0;
 #pragma unroll
-    for (int k = 0; k < per; ++k) t[threadIdx.x + 1024 * k] = cur[k];
-    __syncthreads();
-    unsigned long long v[per], sum = 0;
-#pragma unroll
-    for (int j = 0; j < per; ++j) {
-      v[j] = t[per * threadIdx.x + j];
-      sum += v[j];
-    }
+    for (int j = 0; j < kScanPer; ++j) sum += v[j];
     unsigned long long total;
     unsigned long long run = carry + block_exscan<1024>(sum, s_warp, total);
+    if (vec && i0 + kScanPer <= n) {
 #pragma unroll
-    for (int j = 0; j < per; ++j) {
-      t[per * threadIdx.x + j] = run;
-      run += v[j];
-    }
-    __syncthreads();
+      for (int j = 0; j < kScanPer; j += 2) {
+        const unsigned long long a = run;
+        run += v[j];
+        *reinterpret_cast<ulonglong2 *>(out + i0 + j) = make_ulonglong2(a, run);
+        run += v[j + 1];
+      }
+    } else {
 #pragma unroll
-    for (int k = 0; k < per; ++k) {
-      const uint32_t i = base + threadIdx.x + 1024u * k;
-      if (i < n) out[i] = t[threadIdx.x + 1024 * k];
+      for (int j = 0; j < kScanPer; ++j) {
+        if (i0 + j < n) out[i0 + j] = run;
+        run += v[j];
+      }
     }
     carry += total;
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < per; ++k) cur[k] = nxt[k];
   }
   if (threadIdx.x == 0) out[n] = carry;
 }

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <vector>
 
 #include "../../include/lcp.h"
@@ -118,13 +119,16 @@ void prof_begin(lcp_ctx *c, const char *name, cudaStream_t s);
 void prof_end(lcp_ctx *c, cudaStream_t s);
 }  // namespace
 
-// per-kernel timing of the last call (events recorded on the call's stream)
+// per-kernel timing (events recorded on the call's stream): of the last
+// call, or accumulated over calls until read (lcp_ctx_profile mode 2)
+constexpr int kProfCall = 32;     // stages kept per call
+constexpr int kProfAccum = 4096;  // stages kept while accumulating
 struct Profile {
-  bool on = false;
+  bool on = false, accumulate = false;
   int n = 0;
-  char names[32][32];
-  cudaEvent_t ev[64];
-  bool made = false;
+  std::vector<std::array<char, 32>> names;
+  std::vector<cudaEvent_t> ev;  // two per stage
+  int cap() const { return (int)names.size(); }
 };
 
 struct lcp_ctx {
@@ -165,21 +169,19 @@ struct lcp_traj {
 };
 
 namespace {
-void prof_reset(lcp_ctx *c) { c->prof.n = 0; }
+void prof_reset(lcp_ctx *c) {
+  if (!c->prof.accumulate) c->prof.n = 0;
+}
 void prof_begin(lcp_ctx *c, const char *name, cudaStream_t s) {
   Profile &P = c->prof;
-  if (!P.on || P.n >= 32) return;
-  if (!P.made) {
-    for (int i = 0; i < 64; ++i) cudaEventCreate(&P.ev[i]);
-    P.made = true;
-  }
-  strncpy(P.names[P.n], name, 31);
+  if (!P.on || P.n >= P.cap()) return;
+  strncpy(P.names[P.n].data(), name, 31);
   P.names[P.n][31] = 0;
   cudaEventRecord(P.ev[2 * P.n], s);
 }
 void prof_end(lcp_ctx *c, cudaStream_t s) {
   Profile &P = c->prof;
-  if (!P.on || P.n >= 32) return;
+  if (!P.on || P.n >= P.cap()) return;
   cudaEventRecord(P.ev[2 * P.n + 1], s);
   ++P.n;
 }
@@ -656,6 +658,7 @@ lcp_status lcp_ctx_destroy(lcp_ctx *c) {
   if (c->h_sum) cudaFreeHost(c->h_sum);
   if (c->h_stage) cudaFreeHost(c->h_stage);
   if (c->h_err) cudaFreeHost(c->h_err);
+  for (cudaEvent_t e : c->prof.ev) cudaEventDestroy(e);
   delete c;
   return LCP_OK;
 }
@@ -865,12 +868,24 @@ Action fsm_plan(FsmCopy &f, bool has_ref) {
 
 int traj_buffers(lcp_traj *t, uint64_t n, uint32_t d) {
   const size_t qb = std::max<uint64_t>(n * d, 1) * 4, pb = std::max<uint64_t>(n, 1) * 4;
-  TRY(grow(t->prev_q, qb));
-  TRY(grow(t->prev_pi, pb));
-  TRY(grow(t->anc_q, qb));
-  TRY(grow(t->anc_pi, pb));
-  TRY(grow(t->new_q, qb));
-  TRY(grow(t->new_pi, pb));
+  DevBuf *bufs[6] = {&t->prev_q, &t->prev_pi, &t->anc_q, &t->anc_pi, &t->new_q, &t->new_pi};
+  const size_t need[6] = {qb, pb, qb, pb, qb, pb};
+  bool fresh = false;
+  for (int k = 0; k < 6; ++k) {
+    const void *old = bufs[k]->p;
+    TRY(grow(*bufs[k], need[k]));
+    if (bufs[k]->p != old) {  // new memory starts zeroed: checkpoint images are
+      fresh = true;            // defined even for arrays a decoder never writes
+      if (cudaMemset(bufs[k]->p, 0, bufs[k]->cap) != cudaSuccess) {
+        cudaGetLastError();
+        return ERR_CUDA;
+      }
+    }
+  }
+  if (fresh && cudaStreamSynchronize(cudaStreamLegacy) != cudaSuccess) {
+    cudaGetLastError();
+    return ERR_CUDA;
+  }
   return OK;
 }
 
@@ -1128,7 +1143,7 @@ lcp_status lcp_tune_schedule(lcp_ctx *c, const float *d_fields, uint64_t n, uint
     for (int bd : bds) {
       c->log2_chunk = lc;
       c->bucket_delta = bd;
-      float tsum = 0.0f;
+      float tmin = 0.0f;  // the fastest of the timed rounds (least disturbed)
       uint64_t size = 0;
       for (int r = 0; r <= reps && st == OK; ++r) {  // the first round warms up
         size_t sz = 0;
@@ -1149,13 +1164,13 @@ lcp_status lcp_tune_schedule(lcp_ctx *c, const float *d_fields, uint64_t n, uint
         if (st == OK && r > 0) {
           float ms = 0.0f;
           cudaEventElapsedTime(&ms, e0, e1);
-          tsum += ms;
+          tmin = r == 1 ? ms : std::min(tmin, ms);
         }
         size = sz;
       }
       if (st != OK) break;
       if (lc == 10 && bd == 0) base_size = size;
-      const float t = tsum / (float)reps;
+      const float t = tmin;
       const bool fits = (double)size <= (1.0 + max_growth) * (double)base_size;
       if (fits && (!have || t < best_t)) {
         have = true;
@@ -1690,6 +1705,280 @@ lcp_status lcp_decompress_frame(lcp_ctx *c, lcp_traj *dec, const void *const *d_
                                n_out, d_fields, stream);
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// one time step of many trajectories (config 4): the LCP-T frames in one
+// persistent launch, planned on the device, replayed as a CUDA graph
+// ---------------------------------------------------------------------------
+struct lcp_step {
+  lcp_ctx *ctx = nullptr;
+  int max_frames = 0;
+  // the graph runs on the step's own stream (a capture cannot use the legacy
+  // default stream), ordered after the caller's stream and before its next
+  // work by events
+  cudaStream_t own = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_kernels = 0;  // kernel nodes of the graph
+  // optional lanes for the frames the step does not fuse
+  std::vector<lcp_ctx *> lane_ctx;
+  std::vector<void *> lane_stream;
+  // device
+  uint32_t *d_nf = nullptr;
+  StepIn *d_jobs = nullptr;
+  StepFrame *d_frames = nullptr;
+  HuffTable *d_tabs = nullptr;
+  unsigned long long *d_items = nullptr;
+  StepResult *d_res = nullptr;
+  // pinned host: the step's jobs in, results out
+  uint32_t *h_nf = nullptr;
+  StepIn *h_jobs = nullptr;
+  StepResult *h_res = nullptr;
+  uint8_t *h_head = nullptr;  // container headers (16 bytes each)
+};
+
+extern "C" {
+
+lcp_status lcp_step_create(lcp_ctx *c, int max_frames, lcp_step **out) {
+  if (!c || !out || max_frames < 1 || max_frames > kStepMaxFrames) return LCP_ERR_ARG;
+  *out = nullptr;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  lcp_step *S = new lcp_step();
+  S->ctx = c;
+  S->max_frames = max_frames;
+  const int F = kStepMaxFrames;
+  if (cudaMalloc(&S->d_nf, 16) != cudaSuccess ||
+      cudaMalloc(&S->d_jobs, sizeof(StepIn) * F) != cudaSuccess ||
+      cudaMalloc(&S->d_frames, sizeof(StepFrame) * F) != cudaSuccess ||
+      cudaMalloc(&S->d_tabs, sizeof(HuffTable) * F) != cudaSuccess ||
+      cudaMalloc(&S->d_items, sizeof(unsigned long long) * (F + 2)) != cudaSuccess ||
+      cudaMalloc(&S->d_res, sizeof(StepResult) * F) != cudaSuccess ||
+      cudaMallocHost(&S->h_nf, 16) != cudaSuccess ||
+      cudaMallocHost(&S->h_jobs, sizeof(StepIn) * F) != cudaSuccess ||
+      cudaMallocHost(&S->h_res, sizeof(StepResult) * F) != cudaSuccess ||
+      cudaMallocHost(&S->h_head, 16 * (size_t)F) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&S->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    lcp_step_destroy(S);
+    return LCP_ERR_NOMEM;
+  }
+  *out = S;
+  return LCP_OK;
+}
+
+lcp_status lcp_step_destroy(lcp_step *S) {
+  if (!S) return LCP_ERR_ARG;
+  DeviceGuard g(S->ctx ? S->ctx->device : 0);
+  if (S->exec) cudaGraphExecDestroy(S->exec);
+  if (S->own) {
+    cudaStreamSynchronize(S->own);
+    cudaStreamDestroy(S->own);
+  }
+  if (S->ev_in) cudaEventDestroy(S->ev_in);
+  if (S->ev_out) cudaEventDestroy(S->ev_out);
+  cudaFree(S->d_nf);
+  cudaFree(S->d_jobs);
+  cudaFree(S->d_frames);
+  cudaFree(S->d_tabs);
+  cudaFree(S->d_items);
+  cudaFree(S->d_res);
+  cudaFreeHost(S->h_nf);
+  cudaFreeHost(S->h_jobs);
+  cudaFreeHost(S->h_res);
+  cudaFreeHost(S->h_head);
+  delete S;
+  return LCP_OK;
+}
+
+lcp_status lcp_step_set_lanes(lcp_step *S, lcp_ctx *const *ctxs, void *const *streams,
+                              int lanes) {
+  if (!S || lanes < 0 || (lanes > 0 && !ctxs)) return LCP_ERR_ARG;
+  for (int k = 0; k < lanes; ++k)
+    if (!ctxs[k] || ctxs[k]->device != S->ctx->device) return LCP_ERR_ARG;
+  S->lane_ctx.assign(ctxs, ctxs + lanes);
+  S->lane_stream.assign(lanes, nullptr);
+  if (streams) S->lane_stream.assign(streams, streams + lanes);
+  return LCP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// the step's device work, recorded once on the step's own stream as a
+// graph: jobs in, planning, the persistent decode, patches, results out
+int step_graph(lcp_step *S) {
+  if (S->exec) return OK;
+  cudaStream_t s = S->own;
+  cudaGraph_t graph = nullptr;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaMemcpyAsync(S->d_nf, S->h_nf, 16, cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(S->d_jobs, S->h_jobs, sizeof(StepIn) * S->max_frames, cudaMemcpyHostToDevice, s);
+  S->graph_kernels =
+      launch_step(S->d_nf, S->d_jobs, S->d_frames, S->d_tabs, S->d_items, S->d_res, S->ctx->sms, s);
+  cudaMemcpyAsync(S->h_res, S->d_res, sizeof(StepResult) * S->max_frames, cudaMemcpyDeviceToHost,
+                  s);
+  const cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (e != cudaSuccess || !graph) {
+    note_cuda_error(e, "cudaStreamEndCapture", __LINE__);
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    return ERR_CUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&S->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    note_cuda_error(ei, "cudaGraphInstantiate", __LINE__);
+    cudaGetLastError();
+    S->exec = nullptr;
+    return ERR_CUDA;
+  }
+  return OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lcp_status lcp_decompress_step(lcp_step *S, lcp_decompress_job *jobs, int njobs, void *stream) {
+  if (!S || njobs < 0 || (njobs > 0 && !jobs)) return LCP_ERR_ARG;
+  lcp_ctx *c = S->ctx;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<uint32_t> meth(njobs, 0u), flg(njobs, 0u);
+  // headers of every container (method, flags, n, d): rounds of up to 128
+  // copies, one synchronization each
+  constexpr int kRound = kStepMaxFrames / 2;  // 32-byte slots of h_head
+  for (int base = 0; base < njobs; base += kRound) {
+    const int end = std::min(njobs, base + kRound);
+    for (int k = base; k < end; ++k) {
+      lcp_decompress_job &J = jobs[k];
+      J.status = LCP_OK;
+      J.n_out = 0;
+      J.d_fields = 0;
+      J.ms = 0.0f;
+      if (!J.d_in || J.in_size < 48 || !aligned16(J.d_in)) {
+        J.status = LCP_ERR_FORMAT;
+        continue;
+      }
+      if (cudaMemcpyAsync(S->h_head + 32 * (size_t)(k - base), J.d_in, 32, cudaMemcpyDeviceToHost,
+                          s) != cudaSuccess) {
+        cudaGetLastError();
+        return LCP_ERR_CUDA;
+      }
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaGetLastError();
+      return LCP_ERR_CUDA;
+    }
+    for (int k = base; k < end; ++k) {
+      lcp_decompress_job &J = jobs[k];
+      if (J.status != LCP_OK) continue;
+      const uint8_t *h = S->h_head + 32 * (size_t)(k - base);
+      if (h[0] != 'L' || h[1] != 'C' || h[2] != 'P' || h[3] != '1') {
+        J.status = LCP_ERR_FORMAT;
+        continue;
+      }
+      J.d_fields = h[6];
+      J.n_out = rd64(h + 16);
+      meth[k] = h[5];
+      flg[k] = rd32(h + 8);
+    }
+  }
+  // the LCP-T frames whose reference is on their own grid go to the fused
+  // step; the others are decoded one by one
+  std::vector<int> fused;
+  std::vector<unsigned char> seen_traj;
+  int nf = 0;
+  for (int k = 0; k < njobs; ++k) {
+    lcp_decompress_job &J = jobs[k];
+    if (J.status != LCP_OK) continue;
+    const bool is_t = meth[k] == 1u;
+    const uint32_t flags = flg[k];
+    lcp_traj *t = J.traj;
+    bool ok = is_t && t && !(flags & kFlagRequant) && nf < S->max_frames &&
+              J.n_out <= J.n_cap && J.d_out && aligned16(J.d_out) &&
+              ((flags & kFlagRefAnchor) ? t->has_anchor : t->has_prev) && t->n == J.n_out &&
+              t->d == J.d_fields;
+    for (int i : fused) ok = ok && jobs[i].traj != t;  // one frame per trajectory
+    if (!ok) continue;
+    if (traj_buffers(t, J.n_out, J.d_fields) != OK) continue;
+    StepIn &I = S->h_jobs[nf];
+    I.in = reinterpret_cast<const uint8_t *>(J.d_in);
+    I.in_size = J.in_size;
+    I.qref = (flags & kFlagRefAnchor) ? P<int32_t>(t->anc_q) : P<int32_t>(t->prev_q);
+    I.out = J.d_out;
+    I.qnew = P<int32_t>(t->new_q);
+    I.n = J.n_out;
+    I.d = J.d_fields;
+    I.pad = 0;
+    fused.push_back(k);
+    ++nf;
+  }
+  if (nf > 0) {
+    *S->h_nf = (uint32_t)nf;
+    int st = step_graph(S);
+    if (st != OK) return (lcp_status)st;
+    if (cudaEventRecord(S->ev_in, s) != cudaSuccess ||
+        cudaStreamWaitEvent(S->own, S->ev_in, 0) != cudaSuccess ||
+        cudaGraphLaunch(S->exec, S->own) != cudaSuccess ||
+        cudaEventRecord(S->ev_out, S->own) != cudaSuccess ||
+        cudaStreamWaitEvent(s, S->ev_out, 0) != cudaSuccess ||
+        cudaStreamSynchronize(S->own) != cudaSuccess) {
+      cudaGetLastError();
+      return LCP_ERR_CUDA;
+    }
+    for (int i = 0; i < S->graph_kernels; ++i) note_launch();
+    for (int i = 0; i < nf; ++i) {
+      lcp_decompress_job &J = jobs[fused[i]];
+      const StepResult &R = S->h_res[i];
+      J.status = (lcp_status)R.status;
+      if (R.status != OK) continue;
+      lcp_traj *t = J.traj;
+      std::swap(t->prev_q, t->new_q);
+      for (uint32_t k = 0; k < J.d_fields; ++k) t->prev_F[k] = R.f[k];
+      t->prev_scaled = false;
+      t->has_prev = true;
+      t->t += 1;
+    }
+  }
+  // the rest: over the step's lanes when it has them and no trajectory
+  // comes twice among these frames, else one at a time in job order
+  std::vector<int> rest;
+  for (int k = 0; k < njobs; ++k)
+    if (jobs[k].status == LCP_OK && std::find(fused.begin(), fused.end(), k) == fused.end())
+      rest.push_back(k);
+  bool spread = S->lane_ctx.size() > 1 && rest.size() > 1;
+  for (size_t i = 0; spread && i < rest.size(); ++i)
+    for (size_t j = 0; j < i && spread; ++j)
+      if (jobs[rest[i]].traj && jobs[rest[i]].traj == jobs[rest[j]].traj) spread = false;
+  if (spread) {
+    std::vector<lcp_decompress_job> sub(rest.size());
+    for (size_t i = 0; i < rest.size(); ++i) sub[i] = jobs[rest[i]];
+    lcp_decompress_batch(S->lane_ctx.data(), S->lane_stream.data(), (int)S->lane_ctx.size(),
+                         sub.data(), (int)sub.size());
+    for (size_t i = 0; i < rest.size(); ++i) jobs[rest[i]] = sub[i];
+  } else {
+    for (int k : rest) {
+      lcp_decompress_job &J = jobs[k];
+      uint64_t no = 0;
+      uint32_t dd = 0;
+      J.status = (lcp_status)decompress_impl(c, J.traj, reinterpret_cast<const uint8_t *>(J.d_in),
+                                             J.in_size, J.d_out, J.n_cap, &no, &dd, s);
+      J.n_out = no;
+      J.d_fields = dd;
+    }
+  }
+  for (int k = 0; k < njobs; ++k)
+    if (jobs[k].status != LCP_OK) return LCP_ERR_STATE;  // per-job statuses tell which
+  return LCP_OK;
+}
+
 lcp_status lcp_peek(const void *d_in, size_t in_size, uint64_t *n, uint32_t *d,
                     lcp_method *method, uint32_t *flags, void *stream) {
   if (!d_in || in_size < 48) return LCP_ERR_FORMAT;
@@ -1752,26 +2041,45 @@ const char *lcp_last_error(void) { return g_last_error; }
 uint64_t lcp_kernel_launches(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 lcp_status lcp_ctx_profile(lcp_ctx *c, int enable) {
-  if (!c) return LCP_ERR_ARG;
-  c->prof.on = enable != 0;
-  c->prof.n = 0;
+  if (!c || enable < 0 || enable > 2) return LCP_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  Profile &P = c->prof;
+  P.on = enable != 0;
+  P.accumulate = enable == 2;
+  P.n = 0;
+  const int want = P.on ? (P.accumulate ? kProfAccum : kProfCall) : 0;
+  while (P.cap() < want) {  // events made here, not while timing
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      cudaGetLastError();
+      if (a) cudaEventDestroy(a);
+      P.on = false;
+      return LCP_ERR_CUDA;
+    }
+    P.ev.push_back(a);
+    P.ev.push_back(b);
+    P.names.push_back({});
+  }
   return LCP_OK;
 }
 
 int lcp_ctx_profile_read(lcp_ctx *c, char *names, float *ms, int cap) {
   if (!c || !c->prof.on) return 0;
   DeviceGuard g(c->device);
+  Profile &P = c->prof;
   int k = 0;
-  for (; k < c->prof.n && k < cap; ++k) {
+  for (; k < P.n && k < cap; ++k) {
     float t = 0.0f;
-    if (cudaEventSynchronize(c->prof.ev[2 * k + 1]) != cudaSuccess ||
-        cudaEventElapsedTime(&t, c->prof.ev[2 * k], c->prof.ev[2 * k + 1]) != cudaSuccess) {
+    if (cudaEventSynchronize(P.ev[2 * k + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t, P.ev[2 * k], P.ev[2 * k + 1]) != cudaSuccess) {
       cudaGetLastError();
       t = -1.0f;
     }
     if (ms) ms[k] = t;
-    if (names) memcpy(names + 32 * k, c->prof.names[k], 32);
+    if (names) memcpy(names + 32 * k, P.names[k].data(), 32);
   }
+  if (P.accumulate) P.n = 0;  // read out: the next stages start a new list
   return k;
 }
 

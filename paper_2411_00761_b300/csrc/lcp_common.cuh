@@ -57,6 +57,36 @@ struct FieldPlan {
   uint32_t pad1;
 };
 
+// Decoder-side block grid of a field from its qmax: bn = (qmax >> lp) + 1
+// blocks along the axis and the constants of floor(r / bn) for r < 2^63:
+// m = ceil(2^(63+l) / bn), l = ceil(log2 bn), then floor(r m / 2^(63+l)) =
+// floor(r / bn) (Granlund-Montgomery, division by invariant integers using
+// multiplication, Thm. 4.2).  The stride is the caller's (it depends on the
+// fields before this one).
+__device__ inline void field_block_grid(FieldPlan &F, uint32_t lp) {
+  const unsigned long long bn = ((unsigned long long)F.qmax >> lp) + 1ull;
+  F.bn = bn;
+  if (bn <= 1) {
+    F.bmagic = 0;
+    F.bshift = 255;
+    return;
+  }
+  uint32_t l = 0;
+  while ((1ull << l) < bn) ++l;
+  // binary long division of 2^(63+l) by bn; the quotient fits 64 bits
+  unsigned long long q = 0, rem = 0;
+  for (int bit = 63 + (int)l; bit >= 0; --bit) {
+    rem = (rem << 1) | (bit == 63 + (int)l ? 1ull : 0ull);
+    q <<= 1;
+    if (rem >= bn) {
+      rem -= bn;
+      q |= 1ull;
+    }
+  }
+  F.bmagic = q + (rem != 0 ? 1ull : 0ull);
+  F.bshift = l - 1;
+}
+
 struct MinMax {
   uint32_t lo[kMaxD];  // totalOrder keys
   uint32_t hi[kMaxD];
@@ -116,6 +146,26 @@ __host__ __device__ inline uint32_t bitlen64(unsigned long long v) {
 #else
   return v ? 64u - (uint32_t)__builtin_clzll(v) : 0u;
 #endif
+}
+
+// ---------------------------------------------------------------------------
+// asynchronous 4-byte copies global -> shared (cp.async, zero fill when not
+// valid), per-thread commit groups
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src, bool valid) {
+  const unsigned sdst = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sdst), "l"(src), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait1() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait0() {
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -515,6 +565,9 @@ __device__ inline int plan_field(float mn, float mx, double eb, int mode, uint32
   F.sticky = st;
   F.bn = ((unsigned long long)F.qmax >> lp) + 1ull;
   F.stride = 0;
+  F.bmagic = 0;  // every byte defined: plans are compared and checkpointed
+  F.bshift = 0;
+  F.pad1 = 0;
   return OK;
 }
 

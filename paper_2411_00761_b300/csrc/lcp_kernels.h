@@ -37,6 +37,32 @@ struct HuffTable {
   uint32_t used, ok;
 };
 
+#ifdef __CUDACC__
+// First-level table, one entry per kFastBits-bit window, filled by all the
+// block's threads entry by entry: in canonical order the window starts with
+// a code of length L for the smallest L whose codes end above it, i.e.
+// window < (first[L] + count[L]) 2^(kFastBits - L); that code is the
+// window's top L bits and its symbol the (code - first[L])-th of length L.
+// Windows whose code is longer than kFastBits get 0.  first, count and
+// index are the canonical tables (1 .. kLmax), syms the symbols (U of them).
+__device__ inline void huff_fill_fast(const uint32_t *first, const uint32_t *count,
+                                      const uint32_t *index, const uint16_t *syms, uint32_t U,
+                                      uint32_t *fast) {
+  for (uint32_t e = threadIdx.x; e < (1u << kFastBits); e += blockDim.x) {
+    uint32_t v = 0u;
+    for (int L = 1; L <= kFastBits; ++L) {
+      const uint32_t code = e >> (kFastBits - L);
+      if (code < first[L] + count[L]) {
+        const uint32_t i = index[L] + (code - first[L]);
+        if (code >= first[L] && i < U) v = ((uint32_t)syms[i] << 5) | (uint32_t)L;
+        break;
+      }
+    }
+    fast[e] = v;
+  }
+}
+#endif
+
 // --- frame stage (k_frame.cu) -------------------------------------------
 void launch_minmax(const float *fields, uint64_t n, uint32_t d, MinMax *mm, int sms,
                    cudaStream_t s);
@@ -254,6 +280,9 @@ struct ExpandArgs {
   uint32_t bn[kMaxD];
   unsigned long long bmagic[kMaxD];
   uint32_t bshift[kMaxD];
+  // the same quotient for r < 2^31: umulhi(r, bmagic32) >> bshift (Thm. 4.2
+  // with 31-bit dividends: bmagic32 = ceil(2^(31 + l) / bn) < 2^32)
+  uint32_t bmagic32[kMaxD];
   int div0_64;
   uint32_t qmax2[kMaxD / 2];
   float *out;              // [d][n], or null (codes only)
@@ -263,5 +292,34 @@ struct ExpandArgs {
 void launch_expand(uint32_t d, const ExpandArgs &a, bool lut, int sms, cudaStream_t s);
 void launch_outliers_decode(const Plan *plan, const float *raw, uint64_t K, uint64_t n, uint32_t d,
                             float *out, int32_t *qout, int sms, cudaStream_t s);
+
+// --- one time step of LCP-T frames in one persistent launch (k_step.cu) ---
+constexpr int kStepMaxFrames = 256;
+struct StepIn {             // per frame, from the host
+  const uint8_t *in;        // container (device)
+  unsigned long long in_size;
+  const int32_t *qref;      // reference codes [d][n]
+  float *out;               // decoded frame [d][n]
+  int32_t *qnew;            // its codes [d][n]
+  unsigned long long n;
+  uint32_t d, pad;
+};
+struct StepFrame {          // per frame, planned on the device
+  int status;
+  uint32_t d, coder, width, used, log2_chunk;
+  unsigned long long n, nd, K, n_chunks, payload_bits, nwords, groups, item0;
+  const uint8_t *sec, *ct, *patch;
+  const uint32_t *pl;
+  unsigned int err;
+  FieldPlan f[kMaxD];
+};
+struct StepResult {         // per frame, to the host
+  int status;
+  uint32_t pad;
+  FieldPlan f[kMaxD];
+};
+// nframes (device) <= kStepMaxFrames; items: kStepMaxFrames + 2 entries
+int launch_step(const uint32_t *nframes, const StepIn *jobs, StepFrame *frames, HuffTable *tabs,
+                unsigned long long *items, StepResult *res, int sms, cudaStream_t s);
 
 }  // namespace lcp

@@ -62,6 +62,10 @@ SIGNATURES = {
     "lcp_server_destroy": (C.c_int, [_vp]),
     "lcp_compress_batch": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp, C.c_int]),
     "lcp_decompress_batch": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int, _vp, C.c_int]),
+    "lcp_step_create": (C.c_int, [_vp, C.c_int, C.POINTER(_vp)]),
+    "lcp_step_destroy": (C.c_int, [_vp]),
+    "lcp_decompress_step": (C.c_int, [_vp, _vp, C.c_int, _vp]),
+    "lcp_step_set_lanes": (C.c_int, [_vp, _vp, _vp, C.c_int]),
     "lcp_ctx_set_schedule": (C.c_int, [_vp, _vp]),
     "lcp_ctx_get_schedule": (C.c_int, [_vp, _vp]),
     "lcp_tune_schedule": (C.c_int, [_vp, _vp, _u64, _u32, C.c_double, C.c_int, _u32, C.c_double,
@@ -192,15 +196,18 @@ class Context:
         except Exception:
             pass
 
-    def profile(self, enable: bool = True):
-        """Per-kernel CUDA-event timing of subsequent calls."""
-        _check(_lib.lcp_ctx_profile(self.h, 1 if enable else 0), "lcp_ctx_profile")
+    def profile(self, enable: bool = True, accumulate: bool = False):
+        """Per-kernel CUDA-event timing of subsequent calls; with accumulate,
+        every call's stages are kept until profile_read."""
+        mode = (2 if accumulate else 1) if enable else 0
+        _check(_lib.lcp_ctx_profile(self.h, mode), "lcp_ctx_profile")
 
-    def profile_read(self) -> list[tuple[str, float]]:
-        """(stage, ms) of the most recent call."""
-        names = C.create_string_buffer(32 * 32)
-        ms = (C.c_float * 32)()
-        k = _lib.lcp_ctx_profile_read(self.h, names, ms, 32)
+    def profile_read(self, cap: int = 32) -> list[tuple[str, float]]:
+        """(stage, ms) of the most recent call, or of every call since the
+        last read when accumulating."""
+        names = C.create_string_buffer(32 * cap)
+        ms = (C.c_float * cap)()
+        k = _lib.lcp_ctx_profile_read(self.h, names, ms, cap)
         raw = names.raw
         return [(raw[32 * i:32 * i + 32].split(b"\0")[0].decode(), float(ms[i])) for i in range(k)]
 
@@ -448,6 +455,49 @@ class Lanes:
                for j in arr]
         _check(st, "lcp_decompress_batch")
         return res
+
+
+class Step:
+    """lcp_step: one time step of many trajectories' LCP-T frames decoded in
+    one persistent launch, replayed as a CUDA graph (see include/lcp.h)."""
+
+    def __init__(self, ctx: Context, max_frames: int = 64, lanes: "Lanes | None" = None):
+        """lanes: contexts and streams for the frames the step does not fuse
+        (lcp_step_set_lanes); they must not serve other calls meanwhile."""
+        self.ctx = ctx
+        h = C.c_void_p()
+        _check(_lib.lcp_step_create(ctx.h, max_frames, C.byref(h)), "lcp_step_create")
+        self.h = h
+        self.lanes = lanes
+        if lanes is not None:
+            _check(_lib.lcp_step_set_lanes(h, lanes._c, lanes._s, len(lanes)),
+                   "lcp_step_set_lanes")
+
+    def decompress(self, jobs: list[dict], stream=None) -> list[dict]:
+        """jobs: dicts with buf (uint8 CUDA), size, traj (decoder Trajectory)
+        and out (float32 CUDA [d, n]).  Returns per job n, d and status."""
+        arr = (DecompressJob * len(jobs))()
+        for j, J in zip(arr, jobs):
+            j.traj = J["traj"].h.value if J.get("traj") is not None else None
+            j.d_in = J["buf"].data_ptr()
+            j.in_size = int(J["size"])
+            j.d_out = J["out"].data_ptr()
+            j.n_cap = J["out"].shape[-1]
+        st = _lib.lcp_decompress_step(self.h, arr, len(jobs), _stream(stream))
+        res = [dict(n=int(j.n_out), d=int(j.d_fields), status=int(j.status)) for j in arr]
+        _check(st, "lcp_decompress_step")
+        return res
+
+    def close(self):
+        if self.h:
+            _lib.lcp_step_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

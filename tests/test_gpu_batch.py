@@ -126,3 +126,38 @@ def test_batch_reports_per_job_status(lcp):
     alone = host_bytes(ctx.compress(X, EB, "abs", P))
     arr_ok = lanes.compress([dict(X=X, eb=EB, p=P, out=out)])
     assert host_bytes(arr_ok[0]) == alone
+
+
+@pytest.mark.parametrize("scale,nlanes", [(1, 0), (5, 0), (1, 3)])
+def test_step_decode_equals_oracle(lcp, orc, scale, nlanes):
+    """lcp_decompress_step: every time step's frames decoded together (LCP-T
+    frames in one persistent launch replayed as a CUDA graph, the others one
+    by one) equal the oracle's sequential decode of each trajectory bit for
+    bit; with anchor scaling the frames predicted from a scaled anchor take
+    the one-by-one path.  The decoder state afterwards equals a sequential
+    decoder's (checkpoint images compared).  With lanes, the frames the step
+    does not fuse (the LCP-S anchors) are spread over them."""
+    from oracle import hybrid
+    frames = trajectories()
+    enc = [hybrid.encode_trajectory(fr, EB, "abs", P, batch=BATCH, anchor_scale=scale)
+           for fr in frames]
+    dec = [hybrid.decode_trajectory([b for b, _ in e]) for e in enc]
+    assert any(m == "T" for e in enc for _, m in e)
+    ctx = lcp.Context(0)
+    lanes = lcp.Lanes(nlanes) if nlanes else None
+    step = lcp.Step(ctx, max_frames=len(SIZES), lanes=lanes)
+    trs = [lcp.Trajectory(ctx, batch=BATCH, p=P) for _ in SIZES]
+    seq = [lcp.Trajectory(ctx, batch=BATCH, p=P) for _ in SIZES]
+    outs = [torch.empty((3, n), dtype=torch.float32, device="cuda") for n in SIZES]
+    for t in range(N_STEPS):
+        bufs = [dev(np.frombuffer(enc[k][t][0], np.uint8)) for k in range(len(SIZES))]
+        res = step.decompress([dict(buf=bufs[k], size=bufs[k].numel(), traj=trs[k], out=outs[k])
+                               for k in range(len(SIZES))])
+        for k in range(len(SIZES)):
+            assert res[k]["status"] == lcp.OK and res[k]["n"] == SIZES[k], (k, t)
+            assert np.array_equal(outs[k].cpu().numpy().view(np.uint32),
+                                  dec[k][t].view(np.uint32)), (k, t)
+            ctx.decompress(bufs[k], traj=seq[k])
+    for k in range(len(SIZES)):
+        assert trs[k].export() == seq[k].export(), k
+    step.close()
