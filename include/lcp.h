@@ -134,6 +134,12 @@ LCP_API lcp_status lcp_compress(lcp_ctx *ctx, lcp_traj *traj, const float *d_fie
 LCP_API lcp_status lcp_decompress(lcp_ctx *ctx, lcp_traj *traj, const void *d_in, size_t in_size,
                           float *d_out, uint64_t n_cap, uint64_t *n_out, uint32_t *d_fields,
                           void *stream);
+/* The same, for a caller that does not know the frame's shape beforehand:
+ * d_out holds out_values floats, and the frame needs d n of them (values
+ * [f][n], stride n); LCP_ERR_CAPACITY (nothing written) when it needs more. */
+LCP_API lcp_status lcp_decompress_into(lcp_ctx *ctx, lcp_traj *traj, const void *d_in,
+                                       size_t in_size, float *d_out, uint64_t out_values,
+                                       uint64_t *n_out, uint32_t *d_fields, void *stream);
 
 /*
  * Random-access retrieval (Sec. "Spatial-Anchor-Frame-Based Batch

@@ -79,47 +79,44 @@ __global__ void __launch_bounds__(kCbThreads) k_cb_build(const uint32_t *__restr
     return;
   }
   bitonic_sort_u64(sk, kAlpha);
-  for (int i = threadIdx.x; i < U; i += blockDim.x) nodew[i] = (uint32_t)(sk[i] >> 12);
+  constexpr uint32_t kInf = 0xffffffffu;  // above every weight (U >= 2: each < n < 2^32)
+  for (int i = threadIdx.x; i < 2 * U - 1; i += blockDim.x)
+    nodew[i] = i < U ? (uint32_t)(sk[i] >> 12) : kInf;  // internal nodes not made yet
   __syncthreads();
   if (threadIdx.x == 0) {
     // leaves nodew[0..U) ascending; internal node j (id U + j) has weight
-    // nodew[U + j], created in non-decreasing order.  Branch-free picks: the
-    // next four leaves and three internal nodes are kept in registers; the
-    // refill of each window is loaded right after a pick (clamped in range)
-    // and used at the next one, so its latency overlaps that pick.  An
-    // internal entry not yet created when it is loaded is filled in when its
-    // node is made.
+    // nodew[U + j], created in non-decreasing order.  The heads of both
+    // queues and the entries behind them are kept in registers, an empty
+    // queue's head reading as kInf, so a pick is one comparison (a leaf on
+    // ties); the entry after them is loaded right after a pick and used at
+    // the next one, so its latency overlaps that pick.  An internal entry
+    // loaded before it is made (kInf) is filled in when its node is made.
     const uint32_t *lw = nodew;
     uint32_t *iw = nodew + U;
     int nl = 0, ni = 0;
-    uint32_t L0 = lw[0], L1 = lw[1], L2 = lw[min(2, U - 1)], L3 = lw[min(3, U - 1)];
-    uint32_t I0 = 0u, I1 = 0u, I2 = 0u;
-    uint32_t pL = lw[min(4, U - 1)], pI = 0u;  // lw[nl + 4], iw[ni + 3]
+    uint32_t L0 = lw[0], L1 = lw[1], pL = U > 2 ? lw[2] : kInf;
+    uint32_t I0 = kInf, I1 = kInf, pI = kInf;
     for (int nn = 0; nn < U - 1; ++nn) {
       uint32_t sum = 0u;
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        const bool leaf = nl < U && (ni == nn || L0 <= I0);
+        const bool leaf = L0 <= I0;
         sum += leaf ? L0 : I0;
         parent[leaf ? nl : U + ni] = (uint16_t)(U + nn);
         L0 = leaf ? L1 : L0;
-        L1 = leaf ? L2 : L1;
-        L2 = leaf ? L3 : L2;
-        L3 = leaf ? pL : L3;
+        L1 = leaf ? pL : L1;
         I0 = leaf ? I0 : I1;
-        I1 = leaf ? I1 : I2;
-        I2 = leaf ? I2 : pI;
+        I1 = leaf ? I1 : pI;
         nl += leaf ? 1 : 0;
         ni += leaf ? 0 : 1;
-        pL = lw[min(nl + 4, U - 1)];
-        pI = iw[min(ni + 3, U - 2)];
+        pL = nl + 2 < U ? lw[nl + 2] : kInf;
+        pI = ni + 2 <= U - 2 ? iw[ni + 2] : kInf;
       }
       iw[nn] = sum;
       const int q = nn - ni;  // queue length before this node joins
       I0 = q == 0 ? sum : I0;
       I1 = q == 1 ? sum : I1;
-      I2 = q == 2 ? sum : I2;
-      pI = q == 3 ? sum : pI;  // loaded before this store
+      pI = q == 2 ? sum : pI;  // loaded before this store
     }
     parent[2 * U - 2] = (uint16_t)(2 * U - 2);
   }
@@ -459,7 +456,7 @@ void launch_layout(const LayoutArgs &a, int sms, bool size_only, cudaStream_t s)
 // into a shared-memory stage.
 // ---------------------------------------------------------------------------
 constexpr int kFixWarps = 8;
-constexpr int kFixGroups = 4;  // groups per warp iteration (their loads issued together)
+constexpr int kFixGroups = 8;  // groups per warp iteration (their loads issued together)
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kFixWarps) k_encode_fixed(
@@ -779,7 +776,9 @@ static void encode_stream(const T *vals, uint64_t n, const StreamDesc *desc, con
   unsigned gc = (unsigned)std::min<unsigned long long>((chunks * 32 + 255) / 256, 16ull * sms);
   note_launch();
   k_chunk_bits<T><<<gc, 256, 0, s>>>(vals, desc, codes, lens, log2_chunk, chunk_bits, summary);
-  launch_scan_small(chunk_bits, (uint32_t)chunks, chunk_off, s, &desc->coder);
+  // chunk_bits holds scan_tmp_len(chunks) spare entries after the counts
+  launch_scan_small(chunk_bits, (uint32_t)chunks, chunk_off, s, &desc->coder,
+                    chunk_bits + chunks);
   unsigned gt = (unsigned)std::min<unsigned long long>((chunks + 255) / 256, 4ull * sms);
   note_launch();
   k_chunk_table<<<gt, 256, 0, s>>>(chunk_off, desc, out, summary);

@@ -30,7 +30,8 @@ constexpr int kSubMaxBits = 13; // within these bounds
 constexpr int kSubMax = 1 << kSubMaxBits;
 constexpr int kSplitThreads = 512;
 constexpr int kSplitIlp = 4;    // keys in flight per thread in the split passes
-constexpr uint32_t kSplitChunk = 32768;  // keys per task when a bucket is split by several CTAs
+constexpr uint32_t kSplitChunk = 16384;  // keys per task (staged in shared memory by k_split_big)
+constexpr int kStageThreads = 1024;      // k_split_big: 16 staged keys per thread
 constexpr int kSubThreads = 256;
 constexpr int kSubCtas = 5;     // resident k_subsort CTAs per SM (48 registers)
 
@@ -86,6 +87,49 @@ __global__ void k_bucket_colsum(const uint32_t *__restrict__ tile_hist, int tile
 constexpr int kScanPer = 16;
 constexpr int kScanTileS = 1024 * kScanPer;
 
+// one tile's exclusive scan with carry-in; returns the tile's total
+__device__ __forceinline__ unsigned long long scan_tile(const unsigned long long *__restrict__ in,
+                                                        uint64_t n, uint64_t base,
+                                                        unsigned long long carry,
+                                                        unsigned long long *__restrict__ out,
+                                                        unsigned long long *s_warp, bool vec) {
+  const uint64_t i0 = base + (uint64_t)threadIdx.x * kScanPer;
+  unsigned long long v[kScanPer];
+  if (vec && i0 + kScanPer <= n) {
+#pragma unroll
+    for (int j = 0; j < kScanPer; j += 2) {
+      const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(in + i0 + j);
+      v[j] = x.x;
+      v[j + 1] = x.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) v[j] = i0 + j < n ? in[i0 + j] : 0ull;
+  }
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int j = 0; j < kScanPer; ++j) sum += v[j];
+  unsigned long long total;
+  unsigned long long run = carry + block_exscan<1024>(sum, s_warp, total);
+  if (!out) return total;
+  if (vec && i0 + kScanPer <= n) {
+#pragma unroll
+    for (int j = 0; j < kScanPer; j += 2) {
+      const unsigned long long a = run;
+      run += v[j];
+      *reinterpret_cast<ulonglong2 *>(out + i0 + j) = make_ulonglong2(a, run);
+      run += v[j + 1];
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+      if (i0 + j < n) out[i0 + j] = run;
+      run += v[j];
+    }
+  }
+  return total;
+}
+
 __global__ void __launch_bounds__(1024) k_scan_small(const unsigned long long *__restrict__ in,
                                                      uint32_t n,
                                                      unsigned long long *__restrict__ out,
@@ -94,43 +138,29 @@ __global__ void __launch_bounds__(1024) k_scan_small(const unsigned long long *_
   if (gate && *gate != 1u) return;  // the stream this scan serves is not Huffman coded
   const bool vec = ((((uintptr_t)in) | ((uintptr_t)out)) & 15u) == 0;
   unsigned long long carry = 0;
-  for (uint64_t base = 0; base < n; base += kScanTileS) {
-    const uint64_t i0 = base + (uint64_t)threadIdx.x * kScanPer;
-    unsigned long long v[kScanPer];
-    if (vec && i0 + kScanPer <= n) {
-#pragma unroll
-      for (int j = 0; j < kScanPer; j += 2) {
-        const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(in + i0 + j);
-        v[j] = x.x;
-        v[j + 1] = x.y;
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < kScanPer; ++j) v[j] = i0 + j < n ? in[i0 + j] : 0ull;
-    }
-    unsigned long long sum = 0;
-#pragma unroll
-    for (int j = 0; j < kScanPer; ++j) sum += v[j];
-    unsigned long long total;
-    unsigned long long run = carry + block_exscan<1024>(sum, s_warp, total);
-    if (vec && i0 + kScanPer <= n) {
-#pragma unroll
-      for (int j = 0; j < kScanPer; j += 2) {
-        const unsigned long long a = run;
-        run += v[j];
-        *reinterpret_cast<ulonglong2 *>(out + i0 + j) = make_ulonglong2(a, run);
-        run += v[j + 1];
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < kScanPer; ++j) {
-        if (i0 + j < n) out[i0 + j] = run;
-        run += v[j];
-      }
-    }
-    carry += total;
-  }
+  for (uint64_t base = 0; base < n; base += kScanTileS)
+    carry += scan_tile(in, n, base, carry, out, s_warp, vec);
   if (threadIdx.x == 0) out[n] = carry;
+}
+
+// longer scans: tile totals (one CTA per tile), their scan, then every tile
+// again from its offset
+__global__ void __launch_bounds__(1024) k_scan_tiles(const unsigned long long *__restrict__ in,
+                                                     uint32_t n,
+                                                     const unsigned long long *__restrict__ offs,
+                                                     unsigned long long *__restrict__ out,
+                                                     const uint32_t *__restrict__ gate) {
+  __shared__ unsigned long long s_warp[32];
+  if (gate && *gate != 1u) return;
+  const bool vec = ((((uintptr_t)in) | ((uintptr_t)out)) & 15u) == 0;
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTileS;
+  if (!offs) {  // totals
+    const unsigned long long t = scan_tile(in, n, base, 0ull, nullptr, s_warp, vec);
+    if (threadIdx.x == 0) out[blockIdx.x] = t;
+  } else {
+    scan_tile(in, n, base, offs[blockIdx.x], out, s_warp, vec);
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = offs[gridDim.x];
+  }
 }
 
 // per bucket, the running offset over the tiles (eight tiles' counts loaded
@@ -167,10 +197,23 @@ void launch_bucket_offsets(uint32_t *tile_hist, int tiles, uint32_t nb1,
 }
 
 void launch_scan_small(const unsigned long long *in, uint32_t n, unsigned long long *out,
-                       cudaStream_t s, const uint32_t *gate) {
+                       cudaStream_t s, const uint32_t *gate, unsigned long long *tmp) {
+  const uint32_t tiles = (uint32_t)(((uint64_t)n + kScanTileS - 1) / kScanTileS);
+  if (!tmp || tiles <= 1) {
+    note_launch();
+    k_scan_small<<<1, 1024, 0, s>>>(in, n, out, gate);
+    return;
+  }
+  unsigned long long *tot = tmp, *offs = tmp + tiles + 1;  // scan_tmp_len(n) entries
   note_launch();
-  k_scan_small<<<1, 1024, 0, s>>>(in, n, out, gate);
+  k_scan_tiles<<<tiles, 1024, 0, s>>>(in, n, nullptr, tot, gate);
+  note_launch();
+  k_scan_small<<<1, 1024, 0, s>>>(tot, tiles, offs, gate);
+  note_launch();
+  k_scan_tiles<<<tiles, 1024, 0, s>>>(in, n, offs, out, gate);
 }
+
+uint64_t scan_tmp_len(uint64_t n) { return 2 * ((n + kScanTileS - 1) / kScanTileS + 2); }
 
 // ---------------------------------------------------------------------------
 // scatter: same tiles as the quantize pass; shared-memory cursors per bucket.
@@ -625,16 +668,24 @@ __global__ void __launch_bounds__(kScanThreads) k_split_scan(
   }
 }
 
-// Split tasks (fetched from a work counter).  A bucket of one task: one CTA
-// builds the sub-bucket histogram and offsets (sub_off[32 * big_cb[j] +
-// digit], within the bucket) and scatters.  A task of a bucket of several:
-// its starting positions come from pass 2, and it scatters its key range.
-// Loads are issued kSplitIlp at a time.
-__global__ void __launch_bounds__(kSplitThreads) k_split_big(
+// Split tasks (fetched from a work counter), one CTA per task of up to
+// kSplitChunk keys staged in shared memory: the keys are read once (their
+// sub-bucket histogram counted on the way in), put in sub-bucket order
+// locally (the slot of each key in a second shared array), then written out
+// in that order, so each sub-bucket's keys leave as one contiguous run.  A
+// bucket of one task: its sub-bucket offsets (sub_off[32 * big_cb[j] +
+// digit], within the bucket) are the local ones.  A task of a bucket of
+// several: its starting positions come from k_split_scan.
+constexpr size_t kStageSmem = (size_t)kSplitChunk * (8 + 2);  // keys, local order
+
+__global__ void __launch_bounds__(kStageThreads, 1) k_split_big(
     const Plan *__restrict__ plan, const unsigned long long *__restrict__ bstart, SegBufs g,
     const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ idx,
     unsigned long long *__restrict__ keys_out, uint32_t *__restrict__ idx_out) {
-  constexpr int per = kSubMax / kSplitThreads;
+  constexpr int per = kSubMax / kStageThreads;        // digits per thread in the scan
+  constexpr int kk = (int)kSplitChunk / kStageThreads;  // staged keys per thread
+  extern __shared__ __align__(16) unsigned long long sk[];
+  uint16_t *lord = reinterpret_cast<uint16_t *>(sk + kSplitChunk);  // key index by local slot
   __shared__ uint32_t h[kSubMax];
   __shared__ unsigned long long s_warp[32];
   __shared__ uint32_t s_t;
@@ -643,7 +694,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
   const uint32_t total = g.nbig[3];
   for (;;) {
     if (threadIdx.x == 0) s_t = atomicAdd(&g.nbig[1], 1u);
-    for (int d = threadIdx.x; d < kSubMax; d += kSplitThreads) h[d] = 0u;
+    for (int d = threadIdx.x; d < kSubMax; d += kStageThreads) h[d] = 0u;
     __syncthreads();
     const uint32_t t = s_t;
     if (t >= total) break;
@@ -655,14 +706,36 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
     const int shift2 = (int)P.part_shift - sub;
     const uint32_t mask = (1u << sub) - 1u;
     const uint32_t nsub = 1u << sub;
-    const unsigned long long *kb = keys + lo;
-    uint32_t c0 = 0, c1 = cnt;
-    if (split_tasks(cnt) == 1u) {
-      for (uint32_t q = threadIdx.x; q < sub_chunks(sub); q += kSplitThreads)
+    const bool single = split_tasks(cnt) == 1u;
+    const uint32_t k = single ? 0u : t - g.big_tb[j];
+    const uint32_t c0 = k * kSplitChunk;
+    const uint32_t m = min(cnt, c0 + kSplitChunk) - c0;  // keys of this task
+    const unsigned long long *kb = keys + lo + c0;
+    if (single)
+      for (uint32_t q = threadIdx.x; q < sub_chunks(sub); q += kStageThreads)
         g.chunk_owner[g.big_cb[j] + q] = j;
-      split_count(kb, 0u, cnt, shift2, mask, h);
-      __syncthreads();
-      // offsets; thread t owns sub-buckets t*per .. t*per+per-1
+    // 1. stage the keys (all loads in flight at once) and count the digits
+    {
+      unsigned long long kv[kk];
+#pragma unroll
+      for (int r = 0; r < kk; ++r) {
+        const uint32_t i = (uint32_t)r * kStageThreads + threadIdx.x;
+        kv[r] = i < m ? kb[i] : 0ull;
+      }
+#pragma unroll
+      for (int r = 0; r < kk; ++r) {
+        const uint32_t i = (uint32_t)r * kStageThreads + threadIdx.x;
+        const uint32_t dg = (uint32_t)(kv[r] >> shift2) & mask;
+        if (i < m) sk[i] = kv[r];
+        int leader;
+        uint32_t rank, len;
+        lane_runs(dg, i < m, leader, rank, len);
+        if (i < m && rank == 0u) atomicAdd(&h[dg], len);
+      }
+    }
+    __syncthreads();
+    // 2. local sub-bucket starts; thread t owns digits t*per .. t*per+per-1
+    {
       uint32_t c[per];
       unsigned long long sum = 0;
 #pragma unroll
@@ -672,65 +745,48 @@ __global__ void __launch_bounds__(kSplitThreads) k_split_big(
         sum += c[q];
       }
       unsigned long long tot;
-      uint32_t run = (uint32_t)block_exscan<kSplitThreads>(sum, s_warp, tot);
+      uint32_t run = (uint32_t)block_exscan<kStageThreads>(sum, s_warp, tot);
       uint32_t *so = g.sub_off + (uint64_t)g.big_cb[j] * 32u;
 #pragma unroll
       for (int q = 0; q < per; ++q) {
         const uint32_t dg = threadIdx.x * per + q;
         if (dg < nsub) {
-          so[dg] = run;
+          if (single) so[dg] = run;
           h[dg] = run;
         }
         run += c[q];
       }
-    } else {
-      const uint32_t k = t - g.big_tb[j];
-      c0 = k * kSplitChunk;
-      c1 = min(cnt, c0 + kSplitChunk);
-      const uint32_t *base = g.shist + ((uint64_t)g.big_hs[j] + k) * kSubMax;
-      for (uint32_t d = threadIdx.x; d < nsub; d += kSplitThreads) h[d] = base[d];
     }
     __syncthreads();
-    // scatter; the next round's keys are loaded before this round's cursor
-    // updates and stores
-    constexpr uint32_t kStep = kSplitThreads * kSplitIlp;
-    unsigned long long kn[kSplitIlp];
-#pragma unroll
-    for (int r = 0; r < kSplitIlp; ++r) {
-      const uint32_t u = c0 + r * kSplitThreads + threadIdx.x;
-      kn[r] = u < c1 ? kb[u] : 0ull;
+    // 3. local order: lord[local slot] = staged index (h[d] ends at the
+    // start of digit d + 1)
+#pragma unroll 4
+    for (int r = 0; r < kk; ++r) {
+      const uint32_t i = (uint32_t)r * kStageThreads + threadIdx.x;
+      const bool on = i < m;
+      const uint32_t dg = on ? (uint32_t)(sk[i] >> shift2) & mask : 0u;
+      int leader;
+      uint32_t rank, len;
+      lane_runs(dg, on, leader, rank, len);
+      uint32_t bs = 0u;
+      if (on && rank == 0u) bs = atomicAdd(&h[dg], len);
+      const uint32_t ls = __shfl_sync(0xffffffffu, bs, leader) + rank;
+      if (on) lord[ls] = (uint16_t)i;
     }
-    for (uint32_t t0 = c0; t0 < c1; t0 += kStep) {
-      unsigned long long k[kSplitIlp];
-      uint32_t ix[kSplitIlp];
-#pragma unroll
-      for (int r = 0; r < kSplitIlp; ++r) {
-        const uint32_t u = t0 + r * kSplitThreads + threadIdx.x;
-        k[r] = kn[r];
-        ix[r] = (idx_out && u < c1) ? idx[lo + u] : 0u;
-        const uint32_t un = u + kStep;
-        kn[r] = un < c1 ? kb[un] : 0ull;
+    __syncthreads();
+    // 4. out in local order: runs of one sub-bucket go to consecutive slots
+    const uint32_t *gb = single ? nullptr : g.shist + ((uint64_t)g.big_hs[j] + k) * kSubMax;
+    for (uint32_t p = threadIdx.x; p < m; p += kStageThreads) {
+      const uint32_t i = lord[p];
+      const unsigned long long key = sk[i];
+      uint32_t pos = p;
+      if (!single) {
+        const uint32_t dg = (uint32_t)(key >> shift2) & mask;
+        const uint32_t ls = dg ? h[dg - 1] : 0u;  // local start of the digit
+        pos = gb[dg] + (p - ls);
       }
-      uint32_t pos[kSplitIlp];
-#pragma unroll
-      for (int r = 0; r < kSplitIlp; ++r) {
-        const uint32_t u = t0 + r * kSplitThreads + threadIdx.x;
-        const uint32_t dg = (uint32_t)(k[r] >> shift2) & mask;
-        int leader;
-        uint32_t rank, len;
-        lane_runs(dg, u < c1, leader, rank, len);
-        uint32_t bs = 0u;
-        if (u < c1 && rank == 0u) bs = atomicAdd(&h[dg], len);
-        pos[r] = __shfl_sync(0xffffffffu, bs, leader) + rank;
-      }
-#pragma unroll
-      for (int r = 0; r < kSplitIlp; ++r) {
-        const uint32_t u = t0 + r * kSplitThreads + threadIdx.x;
-        if (u < c1) {
-          keys_out[lo + pos[r]] = k[r];
-          if (idx_out) idx_out[lo + pos[r]] = ix[r];
-        }
-      }
+      keys_out[lo + pos] = key;
+      if (idx_out) idx_out[lo + pos] = idx[lo + c0 + i];
     }
     __syncthreads();
   }
@@ -842,8 +898,13 @@ void launch_segments(const Plan *plan, uint32_t nb1, const unsigned long long *b
     k_split_scan<<<(unsigned)std::min<uint64_t>(mmax, sms), kScanThreads, 0, s>>>(plan, bstart,
                                                                                  g);
   }
+  static const bool attr =  // once per process, thread-safe
+      cudaFuncSetAttribute(k_split_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kStageSmem) == cudaSuccess;
+  (void)attr;
   note_launch();
-  k_split_big<<<4 * sms, kSplitThreads, 0, s>>>(plan, bstart, g, keys, idx, keys_alt, idx_alt);
+  k_split_big<<<sms, kStageThreads, kStageSmem, s>>>(plan, bstart, g, keys, idx, keys_alt,
+                                                      idx_alt);
   note_launch();
   k_units_small<<<1, 1024, 0, s>>>(nb1, bstart, g.big_of, u_lo, u_cnt, u_meta, nunit);
 }

@@ -223,7 +223,7 @@ int ws_common(lcp_ctx *c, uint64_t n, uint32_t d) {
   // per-chunk bit counts and offsets of the longest stream (n d values in
   // LCP-T) at the context's chunk size
   const uint64_t chunks = (std::max<uint64_t>(nd, n) >> c->log2_chunk) + 2;
-  TRY(grow(w.chunk_bits, chunks * 8));
+  TRY(grow(w.chunk_bits, (chunks + scan_tmp_len(chunks)) * 8));  // counts, scan scratch
   TRY(grow(w.chunk_off, (chunks + 1) * 8));
   return OK;
 }
@@ -555,10 +555,11 @@ int check_p(uint32_t p, uint32_t d) {
 
 // p == 0: exact size for each candidate, smallest wins, ties to the smaller p
 // one container (below, with the decompression entry points); codes_only: a
-// frame decoded only as the reference of later frames
+// frame decoded only as the reference of later frames; floats_cap > 0: the
+// output's capacity in values (d n of them needed) instead of n_cap
 int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, float *out,
                     uint64_t n_cap, uint64_t *n_out, uint32_t *d_out, cudaStream_t s,
-                    bool codes_only = false);
+                    bool codes_only = false, uint64_t floats_cap = 0);
 
 int choose_p(lcp_ctx *c, const float *X, uint64_t n, uint32_t d, double eb, int mode,
              uint32_t *best, cudaStream_t s) {
@@ -1372,9 +1373,10 @@ int read_header(lcp_ctx *c, const uint8_t *in, size_t in_size, Header &h, cudaSt
 // codes into the trajectory, no values; out is ignored)
 int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, float *out,
                     uint64_t n_cap, uint64_t *n_out, uint32_t *d_out, cudaStream_t s,
-                    bool codes_only) {
+                    bool codes_only, uint64_t floats_cap) {
   Header h;
   TRY(read_header(c, in, in_size, h, s));
+  if (floats_cap) n_cap = floats_cap / std::max<uint32_t>(h.d, 1u);
   if (n_out) *n_out = h.n;
   if (d_out) *d_out = h.d;
   if (codes_only) {
@@ -1544,6 +1546,18 @@ lcp_status lcp_decompress(lcp_ctx *c, lcp_traj *traj, const void *d_in, size_t i
   prof_reset(c);
   return (lcp_status)decompress_impl(c, traj, (const uint8_t *)d_in, in_size, d_out, n_cap, n_out,
                                      d_fields, (cudaStream_t)stream);
+}
+
+lcp_status lcp_decompress_into(lcp_ctx *c, lcp_traj *traj, const void *d_in, size_t in_size,
+                               float *d_out, uint64_t out_values, uint64_t *n_out,
+                               uint32_t *d_fields, void *stream) {
+  if (!c) return LCP_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  prof_reset(c);
+  return (lcp_status)decompress_impl(c, traj, (const uint8_t *)d_in, in_size, d_out, 0, n_out,
+                                     d_fields, (cudaStream_t)stream, false,
+                                     std::max<uint64_t>(out_values, 1));
 }
 
 }  // extern "C"

@@ -78,9 +78,12 @@ void launch_element_rules(const float *x, uint64_t n, FieldPlan *fp_dev, int32_t
                           uint8_t *viol, int *status, cudaStream_t s);
 
 // --- partition and segmentation (k_sort.cu) -----------------------------
-// exclusive scan, out[n] = total; skipped when gate is given and *gate != 1
+// exclusive scan, out[n] = total; skipped when gate is given and *gate != 1.
+// With tmp (scan_tmp_len(n) entries) a long scan runs one CTA per tile.
 void launch_scan_small(const unsigned long long *in, uint32_t n, unsigned long long *out,
-                       cudaStream_t s, const uint32_t *gate = nullptr);
+                       cudaStream_t s, const uint32_t *gate = nullptr,
+                       unsigned long long *tmp = nullptr);
+uint64_t scan_tmp_len(uint64_t n);
 void launch_bucket_offsets(uint32_t *tile_hist, int tiles, uint32_t nb1,
                            unsigned long long *bucket_start, unsigned long long *totals,
                            cudaStream_t s);

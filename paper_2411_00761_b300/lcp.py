@@ -34,6 +34,8 @@ SIGNATURES = {
                                _sz, C.POINTER(_sz), C.POINTER(C.c_int), _vp, _vp]),
     "lcp_decompress": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _u64, C.POINTER(_u64), C.POINTER(_u32),
                                  _vp]),
+    "lcp_decompress_into": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _u64, C.POINTER(_u64),
+                                      C.POINTER(_u32), _vp]),
     "lcp_peek": (C.c_int, [_vp, _sz, C.POINTER(_u64), C.POINTER(_u32), C.POINTER(C.c_int),
                            C.POINTER(_u32), _vp]),
     "lcp_select": (C.c_int, [_vp, _vp, _vp, _u64, _u32, C.c_double, C.c_int, C.POINTER(C.c_int),
@@ -245,15 +247,19 @@ class Context:
         order."""
         assert buf.is_cuda and buf.dtype == torch.uint8
         size = buf.numel() if size is None else size
-        n, d, _, _ = self.peek(buf, size, stream)
         if out is None:
+            n, d, _, _ = self.peek(buf, size, stream)
             out = torch.empty((d, n), dtype=torch.float32, device=buf.device)
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+        # the output's capacity in values: the call checks d n against it, so
+        # no header read is needed here
         nn = C.c_uint64(0)
         dd = C.c_uint32(0)
-        st = _lib.lcp_decompress(self.h, traj.h if traj is not None else None, _ptr(buf), size,
-                                 _ptr(out), out.numel() // max(d, 1), C.byref(nn), C.byref(dd),
-                                 _stream(stream))
+        st = _lib.lcp_decompress_into(self.h, traj.h if traj is not None else None, _ptr(buf),
+                                      size, _ptr(out), out.numel(), C.byref(nn), C.byref(dd),
+                                      _stream(stream))
         _check(st, "lcp_decompress")
+        n, d = nn.value, dd.value
         return out.view(-1)[: d * n].view(d, n)
 
     def set_schedule(self, log2_chunk: int = 10, bucket_delta: int = 0):
