@@ -9,6 +9,7 @@
 // Streams are cut into chunks of 2^log2_chunk symbols whose starting bit
 // offsets are stored, so the decoder can work on chunks in parallel.
 #include <algorithm>
+#include <type_traits>
 
 #include "lcp_kernels.h"
 
@@ -244,40 +245,48 @@ __global__ void __launch_bounds__(kCbThreads) k_codebook(const uint32_t *__restr
   }
   __syncthreads();
   {
-    __shared__ uint32_t s_wsum[32];
-    const int per = kAlpha / kCbThreads;  // 4
-    for (int L = 1; L <= kLmax; ++L) {
-      if (s_lc[L] == 0) continue;  // uniform across the block
-      uint32_t c = 0;
-      for (int k = 0; k < per; ++k) c += depth8[threadIdx.x * per + k] == L;
-      // block exclusive scan of c
-      uint32_t x = c;
-      const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-      for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+    // ranks among the codes of one length in symbol order: warp w owns
+    // symbols 128 w + 32 k + lane (k = 0..3, in that order); lanes of equal
+    // length are grouped by __match_any_sync, a warp's running count per
+    // length is kept in shared memory, and the warps' counts per length are
+    // turned into bases by one thread per length
+    constexpr int kW = kCbThreads / 32;
+    __shared__ uint32_t s_wl[kW][kLmax + 1];  // per warp, per length: count, then base
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int L = lane; L <= kLmax; L += 32) s_wl[wp][L] = 0u;
+    __syncwarp();
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t lrank[kAlpha / kCbThreads];
+#pragma unroll
+    for (int k = 0; k < kAlpha / kCbThreads; ++k) {
+      const int sym = wp * 128 + k * 32 + lane;
+      const uint32_t L = depth8[sym];
+      const uint32_t m = __match_any_sync(0xffffffffu, L);
+      lrank[k] = L ? s_wl[wp][L] + __popc(m & lt) : 0u;
+      __syncwarp();
+      if (L && (m & lt) == 0u) s_wl[wp][L] += __popc(m);  // the group's first lane
+      __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x >= 1 && threadIdx.x <= kLmax) {
+      const int L = threadIdx.x;
+      uint32_t run = 0u;
+      for (int w = 0; w < kW; ++w) {
+        const uint32_t c = s_wl[w][L];
+        s_wl[w][L] = run;
+        run += c;
       }
-      if (lane == 31) s_wsum[wp] = x;
-      __syncthreads();
-      if (wp == 0) {
-        uint32_t t = s_wsum[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-          uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-          if (lane >= o) t += y;
-        }
-        s_wsum[lane] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kAlpha / kCbThreads; ++k) {
+      const int sym = wp * 128 + k * 32 + lane;
+      const uint32_t L = depth8[sym];
+      if (L) {
+        const uint32_t rank = s_wl[wp][L] + lrank[k];
+        codes[(uint64_t)s * kAlpha + sym] = s_first[L] + rank;
+        tables[(uint64_t)s * (kAlpha + 32) + 32 + s_index[L] + rank] = (uint16_t)sym;
       }
-      __syncthreads();
-      uint32_t rank = (wp ? s_wsum[wp - 1] : 0u) + x - c;
-      for (int k = 0; k < per; ++k) {
-        int sym = threadIdx.x * per + k;
-        if (depth8[sym] == L) {
-          codes[(uint64_t)s * kAlpha + sym] = s_first[L] + rank;
-          tables[(uint64_t)s * (kAlpha + 32) + 32 + s_index[L] + rank] = (uint16_t)sym;
-          ++rank;
-        }
-      }
-      __syncthreads();
     }
   }
   for (int i = threadIdx.x; i < kAlpha; i += blockDim.x) {
@@ -475,10 +484,71 @@ __global__ void __launch_bounds__(32 * kFixWarps) k_encode_fixed(
   const unsigned long long nw = (unsigned long long)gridDim.x * kFixWarps;
   // word `lane` of a group spans bits [32 lane, 32 lane + 32): values
   // i_lo = floor(32 lane / w) onwards, value i shifted left by
-  // 32 lane + 64 - (i + 1) w within a 64-bit accumulator whose high word is
-  // the output (bits of neighbouring words fall off either end)
+  // sh = 32 lane + 64 - (i + 1) w within a 64-bit accumulator whose high word
+  // is the output (bits of neighbouring words fall off either end)
   const uint32_t i_lo = w <= 32u ? (32u * (uint32_t)lane) / w : 0u;
   const int nj = w <= 32u ? (int)((32u + w - 1u) / w) + 1 : 0;  // values a word can touch
+  // for w >= 8 (at most kFixJ values per word) the high word of each shifted
+  // value is (x << L) >> R with (L, R) = (sh - 32, 0) or (0, 32 - sh); the
+  // sources, shifts and validity depend only on the lane and are set once
+  constexpr int kFixJ = 5;
+  uint32_t src[kFixJ], shl[kFixJ], shr[kFixJ], jm = 0u;
+#pragma unroll
+  for (int j = 0; j < kFixJ; ++j) {
+    const uint32_t i = i_lo + (uint32_t)j;
+    const int sh = 32 * lane + 64 - (int)((i + 1u) * w);
+    const bool ok = w >= 8u && j < nj && i < 32u && (int)(i * w) < 32 * lane + 32 && sh < 64;
+    src[j] = i & 31u;
+    shl[j] = ok && sh >= 32 ? (uint32_t)(sh - 32) : 0u;
+    shr[j] = ok && sh < 32 ? (uint32_t)(32 - sh) : 0u;
+    jm |= ok ? (1u << j) : 0u;
+  }
+  if constexpr (std::is_same<T, uint32_t>::value) {
+    if (w >= 8u && w <= 32u) {
+      // 4-byte values: a warp stages 1024 of them (32 groups) with 16-byte
+      // loads, all in flight together, then assembles each group's words from
+      // the staged values (the sources and shifts above, read from shared
+      // memory instead of shuffled)
+      __shared__ __align__(16) uint32_t st32[kFixWarps][1024];
+      uint32_t *sv = st32[wl];
+      const unsigned long long supers = (D.n + 1023) >> 10;
+      const unsigned long long nsw = (unsigned long long)gridDim.x * kFixWarps;
+      const bool vec = (((uintptr_t)vals) & 15u) == 0;
+      for (unsigned long long sg = (unsigned long long)blockIdx.x * kFixWarps + wl; sg < supers;
+           sg += nsw) {
+        const unsigned long long base = sg << 10;
+        uint4 r[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+          const unsigned long long i = base + (unsigned long long)a * 128 + 4ull * lane;
+          if (vec && i + 4 <= D.n) {
+            r[a] = *reinterpret_cast<const uint4 *>(vals + i);
+          } else {
+            r[a].x = i < D.n ? (uint32_t)vals[i] : 0u;
+            r[a].y = i + 1 < D.n ? (uint32_t)vals[i + 1] : 0u;
+            r[a].z = i + 2 < D.n ? (uint32_t)vals[i + 2] : 0u;
+            r[a].w = i + 3 < D.n ? (uint32_t)vals[i + 3] : 0u;
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < 8; ++a) reinterpret_cast<uint4 *>(sv)[a * 32 + lane] = r[a];
+        __syncwarp();
+        const unsigned long long g_first = base >> 5;
+        const uint32_t ng = (uint32_t)min(32ull, groups - g_first);
+        for (uint32_t gq = 0; gq < ng; ++gq) {
+          const uint32_t *gv = sv + gq * 32;
+          uint32_t word = 0u;
+#pragma unroll
+          for (int j = 0; j < kFixJ; ++j)
+            if ((jm >> j) & 1u) word |= (gv[src[j]] << shl[j]) >> shr[j];
+          const unsigned long long wb = (g_first + gq) * (unsigned long long)w;
+          if ((uint32_t)lane < w && wb + lane < words) pl[wb + lane] = word;
+        }
+        __syncwarp();
+      }
+      return;
+    }
+  }
   for (unsigned long long g0 = ((unsigned long long)blockIdx.x * kFixWarps + wl) * kFixGroups;
        g0 < groups; g0 += nw * kFixGroups) {
     unsigned long long v[kFixGroups];
@@ -492,7 +562,16 @@ __global__ void __launch_bounds__(32 * kFixWarps) k_encode_fixed(
       const unsigned long long g = g0 + q;
       if (g >= groups) break;
       const unsigned long long wbase = g * (unsigned long long)w;
-      if (w <= 32u) {
+      if (w >= 8u && w <= 32u) {
+        const uint32_t x32 = (uint32_t)v[q];
+        uint32_t word = 0u;
+#pragma unroll
+        for (int j = 0; j < kFixJ; ++j) {
+          const uint32_t x = __shfl_sync(0xffffffffu, x32, (int)src[j]);
+          word |= ((jm >> j) & 1u) ? ((x << shl[j]) >> shr[j]) : 0u;
+        }
+        if ((uint32_t)lane < w && wbase + lane < words) pl[wbase + lane] = word;
+      } else if (w <= 32u) {
         const uint32_t x32 = (uint32_t)v[q];
         unsigned long long acc = 0ull;
         for (int j = 0; j < nj; ++j) {
@@ -537,6 +616,11 @@ __global__ void __launch_bounds__(32 * kFixWarps) k_encode_fixed(
 constexpr int kEncWarps = 8;
 constexpr int kStageWords = 2848;  // >= (1024 * (24 + 64)) / 32 + 2
 constexpr size_t kEncSmem = sizeof(uint32_t) * ((size_t)kEncWarps * kStageWords + kAlpha);
+// a warp's stage for chunks of 2^log2_chunk symbols (at most 24 + 64 bits each)
+__host__ __device__ constexpr uint32_t enc_stage_words(uint32_t log2_chunk) {
+  return (uint32_t)((((1ull << log2_chunk) * (kLmax + 64)) + 31) / 32 + 2);
+}
+static_assert(enc_stage_words(10) <= (uint32_t)kStageWords, "stage of the largest chunks");
 
 // code table of the stream in shared memory: (code << 5) | length
 __device__ __forceinline__ void load_code_table(uint32_t *t, const uint32_t *codes,
@@ -648,7 +732,8 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_huff_encode(
     const unsigned long long *__restrict__ chunk_off, uint8_t *__restrict__ out,
     const Summary *__restrict__ summary) {
   extern __shared__ uint32_t enc_smem[];  // per-warp stages, then the code table
-  uint32_t *tab = enc_smem + (size_t)kEncWarps * kStageWords;
+  const uint32_t stage_words = enc_stage_words(log2_chunk);
+  uint32_t *tab = enc_smem + (size_t)kEncWarps * stage_words;
   if (summary->status != OK) return;
   const StreamDesc D = *dp;
   if (D.coder != 1) return;
@@ -657,7 +742,7 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_huff_encode(
   const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
   const unsigned long long cs = 1ull << log2_chunk;
   const uint32_t width = D.width;
-  uint32_t *buf = enc_smem + (size_t)wl * kStageWords;
+  uint32_t *buf = enc_smem + (size_t)wl * stage_words;
   uint32_t *pl = reinterpret_cast<uint32_t *>(out + D.offset + pad16(80ull + 2ull * D.used) +
                                               pad16(8ull * D.n_chunks));
   const unsigned long long total_words = words_of(D.payload_bits);
@@ -669,14 +754,18 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_huff_encode(
     const unsigned long long end = (c + 1 < D.n_chunks) ? chunk_off[c + 1] : D.payload_bits;
     const unsigned long long w0 = start >> 5, w1 = (end + 31) >> 5;  // [w0, w1)
     const uint32_t nwords = (uint32_t)(w1 - w0);
-    if (nwords > (uint32_t)kStageWords || w1 > total_words) continue;  // cannot happen
+    if (nwords > stage_words || w1 > total_words) continue;  // cannot happen
     for (uint32_t i = lane; i < nwords; i += 32) buf[i] = 0u;
     __syncwarp();
     uint32_t base = (uint32_t)(start & 31ull);  // bit position relative to word w0
+    unsigned long long vn[kEncPer];  // the next round's values, loaded a round ahead
+    enc_load4<T>(vals, lo + (unsigned long long)lane * kEncPer, hi, vn);
     for (unsigned long long b0 = lo; b0 < hi; b0 += 32 * kEncPer) {
       const unsigned long long i0 = b0 + (unsigned long long)lane * kEncPer;
       unsigned long long v[kEncPer];
-      enc_load4<T>(vals, i0, hi, v);
+#pragma unroll
+      for (int j = 0; j < kEncPer; ++j) v[j] = vn[j];
+      if (b0 + 32 * kEncPer < hi) enc_load4<T>(vals, i0 + 32 * kEncPer, hi, vn);
       uint32_t e[kEncPer], bits = 0u, em = 0u;  // em: escapes with raw bits
 #pragma unroll
       for (int j = 0; j < kEncPer; ++j) {
@@ -782,14 +871,23 @@ static void encode_stream(const T *vals, uint64_t n, const StreamDesc *desc, con
   unsigned gt = (unsigned)std::min<unsigned long long>((chunks + 255) / 256, 4ull * sms);
   note_launch();
   k_chunk_table<<<gt, 256, 0, s>>>(chunk_off, desc, out, summary);
-  unsigned ge = (unsigned)std::min<unsigned long long>((chunks + kEncWarps - 1) / kEncWarps, 2ull * sms);
   static const bool attr =  // once per instantiation, thread-safe
       cudaFuncSetAttribute(k_huff_encode<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)kEncSmem) == cudaSuccess;
   (void)attr;
+  // stages sized for this chunk size: more CTAs fit an SM for small chunks
+  const size_t esmem =
+      sizeof(uint32_t) * ((size_t)kEncWarps * enc_stage_words(log2_chunk) + kAlpha);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_huff_encode<T>, 32 * kEncWarps,
+                                                    esmem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  unsigned ge = (unsigned)std::min<unsigned long long>((chunks + kEncWarps - 1) / kEncWarps,
+                                                       (unsigned long long)per_sm * sms);
   note_launch();
-  k_huff_encode<T><<<ge, 32 * kEncWarps, kEncSmem, s>>>(vals, desc, codes, lens, log2_chunk,
-                                                         chunk_off, out, summary);
+  k_huff_encode<T><<<ge, 32 * kEncWarps, esmem, s>>>(vals, desc, codes, lens, log2_chunk,
+                                                     chunk_off, out, summary);
 }
 
 void launch_encode_u64(const unsigned long long *vals, uint64_t n, const StreamDesc *desc,

@@ -160,6 +160,18 @@ def test_status_codes(ctx, lcp):
     with pytest.raises(lcp.LcpError) as ei:
         ctx.compress(to_dev(Xf), 1e-3, out=out)
     assert ei.value.status == lcp.ERR_CAPACITY
+    # decompression into a buffer of a given number of values (no header read
+    # by the caller): one value short is refused, the exact size decodes
+    buf = ctx.compress(to_dev(Xf), 1e-3)["bytes"]
+    short = torch.full((3 * 10000 - 1,), -7.0, dtype=torch.float32, device="cuda")
+    with pytest.raises(lcp.LcpError) as ei:
+        ctx.decompress(buf, out=short)
+    assert ei.value.status == lcp.ERR_CAPACITY
+    assert bool((short == -7.0).all())  # nothing written
+    exact = torch.empty((3 * 10000,), dtype=torch.float32, device="cuda")
+    y = ctx.decompress(buf, out=exact)
+    assert tuple(y.shape) == (3, 10000)
+    assert torch.equal(y, ctx.decompress(buf))
 
 
 def test_block_size_autotune_matches_oracle(ctx, orc):
