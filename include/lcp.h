@@ -142,6 +142,25 @@ LCP_API lcp_status lcp_decompress_into(lcp_ctx *ctx, lcp_traj *traj, const void 
                                        uint64_t *n_out, uint32_t *d_fields, void *stream);
 
 /*
+ * Host-buffer variants of lcp_compress and lcp_decompress_into: the frame
+ * h_fields [d][n] (compress) or the container h_in (decompress) is in host
+ * memory, and so is the result (h_out: out_cap bytes of container, or
+ * out_values floats of frame).  The library copies the input to the device,
+ * makes the device call and copies the result back, all on `stream`; the
+ * device copies live in the context's workspace (grown on demand, kept).
+ * Host memory should be pinned (cudaHostAlloc / cudaHostRegister) for full
+ * copy speed; pageable memory works but is staged by the driver.  Statuses
+ * as for the device calls; synchronizes `stream`.
+ */
+LCP_API lcp_status lcp_compress_host(lcp_ctx *ctx, lcp_traj *traj, const float *h_fields,
+                                     uint64_t n, uint32_t d, double eb, lcp_eb_mode mode,
+                                     uint32_t p, lcp_method method, void *h_out, size_t out_cap,
+                                     size_t *out_size, lcp_method *chosen, void *stream);
+LCP_API lcp_status lcp_decompress_host(lcp_ctx *ctx, lcp_traj *traj, const void *h_in,
+                                       size_t in_size, float *h_out, uint64_t out_values,
+                                       uint64_t *n_out, uint32_t *d_fields, void *stream);
+
+/*
  * Random-access retrieval (Sec. "Spatial-Anchor-Frame-Based Batch
  * Compression", its recursive decompression): frames first..last of one
  * trajectory, decoded into d_outs[0 .. last - first] ([d][n_cap] each).

@@ -52,6 +52,7 @@ struct Workspace {
       tables, chunk_bits, chunk_off, outl_idx, summary, q_in, q_slot, perm, sym, patch_s,
       patch_i, patch_x, patch_s2, patch_i2, patch_so, patch_io, dec_fields, hufft, err,
       scan_tmp, cand, tq, fplan, fstatus, cbwork, sample, rq, lut, sbounds;
+  DevBuf host_in, host_out;  // device copies for the host-buffer entry points
 };
 
 __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
@@ -1546,6 +1547,66 @@ lcp_status lcp_decompress(lcp_ctx *c, lcp_traj *traj, const void *d_in, size_t i
   prof_reset(c);
   return (lcp_status)decompress_impl(c, traj, (const uint8_t *)d_in, in_size, d_out, n_cap, n_out,
                                      d_fields, (cudaStream_t)stream);
+}
+
+lcp_status lcp_compress_host(lcp_ctx *c, lcp_traj *traj, const float *h_fields, uint64_t n,
+                             uint32_t d, double eb, lcp_eb_mode mode, uint32_t p,
+                             lcp_method method, void *h_out, size_t out_cap, size_t *out_size,
+                             lcp_method *chosen, void *stream) {
+  if (!c || !out_size || (n > 0 && !h_fields) || !h_out || d < 1 || d > kMaxD) return LCP_ERR_ARG;
+  *out_size = 0;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace &w = c->ws;
+  const size_t fb = (size_t)std::max<uint64_t>(n, 1) * d * 4;
+  if (grow(w.host_in, fb) != OK || grow(w.host_out, std::max<size_t>(out_cap, 16)) != OK)
+    return LCP_ERR_NOMEM;
+  if (n > 0 && cudaMemcpyAsync(w.host_in.p, h_fields, (size_t)n * d * 4, cudaMemcpyHostToDevice,
+                               s) != cudaSuccess) {
+    cudaGetLastError();
+    return LCP_ERR_CUDA;
+  }
+  lcp_status st = lcp_compress(c, traj, P<float>(w.host_in), n, d, eb, mode, p, method,
+                               w.host_out.p, out_cap, out_size, chosen, nullptr, stream);
+  if (st != LCP_OK) return st;
+  if (cudaMemcpyAsync(h_out, w.host_out.p, *out_size, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return LCP_ERR_CUDA;
+  }
+  return LCP_OK;
+}
+
+lcp_status lcp_decompress_host(lcp_ctx *c, lcp_traj *traj, const void *h_in, size_t in_size,
+                               float *h_out, uint64_t out_values, uint64_t *n_out,
+                               uint32_t *d_fields, void *stream) {
+  if (!c || !h_in || !h_out) return LCP_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace &w = c->ws;
+  if (grow(w.host_in, std::max<size_t>(in_size, 16)) != OK ||
+      grow(w.host_out, (size_t)std::max<uint64_t>(out_values, 4) * 4) != OK)
+    return LCP_ERR_NOMEM;
+  if (cudaMemcpyAsync(w.host_in.p, h_in, in_size, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    cudaGetLastError();
+    return LCP_ERR_CUDA;
+  }
+  uint64_t no = 0;
+  uint32_t dd = 0;
+  lcp_status st = lcp_decompress_into(c, traj, w.host_in.p, in_size, P<float>(w.host_out),
+                                      out_values, &no, &dd, stream);
+  if (n_out) *n_out = no;
+  if (d_fields) *d_fields = dd;
+  if (st != LCP_OK) return st;
+  if (cudaMemcpyAsync(h_out, w.host_out.p, (size_t)no * dd * 4, cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return LCP_ERR_CUDA;
+  }
+  return LCP_OK;
 }
 
 lcp_status lcp_decompress_into(lcp_ctx *c, lcp_traj *traj, const void *d_in, size_t in_size,

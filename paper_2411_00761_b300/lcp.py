@@ -36,6 +36,11 @@ SIGNATURES = {
                                  _vp]),
     "lcp_decompress_into": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _u64, C.POINTER(_u64),
                                       C.POINTER(_u32), _vp]),
+    "lcp_compress_host": (C.c_int, [_vp, _vp, _vp, _u64, _u32, C.c_double, C.c_int, _u32,
+                                    C.c_int, _vp, _sz, C.POINTER(_sz), C.POINTER(C.c_int),
+                                    _vp]),
+    "lcp_decompress_host": (C.c_int, [_vp, _vp, _vp, _sz, _vp, _u64, C.POINTER(_u64),
+                                      C.POINTER(_u32), _vp]),
     "lcp_peek": (C.c_int, [_vp, _sz, C.POINTER(_u64), C.POINTER(_u32), C.POINTER(C.c_int),
                            C.POINTER(_u32), _vp]),
     "lcp_select": (C.c_int, [_vp, _vp, _vp, _u64, _u32, C.c_double, C.c_int, C.POINTER(C.c_int),
@@ -259,6 +264,44 @@ class Context:
                                       size, _ptr(out), out.numel(), C.byref(nn), C.byref(dd),
                                       _stream(stream))
         _check(st, "lcp_decompress")
+        n, d = nn.value, dd.value
+        return out.view(-1)[: d * n].view(d, n)
+
+    def compress_host(self, X: torch.Tensor, eb: float, mode="abs", p: int = 8,
+                      method="spatial", traj: "Trajectory | None" = None,
+                      out: torch.Tensor | None = None, stream=None) -> dict:
+        """lcp_compress_host: X [d, n] float32 in host memory (pinned for full
+        speed), the container into the host uint8 tensor out."""
+        assert not X.is_cuda and X.dtype == torch.float32 and X.dim() == 2 and X.is_contiguous()
+        d, n = X.shape
+        if out is None:
+            out = torch.empty(max_compressed_size(n, d), dtype=torch.uint8)
+        assert not out.is_cuda and out.dtype == torch.uint8
+        size = C.c_size_t(0)
+        chosen = C.c_int(0)
+        st = _lib.lcp_compress_host(self.h, traj.h if traj is not None else None, X.data_ptr(), n,
+                                    d, float(eb), _mode(mode), p, _method(method),
+                                    out.data_ptr(), out.numel(), C.byref(size), C.byref(chosen),
+                                    _stream(stream))
+        _check(st, "lcp_compress_host")
+        return dict(bytes=out[: size.value], size=size.value,
+                    method="temporal" if chosen.value == TEMPORAL else "spatial")
+
+    def decompress_host(self, buf: torch.Tensor, size: int | None = None,
+                        traj: "Trajectory | None" = None, out: torch.Tensor | None = None,
+                        stream=None) -> torch.Tensor:
+        """lcp_decompress_host: a container in host memory decoded into the
+        host float32 tensor out (capacity out.numel() values)."""
+        assert not buf.is_cuda and buf.dtype == torch.uint8
+        assert out is not None and not out.is_cuda and out.dtype == torch.float32
+        assert out.is_contiguous()
+        size = buf.numel() if size is None else size
+        nn = C.c_uint64(0)
+        dd = C.c_uint32(0)
+        st = _lib.lcp_decompress_host(self.h, traj.h if traj is not None else None,
+                                      buf.data_ptr(), size, out.data_ptr(), out.numel(),
+                                      C.byref(nn), C.byref(dd), _stream(stream))
+        _check(st, "lcp_decompress_host")
         n, d = nn.value, dd.value
         return out.view(-1)[: d * n].view(d, n)
 

@@ -172,6 +172,12 @@ def test_status_codes(ctx, lcp):
     y = ctx.decompress(buf, out=exact)
     assert tuple(y.shape) == (3, 10000)
     assert torch.equal(y, ctx.decompress(buf))
+    # host-buffer entry points: the same container and the same frame
+    Xh = torch.from_numpy(np.ascontiguousarray(Xf)).pin_memory()
+    rh = ctx.compress_host(Xh, 1e-3)
+    assert bytes(rh["bytes"].numpy()) == bytes(buf.cpu().numpy())
+    yh = ctx.decompress_host(rh["bytes"].clone(), out=torch.empty(3 * 10000).pin_memory())
+    assert torch.equal(yh, y.cpu())
 
 
 def test_block_size_autotune_matches_oracle(ctx, orc):
