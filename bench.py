@@ -299,7 +299,9 @@ def run_reference_batched(args):
     of the multi-frame workload: the next frame of the smallest trajectory."""
     from oracle import hybrid
     from paper_2411_00761_b300 import synth
-    w = WORKLOADS["batched"]
+    w = dict(WORKLOADS["batched"])
+    if args.lanes > 0:
+        w["lanes"] = args.lanes
     sizes = synth.trajectory_sizes(w["trajectories"], 1e4, 4e6, w["seed"])
     k = int(np.argmin(sizes))
     steps = args.warmup + args.steps
@@ -629,7 +631,9 @@ def run_serving(args):
     if world > 1:  # independent replicas; only the totals are combined
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    w = WORKLOADS["serving"]
+    w = dict(WORKLOADS["serving"])
+    if args.lanes > 0:
+        w["lanes"] = args.lanes
     seconds = w["seconds"] if args.seconds <= 0 else args.seconds
     rate = w["rate"] if args.rate <= 0 else args.rate
     max_pending = 1024  # producers shed load beyond this many unanswered requests
@@ -809,6 +813,7 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override the particle count (small cases)")
     ap.add_argument("--seconds", type=float, default=0.0, help="serving: measured seconds")
     ap.add_argument("--rate", type=float, default=0.0, help="serving: offered requests/s")
+    ap.add_argument("--lanes", type=int, default=0, help="batched / serving: lanes (contexts)")
     args = ap.parse_args()
     if args.n:
         WORKLOADS[args.workload]["n"] = args.n

@@ -66,20 +66,36 @@ __global__ void __launch_bounds__(kCbThreads) k_cb_build(const uint32_t *__restr
     s_maxlen = 0;
   }
   __syncthreads();
+  // the used symbols' (weight, symbol) keys, gathered in any order (the sort
+  // below orders them; the keys are distinct)
   for (int i = threadIdx.x; i < kAlpha; i += blockDim.x) {
     const unsigned long long c = n ? h[i] : 0u;
     const unsigned long long wk = (c + (1ull << k) - 1ull) >> k;
-    sk[i] = c ? ((wk << 12) | (unsigned long long)i) : ~0ull;
-    if (c) atomicAdd(&s_U, 1);
+    if (c) sk[atomicAdd(&s_U, 1)] = (wk << 12) | (unsigned long long)i;
   }
   __syncthreads();
   const int U = s_U;
   if (U <= 1) {
-    for (int i = threadIdx.x; i < kAlpha; i += blockDim.x) lens[i] = sk[i] != ~0ull ? 1 : 0;
-    if (threadIdx.x == 0) maxlen_k[s * kHalvings + k] = (uint32_t)U;
+    for (int i = threadIdx.x; i < kAlpha; i += blockDim.x) lens[i] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (U == 1) lens[sk[0] & 4095ull] = 1;
+      maxlen_k[s * kHalvings + k] = (uint32_t)U;
+    }
     return;
   }
-  bitonic_sort_u64(sk, kAlpha);
+  // k > 0 matters only when some code exceeds kLmax bits, impossible with at
+  // most kLmax + 1 symbols (depth <= U - 1)
+  if (k > 0 && U <= kLmax + 1) {
+    if (threadIdx.x == 0) maxlen_k[s * kHalvings + k] = 0xffffffffu;
+    return;
+  }
+  // sort the next power of two at or above U (padding sorts last)
+  int P2 = 2;
+  while (P2 < U) P2 <<= 1;
+  for (int i = U + threadIdx.x; i < P2; i += blockDim.x) sk[i] = ~0ull;
+  __syncthreads();
+  bitonic_sort_u64(sk, P2);
   constexpr uint32_t kInf = 0xffffffffu;  // above every weight (U >= 2: each < n < 2^32)
   for (int i = threadIdx.x; i < 2 * U - 1; i += blockDim.x)
     nodew[i] = i < U ? (uint32_t)(sk[i] >> 12) : kInf;  // internal nodes not made yet
