@@ -39,6 +39,35 @@ __global__ void k_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan) {
   }
 }
 
+// The bytes the host reads before decoding, gathered into one small buffer
+// so that a single copy (and synchronization) brings them over: the fixed
+// header with its field table and section directory (kHeadBytes, or the
+// container if shorter) and the 32-byte header of each stream section the
+// directory names (zeros where a section lies outside the container).
+__global__ void k_head_gather(const uint8_t *__restrict__ in, uint64_t in_size,
+                              uint8_t *__restrict__ stage) {
+  const uint32_t t = threadIdx.x;
+  const uint64_t head = in_size < (uint64_t)kHeadBytes ? in_size : (uint64_t)kHeadBytes;
+  for (uint32_t i = t; i < (uint32_t)kHeadBytes; i += blockDim.x) stage[i] = i < head ? in[i] : 0;
+  if (head < 48) return;
+  const uint32_t method = in[5], d = in[6];
+  if (d < 1 || d > kMaxD || method > 1) return;
+  const uint32_t ns = method == 0 ? 3u : 1u;
+  for (uint32_t k = 0; k < ns; ++k) {
+    const uint64_t at = 48ull + 16ull * d + 16ull * k;
+    uint64_t off = 0;
+    for (int b = 7; b >= 0; --b) off = (off << 8) | in[at + b];
+    const bool ok = (off & 15) == 0 && off + 32 <= in_size;
+    for (uint32_t i = t; i < 32; i += blockDim.x)
+      stage[kHeadBytes + 32 * k + i] = ok ? in[off + i] : 0;
+  }
+}
+
+void launch_head_gather(const uint8_t *in, uint64_t in_size, uint8_t *stage, cudaStream_t s) {
+  note_launch();
+  k_head_gather<<<1, 64, 0, s>>>(in, in_size, stage);
+}
+
 void launch_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan, cudaStream_t s) {
   note_launch();
   k_decode_plan<<<1, 32, 0, s>>>(df, d, plan);

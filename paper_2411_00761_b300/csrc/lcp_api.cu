@@ -53,6 +53,7 @@ struct Workspace {
       patch_i, patch_x, patch_s2, patch_i2, patch_so, patch_io, dec_fields, hufft, err,
       scan_tmp, cand, tq, fplan, fstatus, cbwork, sample, rq, lut, sbounds;
   DevBuf host_in, host_out;  // device copies for the host-buffer entry points
+  DevBuf hstage;             // container header bytes gathered for one copy
 };
 
 __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
@@ -1295,9 +1296,13 @@ int read_header(lcp_ctx *c, const uint8_t *in, size_t in_size, Header &h, cudaSt
   if (!in || !aligned16(in) || in_size < 48) return ERR_FORMAT;
   uint8_t *st = c->h_stage;
   // the fixed header with the largest field table and directory (8 fields, 4
-  // sections): one copy
-  const size_t head = std::min<size_t>(in_size, 48 + 16 * 8 + 16 * 4 + 16);
-  CK(cudaMemcpyAsync(st, in, head, cudaMemcpyDeviceToHost, s));
+  // sections) and the stream section headers it names, gathered on the
+  // device: one copy, one synchronization
+  const size_t head = std::min<size_t>(in_size, (size_t)kHeadBytes);
+  TRY(grow(c->ws.hstage, kHeadStage));
+  launch_head_gather(in, in_size, P<uint8_t>(c->ws.hstage), s);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(st, c->ws.hstage.p, kHeadStage, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (st[0] != 'L' || st[1] != 'C' || st[2] != 'P' || st[3] != '1' || st[4] != 1) return ERR_FORMAT;
   h.method = st[5];
@@ -1336,13 +1341,10 @@ int read_header(lcp_ctx *c, const uint8_t *in, size_t in_size, Header &h, cudaSt
   } else {
     if (h.bytes[1] != pad16(8ull * h.K) + pad16(4ull * h.K) || h.K > h.n * h.d) return ERR_FORMAT;
   }
-  for (int k = 0; k < h.ns; ++k) {
+  for (int k = 0; k < h.ns; ++k)
     if (h.bytes[k] < 32) return ERR_FORMAT;
-    CK(cudaMemcpyAsync(st + 4096 + 32 * k, in + h.off[k], 32, cudaMemcpyDeviceToHost, s));
-  }
-  CK(cudaStreamSynchronize(s));
   for (int k = 0; k < h.ns; ++k) {
-    const uint8_t *sh = st + 4096 + 32 * k;
+    const uint8_t *sh = st + kHeadBytes + 32 * k;
     StreamInfo &I = h.si[k];
     I.coder = sh[0];
     I.width = sh[1];

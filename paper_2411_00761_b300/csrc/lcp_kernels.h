@@ -234,6 +234,12 @@ void launch_requant(const Plan *plan, uint64_t n, uint32_t d, const int32_t *qre
                     const RefGrid &g, int32_t *qout, int sms, cudaStream_t s);
 
 // --- decode (k_decode.cu) --------------------------------------------------
+// container bytes the host needs before decoding, gathered on the device:
+// [0, kHeadBytes) the fixed header, field table and section directory, then
+// 32 bytes per stream section header (up to 3)
+constexpr int kHeadBytes = 48 + 16 * kMaxD + 16 * 4 + 16;
+constexpr int kHeadStage = kHeadBytes + 3 * 32;
+void launch_head_gather(const uint8_t *in, uint64_t in_size, uint8_t *stage, cudaStream_t s);
 void launch_decode_plan(const DecodeFields *df, uint32_t d, Plan *plan, cudaStream_t s);
 void launch_huff_table(const uint8_t *sec, HuffTable *T, cudaStream_t s);
 // decodes ns streams (secs[k], infos[k]) into outs[k] (8-byte values when
