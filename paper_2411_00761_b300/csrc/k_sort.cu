@@ -1709,22 +1709,33 @@ __global__ void __launch_bounds__(512) k_blocks_map(const Plan *__restrict__ pla
   const uint64_t M = *mcount;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   unsigned long long x0 = 0ull, x1 = 0ull;
-  // trip count uniform across the warp (ballots below)
+  // trip count uniform across the warp (ballots below); the next round's
+  // positions and ids are loaded before this round's are used
   const uint64_t iters = (M + stride - 1) / stride;
+  const uint64_t g0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t np = 0u, npn = 0u, npp = 0u;
+  unsigned long long nb = 0ull, nbp = 0ull;
+  auto fetch = [&](uint64_t B) {
+    if (B < M) {
+      np = bpos[B];
+      npn = bpos[B + 1];
+      nb = bidv[B];
+      npp = B > 0 ? bpos[B - 1] : 0u;
+      nbp = B > 0 ? bidv[B - 1] : 0ull;
+    }
+  };
+  fetch(g0);
   for (uint64_t it = 0; it < iters; ++it) {
-    const uint64_t B = it * stride + (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t B = it * stride + g0;
     const bool valid = B < M;
+    const uint32_t p = np, pn = npn, pp = npp;
+    const unsigned long long bid = nb, pbid = nbp;
+    fetch(B + stride);
     unsigned long long v0 = 0ull, v1 = 0ull;
     if (valid) {
-      const uint32_t p = bpos[B], pn = bpos[B + 1];
       const long long c = (long long)(pn - p);
-      unsigned long long pbid = 0ull;
-      long long pc = 0;
-      if (B > 0) {
-        pbid = bidv[B - 1];
-        pc = (long long)(p - bpos[B - 1]);
-      }
-      v0 = bidv[B] - pbid;
+      const long long pc = B > 0 ? (long long)(p - pp) : 0ll;
+      v0 = bid - pbid;
       v1 = zigzag(c - pc);
       s_id[B] = v0;
       s_cnt[B] = v1;
