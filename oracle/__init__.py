@@ -103,6 +103,12 @@ def _declare(L):
                            C.POINTER(_FieldPlan)]
     L.orc_decompress.restype = C.c_int
     L.orc_decompress.argtypes = [_u8p, C.c_size_t, _i32p, _fp, C.c_uint64, _i32p]
+    L.orc_dict_max_size.restype = C.c_size_t
+    L.orc_dict_max_size.argtypes = [C.c_uint64]
+    L.orc_dict_compress.restype = C.c_int
+    L.orc_dict_compress.argtypes = [_u8p, C.c_uint64, _u8p, C.c_size_t, _szp]
+    L.orc_dict_decompress.restype = C.c_int
+    L.orc_dict_decompress.argtypes = [_u8p, C.c_size_t, _u8p, C.c_size_t, _szp]
 
 
 def _ptr(a, t):
@@ -264,3 +270,34 @@ def decompress(buf: bytes, ref_q=None) -> tuple[np.ndarray, np.ndarray]:
     if st != OK:
         raise OracleError(st, "decompress")
     return out[:, :n], q[:, :n]
+
+
+def dict_max_size(raw_bytes: int) -> int:
+    """Size of the LCPZ image when every chunk is stored (lcp_oracle.h)."""
+    return int(lib().orc_dict_max_size(raw_bytes))
+
+
+def dict_compress(raw: bytes) -> bytes:
+    """The dictionary stage (Sec. "Block coding", its last step): the LCPZ
+    image of a byte string, normally a container."""
+    b = np.frombuffer(raw, dtype=np.uint8)
+    out = np.zeros(dict_max_size(b.size), dtype=np.uint8)
+    sz = np.zeros(1, dtype=np.uint64)
+    st = lib().orc_dict_compress(_ptr(b, _u8p) if b.size else None, b.size, _ptr(out, _u8p),
+                                 out.size, sz.ctypes.data_as(_szp))
+    if st != OK:
+        raise OracleError(st, "dict_compress")
+    return out[:int(sz[0])].tobytes()
+
+
+def dict_decompress(img: bytes) -> bytes:
+    """Inverse of dict_compress."""
+    b = np.frombuffer(img, dtype=np.uint8)
+    raw = int(np.frombuffer(img[8:16], dtype="<u8")[0]) if b.size >= 16 else 0
+    out = np.zeros(max(raw, 1), dtype=np.uint8)
+    sz = np.zeros(1, dtype=np.uint64)
+    st = lib().orc_dict_decompress(_ptr(b, _u8p), b.size, _ptr(out, _u8p), raw,
+                                   sz.ctypes.data_as(_szp))
+    if st != OK:
+        raise OracleError(st, "dict_decompress")
+    return out[:int(sz[0])].tobytes()

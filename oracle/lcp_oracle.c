@@ -979,3 +979,238 @@ int orc_decompress(const uint8_t *in, size_t in_size, const int32_t *ref_q, floa
   free(sym);
   return st;
 }
+
+/* ======================================================================== */
+/* Dictionary stage (Sec. "Block coding": dictionary coding is the last     */
+/* step of the encoding stage).  The paper uses Zstd; this is an LZ77-style */
+/* coder with the LCPZ layout:                                              */
+/*   0  "LCPZ", u8 version 1, u8 log2 chunk (16), u16 0                     */
+/*   8  u64 raw bytes S, 16 u64 chunks C = ceil(S / 2^16), 24 u64 total T   */
+/*   32 the first min(S, 48) raw bytes, zero padded to 48 (a preview of the */
+/*      container header)                                                   */
+/*   80 u32 per chunk: its coded bytes, bit 31 set when stored raw          */
+/*   pad16, then the chunks back to back, pad16 to T.                       */
+/* A coded chunk is a list of sequences: a token byte (literal count in the */
+/* high nibble, copy length - 4 in the low one, 15 meaning "add the         */
+/* extension": bytes 255 ... 255 r summed), the extension of the literal    */
+/* count, the literals, then, unless the chunk is complete after the        */
+/* literals, a u16 copy offset and the extension of the copy length.        */
+/* Parity status: pinned by hand-worked byte strings and closed forms.      */
+/* ======================================================================== */
+#define DICT_CHUNK (1u << ORC_DICT_LOG2_CHUNK)
+#define DICT_NONE 0xffffffffu
+
+size_t orc_dict_max_size(uint64_t raw_bytes) {
+  uint64_t c = (raw_bytes + DICT_CHUNK - 1) >> ORC_DICT_LOG2_CHUNK;
+  return (size_t)pad16(pad16(ORC_DICT_HEAD + 4 * c) + raw_bytes);
+}
+
+/* the four bytes at x as a little-endian word, multiplied by 2654435761
+ * (Knuth's multiplicative hash) modulo 2^32, top 12 bits */
+static uint32_t dict_hash(const uint8_t *x) {
+  uint32_t w = (uint32_t)x[0] | ((uint32_t)x[1] << 8) | ((uint32_t)x[2] << 16) |
+               ((uint32_t)x[3] << 24);
+  return (uint32_t)(w * 2654435761u) >> 20;
+}
+
+static uint64_t dict_ext_bytes(uint64_t v) { return v >= 15 ? (v - 15) / 255 + 1 : 0; }
+
+static uint64_t dict_put_ext(uint8_t *o, uint64_t v) {
+  uint64_t k = 0;
+  v -= 15;
+  while (v >= 255) {
+    o[k++] = 255;
+    v -= 255;
+  }
+  o[k++] = (uint8_t)v;
+  return k;
+}
+
+/* one sequence; ml = 0 for the literal-only last one.  Returns its size and
+ * writes it when o is non-null. */
+static uint64_t dict_sequence(uint8_t *o, const uint8_t *lit, uint64_t ll, uint64_t off,
+                              uint64_t ml) {
+  uint64_t sz = 1 + dict_ext_bytes(ll) + ll + (ml ? 2 + dict_ext_bytes(ml - 4) : 0);
+  if (!o) return sz;
+  uint64_t k = 0;
+  o[k++] = (uint8_t)(((ll < 15 ? ll : 15) << 4) | (ml ? (ml - 4 < 15 ? ml - 4 : 15) : 0));
+  if (ll >= 15) k += dict_put_ext(o + k, ll);
+  memcpy(o + k, lit, ll);
+  k += ll;
+  if (ml) {
+    o[k++] = (uint8_t)(off & 0xff);
+    o[k++] = (uint8_t)(off >> 8);
+    if (ml - 4 >= 15) k += dict_put_ext(o + k, ml - 4);
+  }
+  return k;
+}
+
+/* codes x[0..m) into o (room for m bytes); returns the coded size, or m
+ * when the coding is not strictly shorter (the chunk is then stored) */
+static uint64_t dict_chunk(const uint8_t *x, uint64_t m, uint8_t *o) {
+  uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * (m ? m : 1));
+  uint32_t table[4096];
+  for (int h = 0; h < 4096; h++) table[h] = DICT_NONE;
+  /* every position with four bytes left enters the table in order; its
+   * candidate is the table entry just before it enters */
+  for (uint64_t i = 0; i < m; i++) {
+    cand[i] = DICT_NONE;
+    if (i + 4 <= m) {
+      uint32_t h = dict_hash(x + i);
+      cand[i] = table[h];
+      table[h] = (uint32_t)i;
+    }
+  }
+  /* greedy parse: a copy wherever the candidate agrees on >= 4 bytes */
+  uint64_t size = 0, p = 0, lit = 0;
+  int stored = 0;
+  while (p < m && !stored) {
+    uint64_t len = 0;
+    if (cand[p] != DICT_NONE) {
+      uint64_t j = cand[p];
+      while (p + len < m && x[j + len] == x[p + len]) len++;
+    }
+    if (len < 4) {
+      p++;
+      continue;
+    }
+    uint64_t sz = dict_sequence(NULL, x + lit, p - lit, p - cand[p], len);
+    if (size + sz >= m) {
+      stored = 1;
+      break;
+    }
+    dict_sequence(o + size, x + lit, p - lit, p - cand[p], len);
+    size += sz;
+    p += len;
+    lit = p;
+  }
+  if (!stored && lit < m) {
+    uint64_t sz = dict_sequence(NULL, x + lit, m - lit, 0, 0);
+    if (size + sz >= m)
+      stored = 1;
+    else {
+      dict_sequence(o + size, x + lit, m - lit, 0, 0);
+      size += sz;
+    }
+  }
+  free(cand);
+  return stored ? m : size;
+}
+
+int orc_dict_compress(const uint8_t *in, uint64_t in_size, uint8_t *out, size_t out_cap,
+                      size_t *out_size) {
+  if ((!in && in_size) || !out_size) return ORC_ERR_ARG;
+  const uint64_t C = (in_size + DICT_CHUNK - 1) >> ORC_DICT_LOG2_CHUNK;
+  const uint64_t p0 = pad16(ORC_DICT_HEAD + 4 * C);
+  uint8_t *tmp = (uint8_t *)malloc(DICT_CHUNK);
+  uint32_t *sz = (uint32_t *)malloc(sizeof(uint32_t) * (C ? C : 1));
+  uint8_t *body = (uint8_t *)malloc(in_size ? in_size : 1);
+  if (!tmp || !sz || !body) {
+    free(tmp);
+    free(sz);
+    free(body);
+    return ORC_ERR_NOMEM;
+  }
+  uint64_t at = 0;
+  for (uint64_t k = 0; k < C; k++) {
+    const uint8_t *x = in + (k << ORC_DICT_LOG2_CHUNK);
+    uint64_t m = in_size - (k << ORC_DICT_LOG2_CHUNK);
+    if (m > DICT_CHUNK) m = DICT_CHUNK;
+    uint64_t c = dict_chunk(x, m, tmp);
+    if (c == m) {
+      memcpy(body + at, x, m);
+      sz[k] = (uint32_t)m | 0x80000000u;
+    } else {
+      memcpy(body + at, tmp, c);
+      sz[k] = (uint32_t)c;
+    }
+    at += c;
+  }
+  const uint64_t total = pad16(p0 + at);
+  *out_size = (size_t)total;
+  int st = ORC_OK;
+  if (total > out_cap) {
+    st = ORC_ERR_CAPACITY;
+  } else {
+    memset(out, 0, total);
+    out[0] = 'L';
+    out[1] = 'C';
+    out[2] = 'P';
+    out[3] = 'Z';
+    out[4] = 1;
+    out[5] = ORC_DICT_LOG2_CHUNK;
+    st64(out + 8, in_size);
+    st64(out + 16, C);
+    st64(out + 24, total);
+    memcpy(out + 32, in, in_size < 48 ? in_size : 48);
+    for (uint64_t k = 0; k < C; k++) st32(out + ORC_DICT_HEAD + 4 * k, sz[k]);
+    memcpy(out + p0, body, at);
+  }
+  free(tmp);
+  free(sz);
+  free(body);
+  return st;
+}
+
+/* reads an extension (255 ... 255 r) at in[*q], below end */
+static int dict_get_ext(const uint8_t *in, uint64_t *q, uint64_t end, uint64_t *v) {
+  for (;;) {
+    if (*q >= end) return ORC_ERR_FORMAT;
+    uint8_t b = in[(*q)++];
+    *v += b;
+    if (b != 255) return ORC_OK;
+  }
+}
+
+int orc_dict_decompress(const uint8_t *in, size_t in_size, uint8_t *out, size_t out_cap,
+                        size_t *out_size) {
+  if (!in || !out_size || in_size < ORC_DICT_HEAD) return ORC_ERR_FORMAT;
+  if (in[0] != 'L' || in[1] != 'C' || in[2] != 'P' || in[3] != 'Z' || in[4] != 1 ||
+      in[5] != ORC_DICT_LOG2_CHUNK)
+    return ORC_ERR_FORMAT;
+  const uint64_t S = ld64(in + 8), C = ld64(in + 16), T = ld64(in + 24);
+  if (C != (S + DICT_CHUNK - 1) >> ORC_DICT_LOG2_CHUNK || T > in_size) return ORC_ERR_FORMAT;
+  const uint64_t p0 = pad16(ORC_DICT_HEAD + 4 * C);
+  if (p0 > T) return ORC_ERR_FORMAT;
+  *out_size = (size_t)S;
+  if (S > out_cap) return ORC_ERR_CAPACITY;
+  uint64_t at = p0;
+  for (uint64_t k = 0; k < C; k++) {
+    uint32_t e = ld32(in + ORC_DICT_HEAD + 4 * k);
+    uint64_t c = e & 0x7fffffffu;
+    uint64_t m = S - (k << ORC_DICT_LOG2_CHUNK);
+    if (m > DICT_CHUNK) m = DICT_CHUNK;
+    if (c > T - at) return ORC_ERR_FORMAT;
+    uint8_t *y = out + (k << ORC_DICT_LOG2_CHUNK);
+    const uint64_t end = at + c;
+    if (e & 0x80000000u) {
+      if (c != m) return ORC_ERR_FORMAT;
+      memcpy(y, in + at, m);
+    } else {
+      uint64_t q = at, w = 0;
+      while (w < m) {
+        if (q >= end) return ORC_ERR_FORMAT;
+        uint8_t tok = in[q++];
+        uint64_t ll = tok >> 4, ml = tok & 15;
+        if (ll == 15 && dict_get_ext(in, &q, end, &ll)) return ORC_ERR_FORMAT;
+        if (ll > m - w || ll > end - q) return ORC_ERR_FORMAT;
+        memcpy(y + w, in + q, ll);
+        w += ll;
+        q += ll;
+        if (w == m) break;
+        if (end - q < 2) return ORC_ERR_FORMAT;
+        uint64_t off = (uint64_t)in[q] | ((uint64_t)in[q + 1] << 8);
+        q += 2;
+        if (ml == 15 && dict_get_ext(in, &q, end, &ml)) return ORC_ERR_FORMAT;
+        ml += 4;
+        if (off == 0 || off > w || ml > m - w) return ORC_ERR_FORMAT;
+        for (uint64_t t = 0; t < ml; t++) y[w + t] = y[w - off + t];  /* may overlap */
+        w += ml;
+      }
+      if (q != end) return ORC_ERR_FORMAT;
+    }
+    at = end;
+  }
+  if (pad16(at) != T) return ORC_ERR_FORMAT;
+  return ORC_OK;
+}

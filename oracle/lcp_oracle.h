@@ -102,6 +102,25 @@ int orc_peek(const uint8_t *in, size_t in_size, uint64_t *n, uint32_t *d, uint32
 int orc_decompress(const uint8_t *in, size_t in_size, const int32_t *ref_q, float *out,
                    uint64_t n_cap, int32_t *q_out);
 
+/* ---- dictionary stage (Sec. "Block coding", its last step) ------------- */
+/* The paper ends the encoding stage with a dictionary coder (Zstd).  This
+ * is the library's own LZ77-style coder of a byte string (normally a whole
+ * container), the "LCPZ" format written out in prose in the design notes:
+ * 2^16-byte chunks coded independently; per chunk a greedy parse in which
+ * position i may copy from the latest earlier position j of the chunk whose
+ * four bytes hash alike (every position enters the table, also those
+ * inside a copy), a copy being kept when at least four bytes agree; a chunk
+ * whose coding is not strictly shorter is stored as it is. */
+#define ORC_DICT_LOG2_CHUNK 16
+#define ORC_DICT_HEAD 80
+/* Size of the LCPZ image of raw_bytes bytes when every chunk is stored. */
+size_t orc_dict_max_size(uint64_t raw_bytes);
+int orc_dict_compress(const uint8_t *in, uint64_t in_size, uint8_t *out, size_t out_cap,
+                      size_t *out_size);
+/* out receives the raw bytes; *out_size their count (the header's). */
+int orc_dict_decompress(const uint8_t *in, size_t in_size, uint8_t *out, size_t out_cap,
+                        size_t *out_size);
+
 #ifdef __cplusplus
 }
 #endif
