@@ -234,7 +234,48 @@ LCP_API lcp_status lcp_tune_schedule(lcp_ctx *ctx, const float *d_fields, uint64
                              double eb, lcp_eb_mode mode, uint32_t p, double max_growth,
                              int reps, lcp_schedule *best, float *best_ms, void *stream);
 
-/* Reads n, d, method and flags from a container's header (device memory). */
+/*
+ * Dictionary stage (Sec. "Block coding": dictionary coding is the last step
+ * of the encoding stage; the paper uses Zstd).  The library's own LZ77-style
+ * coder turns a byte string -- normally a container -- into an "LCPZ" image:
+ *   - the input is cut into chunks of 2^16 bytes (the last one shorter),
+ *     each coded alone by one warp: a greedy parse that copies from the
+ *     latest earlier position whose four bytes hash alike when at least four
+ *     bytes agree, written as LZ4-like sequences (token, literals, u16
+ *     offset, length extensions); a chunk whose coding is not strictly
+ *     shorter is stored as it is;
+ *   - the image opens with an 80-byte header (magic "LCPZ", raw bytes S,
+ *     chunk count, total bytes, and a copy of the first 48 raw bytes so a
+ *     container's header stays readable), then one u32 size per chunk, then
+ *     the chunks.  Its size is at most lcp_dict_max_size(S).
+ * The layout is fixed and documented with the library; the bytes are a pure
+ * function of the input bytes.
+ *
+ * lcp_ctx_set_dict(ctx, 1) applies the stage after every lcp_compress /
+ * lcp_compress_host / lcp_compress_batch lane call of that context, keeping
+ * the image only when it is shorter than the container; the capacity rule of
+ * those calls is unchanged (out_cap must hold the container before the
+ * stage).  Every decompression entry point, lcp_peek and the random-access
+ * calls accept an image wherever a container is accepted, with or without
+ * the option (lcp_decompress_step decodes images one by one, not fused).
+ */
+LCP_API lcp_status lcp_ctx_set_dict(lcp_ctx *ctx, int on);
+LCP_API size_t lcp_dict_max_size(uint64_t raw_bytes);
+/* The image of d_in[0, in_size) into d_out (16-byte aligned, not overlapping
+ * d_in).  *out_size = the image's size, also on ERR_CAPACITY.  Synchronizes
+ * `stream` once (the size); the image is written asynchronously after it. */
+LCP_API lcp_status lcp_dict_compress(lcp_ctx *ctx, const void *d_in, size_t in_size, void *d_out,
+                                     size_t out_cap, size_t *out_size, void *stream);
+/* The raw bytes of an image (d_in 16-byte aligned) into d_out (out_cap
+ * bytes, not overlapping d_in).  *out_size = the raw size once the header is
+ * read (also on ERR_CAPACITY).  ERR_FORMAT for a malformed image: bad
+ * header, size table, token, offset or length.  Synchronizes `stream`. */
+LCP_API lcp_status lcp_dict_decompress(lcp_ctx *ctx, const void *d_in, size_t in_size,
+                                       void *d_out, size_t out_cap, size_t *out_size,
+                                       void *stream);
+
+/* Reads n, d, method and flags from a container's header (device memory);
+ * for an LCPZ image, from the container header it carries. */
 LCP_API lcp_status lcp_peek(const void *d_in, size_t in_size, uint64_t *n, uint32_t *d,
                     lcp_method *method, uint32_t *flags, void *stream);
 

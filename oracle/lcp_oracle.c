@@ -1187,6 +1187,7 @@ int orc_dict_decompress(const uint8_t *in, size_t in_size, uint8_t *out, size_t 
       if (c != m) return ORC_ERR_FORMAT;
       memcpy(y, in + at, m);
     } else {
+      if (c >= m) return ORC_ERR_FORMAT; /* a coded chunk is shorter than its bytes */
       uint64_t q = at, w = 0;
       while (w < m) {
         if (q >= end) return ORC_ERR_FORMAT;

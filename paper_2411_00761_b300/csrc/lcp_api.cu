@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/lcp.h"
+#include "lcp_dict.h"
 #include "lcp_kernels.h"
 
 using namespace lcp;
@@ -54,6 +55,9 @@ struct Workspace {
       scan_tmp, cand, tq, fplan, fstatus, cbwork, sample, rq, lut, sbounds;
   DevBuf host_in, host_out;  // device copies for the host-buffer entry points
   DevBuf hstage;             // container header bytes gathered for one copy
+  // dictionary stage: coded chunks, size table, chunk offsets, the image
+  // (compress) and the decoded container (decompress of an LCPZ image)
+  DevBuf dict_scratch, dict_sizes, dict_off, dict_img, dict_raw;
 };
 
 __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
@@ -141,6 +145,8 @@ struct lcp_ctx {
   // bytes)
   uint32_t log2_chunk = 10;
   int bucket_delta = 0;
+  // dictionary stage after every compression (lcp_ctx_set_dict)
+  bool dict = false;
   Workspace ws;
   Profile prof;
   Plan *h_plan = nullptr;
@@ -1030,6 +1036,120 @@ int traj_compress(lcp_ctx *c, lcp_traj *t, const float *X, uint64_t n, uint32_t 
   return OK;
 }
 
+// ---------------------------------------------------------------------------
+// dictionary stage (Sec. "Block coding", its last step): LCPZ images, see
+// lcp_dict.h
+// ---------------------------------------------------------------------------
+inline uint64_t le64(const uint8_t *p) {
+  uint64_t v;
+  memcpy(&v, p, 8);
+  return v;
+}
+
+bool overlap(const void *a, uint64_t na, const void *b, uint64_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return na && nb && x < y + nb && y < x + na;
+}
+
+// workspace for the image of up to S raw bytes
+int dict_reserve(lcp_ctx *c, uint64_t S) {
+  Workspace &w = c->ws;
+  const uint64_t C = dict_chunks(S);
+  TRY(grow(w.dict_scratch, S));
+  TRY(grow(w.dict_sizes, 4 * C));
+  TRY(grow(w.dict_off, 8 * (C + 1)));
+  TRY(grow(w.dict_img, dict_max_size(S)));
+  return OK;
+}
+
+// codes in[0, S) chunk by chunk; *T the image's size (one synchronization)
+int dict_encode(lcp_ctx *c, const uint8_t *in, uint64_t S, uint64_t *T, cudaStream_t s) {
+  Workspace &w = c->ws;
+  const uint64_t C = dict_chunks(S);
+  TRY(grow(w.dict_scratch, S));
+  TRY(grow(w.dict_sizes, 4 * C));
+  TRY(grow(w.dict_off, 8 * (C + 1)));
+  prof_begin(c, "dict.encode", s);
+  launch_dict_encode(in, S, P<uint8_t>(w.dict_scratch), P<uint32_t>(w.dict_sizes), c->sms, s);
+  CK(cudaGetLastError());
+  launch_dict_offsets(P<uint32_t>(w.dict_sizes), C, P<unsigned long long>(w.dict_off), s);
+  CK(cudaGetLastError());
+  prof_end(c, s);
+  CK(cudaMemcpyAsync(c->h_stage, P<unsigned long long>(w.dict_off) + C, 8,
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *T = pad16(le64(c->h_stage));
+  return OK;
+}
+
+// the image (T bytes) of in[0, S) after dict_encode, into out
+int dict_pack(lcp_ctx *c, const uint8_t *in, uint64_t S, uint64_t T, uint8_t *out,
+              cudaStream_t s) {
+  Workspace &w = c->ws;
+  prof_begin(c, "dict.pack", s);
+  launch_dict_pack(in, S, P<uint8_t>(w.dict_scratch), P<uint32_t>(w.dict_sizes),
+                   P<unsigned long long>(w.dict_off), T, out, c->sms, s);
+  CK(cudaGetLastError());
+  prof_end(c, s);
+  return OK;
+}
+
+// a container replaced in place by its image when that is shorter
+int dict_apply(lcp_ctx *c, uint8_t *buf, size_t *size, cudaStream_t s) {
+  const uint64_t S = *size;
+  uint64_t T = 0;
+  TRY(grow(c->ws.dict_img, dict_max_size(S)));
+  TRY(dict_encode(c, buf, S, &T, s));
+  if (T >= S) return OK;
+  TRY(dict_pack(c, buf, S, T, P<uint8_t>(c->ws.dict_img), s));
+  CK(cudaMemcpyAsync(buf, c->ws.dict_img.p, T, cudaMemcpyDeviceToDevice, s));
+  *size = T;
+  return OK;
+}
+
+// decodes an image into dst (dst_cap bytes), or into the workspace buffer
+// dict_raw when to_ws; *raw_size = the raw bytes (set once the header is read)
+int dict_decode(lcp_ctx *c, const uint8_t *in, size_t in_size, uint8_t *dst, uint64_t dst_cap,
+                uint64_t *raw_size, bool to_ws, cudaStream_t s) {
+  if (!in || !aligned16(in) || in_size < kDictHead) return ERR_FORMAT;
+  Workspace &w = c->ws;
+  uint8_t *st = c->h_stage;
+  CK(cudaMemcpyAsync(st, in, 32, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (st[0] != 'L' || st[1] != 'C' || st[2] != 'P' || st[3] != 'Z' || st[4] != 1 ||
+      st[5] != kDictLog2Chunk)
+    return ERR_FORMAT;
+  const uint64_t S = le64(st + 8), C = le64(st + 16), T = le64(st + 24);
+  if (C != dict_chunks(S) || T > in_size || dict_body(C) > T) return ERR_FORMAT;
+  *raw_size = S;
+  if (to_ws) {
+    TRY(grow(w.dict_raw, S));
+    dst = P<uint8_t>(w.dict_raw);
+  } else {
+    if (S > dst_cap) return ERR_CAPACITY;
+    if (S && !dst) return ERR_ARG;
+  }
+  TRY(grow(w.dict_off, 8 * (C + 1)));
+  TRY(grow(w.err, 8));
+  int *err = P<int>(w.err);
+  CK(cudaMemsetAsync(err, 0, 4, s));
+  prof_begin(c, "dict.decode", s);
+  launch_dict_offsets(reinterpret_cast<const uint32_t *>(in + kDictHead), C,
+                      P<unsigned long long>(w.dict_off), s);
+  CK(cudaGetLastError());
+  launch_dict_decode(in, in_size, S, T, P<unsigned long long>(w.dict_off), dst, err, c->sms, s);
+  CK(cudaGetLastError());
+  prof_end(c, s);
+  CK(cudaMemcpyAsync(c->h_err, err, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return *c->h_err ? ERR_FORMAT : OK;
+}
+
+int compress_entry(lcp_ctx *c, lcp_traj *traj, const float *d_fields, uint64_t n, uint32_t d,
+                   double eb, lcp_eb_mode mode, uint32_t p, lcp_method method, void *d_out,
+                   size_t out_cap, size_t *out_size, lcp_method *chosen, uint32_t *d_perm,
+                   cudaStream_t s);
+
 }  // namespace
 
 lcp_status lcp_compress(lcp_ctx *c, lcp_traj *traj, const float *d_fields, uint64_t n, uint32_t d,
@@ -1038,14 +1158,31 @@ lcp_status lcp_compress(lcp_ctx *c, lcp_traj *traj, const float *d_fields, uint6
                         void *stream) {
   if (!c || !out_size) return LCP_ERR_ARG;
   *out_size = 0;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the stage's workspace comes first: once a trajectory has taken the frame
+  // the call can no longer fail for memory
+  if (c->dict && d < 1 + (uint32_t)kMaxD &&
+      dict_reserve(c, std::min<uint64_t>(out_cap, lcp_max_compressed_size(n, d))) != OK)
+    return LCP_ERR_NOMEM;
+  int st = compress_entry(c, traj, d_fields, n, d, eb, mode, p, method, d_out, out_cap, out_size,
+                          chosen, d_perm, s);
+  if (st == OK && c->dict) st = dict_apply(c, (uint8_t *)d_out, out_size, s);
+  return (lcp_status)st;
+}
+
+namespace {
+
+int compress_entry(lcp_ctx *c, lcp_traj *traj, const float *d_fields, uint64_t n, uint32_t d,
+                   double eb, lcp_eb_mode mode, uint32_t p, lcp_method method, void *d_out,
+                   size_t out_cap, size_t *out_size, lcp_method *chosen, uint32_t *d_perm,
+                   cudaStream_t s) {
   int st = check_frame_args(d_fields, n, d, eb, mode);
   if (st != OK) return (lcp_status)st;
   if (!d_out || !aligned16(d_out)) return LCP_ERR_ARG;
   if (method != LCP_SPATIAL && method != LCP_TEMPORAL && method != LCP_AUTO) return LCP_ERR_ARG;
   if (!traj && method == LCP_TEMPORAL) return LCP_ERR_STATE;
-  DeviceGuard g(c->device);
-  if (!g.ok) return LCP_ERR_CUDA;
-  cudaStream_t s = (cudaStream_t)stream;
   prof_reset(c);
   if (traj) {
     int ch = LCP_SPATIAL;
@@ -1072,6 +1209,48 @@ lcp_status lcp_compress(lcp_ctx *c, lcp_traj *traj, const float *d_fields, uint6
                        nullptr, &total, s);
   *out_size = total;
   if (chosen) *chosen = LCP_SPATIAL;
+  return (lcp_status)st;
+}
+
+}  // namespace
+
+lcp_status lcp_ctx_set_dict(lcp_ctx *c, int on) {
+  if (!c) return LCP_ERR_ARG;
+  c->dict = on != 0;
+  return LCP_OK;
+}
+
+size_t lcp_dict_max_size(uint64_t raw_bytes) { return (size_t)dict_max_size(raw_bytes); }
+
+lcp_status lcp_dict_compress(lcp_ctx *c, const void *d_in, size_t in_size, void *d_out,
+                             size_t out_cap, size_t *out_size, void *stream) {
+  if (!c || !out_size || (in_size && !d_in) || !d_out || !aligned16(d_out)) return LCP_ERR_ARG;
+  *out_size = 0;
+  if (overlap(d_in, in_size, d_out, out_cap)) return LCP_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  prof_reset(c);
+  uint64_t T = 0;
+  int st = dict_encode(c, (const uint8_t *)d_in, in_size, &T, s);
+  if (st != OK) return (lcp_status)st;
+  *out_size = T;
+  if (T > out_cap) return LCP_ERR_CAPACITY;
+  return (lcp_status)dict_pack(c, (const uint8_t *)d_in, in_size, T, (uint8_t *)d_out, s);
+}
+
+lcp_status lcp_dict_decompress(lcp_ctx *c, const void *d_in, size_t in_size, void *d_out,
+                               size_t out_cap, size_t *out_size, void *stream) {
+  if (!c || !out_size) return LCP_ERR_ARG;
+  *out_size = 0;
+  if (overlap(d_in, in_size, d_out, out_cap)) return LCP_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok) return LCP_ERR_CUDA;
+  prof_reset(c);
+  uint64_t raw = 0;
+  int st = dict_decode(c, (const uint8_t *)d_in, in_size, (uint8_t *)d_out, out_cap, &raw, false,
+                       (cudaStream_t)stream);
+  *out_size = (size_t)raw;
   return (lcp_status)st;
 }
 
@@ -1292,6 +1471,9 @@ struct Header {
   int ns;
 };
 
+// read_header's answer for an LCPZ image (not a status)
+constexpr int kDictImage = 1;
+
 int read_header(lcp_ctx *c, const uint8_t *in, size_t in_size, Header &h, cudaStream_t s) {
   if (!in || !aligned16(in) || in_size < 48) return ERR_FORMAT;
   uint8_t *st = c->h_stage;
@@ -1304,6 +1486,7 @@ int read_header(lcp_ctx *c, const uint8_t *in, size_t in_size, Header &h, cudaSt
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(st, c->ws.hstage.p, kHeadStage, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (st[0] == 'L' && st[1] == 'C' && st[2] == 'P' && st[3] == 'Z') return kDictImage;
   if (st[0] != 'L' || st[1] != 'C' || st[2] != 'P' || st[3] != '1' || st[4] != 1) return ERR_FORMAT;
   h.method = st[5];
   h.d = st[6];
@@ -1378,7 +1561,17 @@ int decompress_impl(lcp_ctx *c, lcp_traj *t, const uint8_t *in, size_t in_size, 
                     uint64_t n_cap, uint64_t *n_out, uint32_t *d_out, cudaStream_t s,
                     bool codes_only, uint64_t floats_cap) {
   Header h;
-  TRY(read_header(c, in, in_size, h, s));
+  int rh = read_header(c, in, in_size, h, s);
+  if (rh == kDictImage) {
+    // the dictionary stage first: its container, decoded into the workspace
+    uint64_t raw = 0;
+    TRY(dict_decode(c, in, in_size, nullptr, 0, &raw, true, s));
+    in = P<uint8_t>(c->ws.dict_raw);
+    in_size = raw;
+    rh = read_header(c, in, in_size, h, s);
+    if (rh == kDictImage) rh = ERR_FORMAT;  // one stage only
+  }
+  TRY(rh);
   if (floats_cap) n_cap = floats_cap / std::max<uint32_t>(h.d, 1u);
   if (n_out) *n_out = h.n;
   if (d_out) *d_out = h.d;
@@ -1642,12 +1835,14 @@ struct ChainPeek {
       uint8_t *st = c->h_stage;
       for (uint64_t k = lo; k <= i; ++k) {
         if (!ins[k] || sizes[k] < 48) continue;
-        CK(cudaMemcpyAsync(st + 16 * (k - lo), ins[k], 16, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(st + 48 * (k - lo), ins[k], 48, cudaMemcpyDeviceToHost, s));
       }
       CK(cudaStreamSynchronize(s));
       for (uint64_t k = lo; k <= i; ++k) {
         if (method[k] >= 0) continue;
-        const uint8_t *h = st + 16 * (k - lo);
+        const uint8_t *h = st + 48 * (k - lo);
+        // an LCPZ image: its container's header from byte 32
+        if (h[0] == 'L' && h[1] == 'C' && h[2] == 'P' && h[3] == 'Z') h += 32;
         if (!ins[k] || sizes[k] < 48) {
           method[k] = 2;  // absent
           continue;
@@ -1957,6 +2152,10 @@ lcp_status lcp_decompress_step(lcp_step *S, lcp_decompress_job *jobs, int njobs,
       lcp_decompress_job &J = jobs[k];
       if (J.status != LCP_OK) continue;
       const uint8_t *h = S->h_head + 32 * (size_t)(k - base);
+      if (h[0] == 'L' && h[1] == 'C' && h[2] == 'P' && h[3] == 'Z') {
+        meth[k] = 2;  // an LCPZ image: decoded one by one
+        continue;
+      }
       if (h[0] != 'L' || h[1] != 'C' || h[2] != 'P' || h[3] != '1') {
         J.status = LCP_ERR_FORMAT;
         continue;
@@ -2059,13 +2258,18 @@ lcp_status lcp_decompress_step(lcp_step *S, lcp_decompress_job *jobs, int njobs,
 lcp_status lcp_peek(const void *d_in, size_t in_size, uint64_t *n, uint32_t *d,
                     lcp_method *method, uint32_t *flags, void *stream) {
   if (!d_in || in_size < 48) return LCP_ERR_FORMAT;
-  uint8_t h[48];
+  uint8_t img[80];
+  const size_t nb = in_size >= kDictHead ? kDictHead : 48;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemcpyAsync(h, d_in, 48, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  if (cudaMemcpyAsync(img, d_in, nb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess) {
     cudaGetLastError();
     return LCP_ERR_CUDA;
   }
+  // an LCPZ image carries its container's header at byte 32
+  const bool dict = nb == kDictHead && img[0] == 'L' && img[1] == 'C' && img[2] == 'P' &&
+                    img[3] == 'Z' && img[4] == 1;
+  const uint8_t *h = dict ? img + 32 : img;
   if (h[0] != 'L' || h[1] != 'C' || h[2] != 'P' || h[3] != '1' || h[4] != 1 || h[5] > 1 ||
       h[6] < 1 || h[6] > 8)
     return LCP_ERR_FORMAT;

@@ -82,6 +82,10 @@ SIGNATURES = {
                                         _vp]),
     "lcp_decompress_frame": (C.c_int, [_vp, _vp, C.POINTER(_vp), C.POINTER(_sz), _u64, _u64, _vp,
                                        _u64, C.POINTER(_u64), C.POINTER(_u32), _vp]),
+    "lcp_ctx_set_dict": (C.c_int, [_vp, C.c_int]),
+    "lcp_dict_max_size": (_sz, [_u64]),
+    "lcp_dict_compress": (C.c_int, [_vp, _vp, _sz, _vp, _sz, C.POINTER(_sz), _vp]),
+    "lcp_dict_decompress": (C.c_int, [_vp, _vp, _sz, _vp, _sz, C.POINTER(_sz), _vp]),
 }
 
 
@@ -178,6 +182,11 @@ def kernel_launches() -> int:
 
 def max_compressed_size(n: int, d: int) -> int:
     return int(load().lcp_max_compressed_size(n, d))
+
+
+def dict_max_size(raw_bytes: int) -> int:
+    """Largest LCPZ image of raw_bytes bytes (every chunk stored)."""
+    return int(load().lcp_dict_max_size(raw_bytes))
 
 
 class Context:
@@ -367,6 +376,37 @@ class Context:
                                          C.byref(nn), C.byref(dd), _stream(stream)),
                "lcp_decompress_frame")
         return out
+
+    def set_dict(self, on: bool = True):
+        """The dictionary stage after every compression of this context (an
+        LCPZ image kept when shorter than the container)."""
+        _check(_lib.lcp_ctx_set_dict(self.h, int(bool(on))), "lcp_ctx_set_dict")
+
+    def dict_compress(self, buf: torch.Tensor, size: int | None = None,
+                      out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """The LCPZ image of buf[:size] (uint8 CUDA), a uint8 view of out."""
+        assert buf.is_cuda and buf.dtype == torch.uint8
+        size = buf.numel() if size is None else size
+        if out is None:
+            out = torch.empty(dict_max_size(size), dtype=torch.uint8, device=buf.device)
+        n = C.c_size_t(0)
+        _check(_lib.lcp_dict_compress(self.h, _ptr(buf), size, _ptr(out), out.numel(), C.byref(n),
+                                      _stream(stream)), "lcp_dict_compress")
+        return out[:n.value]
+
+    def dict_decompress(self, img: torch.Tensor, size: int | None = None,
+                        out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """The raw bytes of an LCPZ image; without out, the size is read from
+        the image's header first."""
+        assert img.is_cuda and img.dtype == torch.uint8
+        size = img.numel() if size is None else size
+        if out is None:
+            raw = int.from_bytes(bytes(img[8:16].cpu().numpy()), "little") if size >= 16 else 0
+            out = torch.empty(max(raw, 1), dtype=torch.uint8, device=img.device)
+        n = C.c_size_t(0)
+        _check(_lib.lcp_dict_decompress(self.h, _ptr(img), size, _ptr(out), out.numel(),
+                                        C.byref(n), _stream(stream)), "lcp_dict_decompress")
+        return out[:n.value]
 
     def peek(self, buf: torch.Tensor, size: int | None = None, stream=None):
         n = C.c_uint64(0)
