@@ -253,6 +253,34 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def dict_stage(ctx, buf, size, raw, stream, reps=3):
+    """The dictionary stage (Sec. "Block coding", its last step) on the
+    frame's container, timed after the steps with CUDA events: the image's
+    size, the ratio with the stage, and each direction's time and container
+    GB/s (the fastest of reps), with a byte check of the round trip."""
+    import torch
+    from paper_2411_00761_b300 import lcp
+    img = torch.empty(lcp.dict_max_size(size), dtype=torch.uint8, device=buf.device)
+    back = torch.empty(size, dtype=torch.uint8, device=buf.device)
+    T = ctx.dict_compress(buf, size, out=img, stream=stream).numel()
+    tc, td = [], []
+    for _ in range(reps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        ctx.dict_compress(buf, size, out=img, stream=stream)
+        e[1].record(stream)
+        ctx.dict_decompress(img, T, out=back, stream=stream)
+        e[2].record(stream)
+        e[2].synchronize()
+        tc.append(e[0].elapsed_time(e[1]))
+        td.append(e[1].elapsed_time(e[2]))
+    ok = bool(torch.equal(back, buf[:size]))
+    return {"image_bytes": T, "container_bytes": size, "image_over_container": T / size,
+            "ratio_with_stage": raw / T, "encode_ms": min(tc), "decode_ms": min(td),
+            "encode_gbs": size / (min(tc) * 1e-3) / 1e9, "decode_gbs": size / (min(td) * 1e-3) / 1e9,
+            "round_trip_equal": ok}
+
+
 def fidelity(ctx, Xd, w, p, out, Y):
     """Per field: PSNR = 20 log10(value range / RMSE) (Sec. "Evaluation
     metrics") and max |x - x'| / eb_f, over every particle, from one
@@ -808,6 +836,7 @@ def main():
     ap.add_argument("--sample", type=int, default=0, help="CPU-baseline sample particles")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-dict", action="store_true", help="skip the dictionary-stage line")
     ap.add_argument("--no-tune", action="store_true", help="default schedule, no autotuning")
     ap.add_argument("--schedule", default="", help="LOG2_CHUNK,BUCKET_DELTA instead of tuning")
     ap.add_argument("--n", type=int, default=0, help="override the particle count (small cases)")
@@ -929,6 +958,8 @@ def main():
     # fidelity (Sec. "Evaluation metrics"): PSNR and the largest error / eb per
     # field, from one compression with the slot permutation (untimed)
     fid = fidelity(ctx, Xd, w, p, out, Y)
+    # the dictionary stage on the same container (untimed by the steps)
+    dst = None if args.no_dict else dict_stage(ctx, out, csize, raw, stream)
 
     # e2e through the host-buffer entry points (lcp_compress_host,
     # lcp_decompress_host): frame in and container out, container in and
@@ -993,6 +1024,7 @@ def main():
                 "traffic": measured_traffic(name, ddom, N),
                 "design_bytes_per_launch": stage_bytes(ddom, N, D, M, K, csize)},
             "fidelity": fid,
+            "dict_stage": dst,
             "stages_ms": {k: round(v, 4) for k, v in sorted(avg.items(), key=lambda x: -x[1])},
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "cpu_baseline": cpu,
