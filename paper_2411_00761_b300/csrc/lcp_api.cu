@@ -55,6 +55,7 @@ struct Workspace {
       scan_tmp, cand, tq, fplan, fstatus, cbwork, sample, rq, lut, sbounds;
   DevBuf host_in, host_out;  // device copies for the host-buffer entry points
   DevBuf hstage;             // container header bytes gathered for one copy
+  DevBuf hpad;               // a short container, zero padded to the largest header
   // dictionary stage: coded chunks, size table, chunk offsets, the image
   // (compress) and the decoded container (decompress of an LCPZ image)
   DevBuf dict_scratch, dict_sizes, dict_off, dict_img, dict_raw;
@@ -1482,7 +1483,17 @@ int read_header(lcp_ctx *c, const uint8_t *in, size_t in_size, Header &h, cudaSt
   // device: one copy, one synchronization
   const size_t head = std::min<size_t>(in_size, (size_t)kHeadBytes);
   TRY(grow(c->ws.hstage, kHeadStage));
-  launch_head_gather(in, in_size, P<uint8_t>(c->ws.hstage), s);
+  const uint8_t *src = in;
+  if (in_size < (size_t)kHeadBytes) {
+    // a buffer shorter than the largest header: gathered from a zero-padded
+    // copy, so the gather's directory reads (up to kHeadBytes) stay in
+    // memory this call owns; the bytes read are the same below in_size
+    TRY(grow(c->ws.hpad, kHeadBytes));
+    CK(cudaMemsetAsync(c->ws.hpad.p, 0, kHeadBytes, s));
+    CK(cudaMemcpyAsync(c->ws.hpad.p, in, in_size, cudaMemcpyDeviceToDevice, s));
+    src = P<uint8_t>(c->ws.hpad);
+  }
+  launch_head_gather(src, in_size, P<uint8_t>(c->ws.hstage), s);
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(st, c->ws.hstage.p, kHeadStage, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
