@@ -193,3 +193,78 @@ def test_decoder_rejects_malformed():
         with pytest.raises(oracle.OracleError) as ei:
             oracle.dict_decompress(b)
         assert ei.value.status == oracle.ERR_FORMAT
+
+
+def py_read(img: bytes) -> bytes:
+    """An independent reader of the LCPZ layout, written from its description
+    (it shares nothing with the oracle's C decoder): sizes table, stored
+    chunks, sequences with their extensions and overlapping copies."""
+    S, C, T = head(img)
+    sizes = struct.unpack_from(f"<{C}I", img, 80)
+    at = pad16(80 + 4 * C)
+    out = bytearray()
+
+    def ext(body, q, v):
+        while True:
+            b = body[q]
+            q += 1
+            v += b
+            if b != 255:
+                return q, v
+
+    for k, e in enumerate(sizes):
+        c, m = e & 0x7FFFFFFF, min(CH, S - CH * k)
+        body = img[at:at + c]
+        at += c
+        if e >> 31:
+            assert c == m
+            out += body
+            continue
+        y, q = bytearray(), 0
+        while len(y) < m:
+            tok = body[q]
+            q += 1
+            ll, ml = tok >> 4, tok & 15
+            if ll == 15:
+                q, ll = ext(body, q, ll)
+            y += body[q:q + ll]
+            q += ll
+            if len(y) == m:
+                break
+            o = body[q] | (body[q + 1] << 8)
+            q += 2
+            if ml == 15:
+                q, ml = ext(body, q, ml)
+            for _ in range(ml + 4):
+                y.append(y[-o])
+        assert q == c and len(y) == m
+        out += y
+    assert pad16(at) == T
+    return bytes(out)
+
+
+def test_independent_reader():
+    rng = np.random.default_rng(12)
+    X = synth.cosmology(1 << 14, 2)
+    inputs = [b"", b"abc", bytes(2 * CH + 100), b"abcd" * 5000, mixed_bytes(rng),
+              rng.integers(0, 256, CH + 5, dtype=np.uint8).tobytes(),
+              oracle.compress_s(X, 1.0, "abs", 8)["bytes"]]
+    for g in examples():
+        inputs.append(g[1])
+    for raw in inputs:
+        assert py_read(oracle.dict_compress(raw)) == raw
+
+
+def mixed_bytes(rng, parts=30):
+    out = []
+    for _ in range(parts):
+        k = int(rng.integers(1, 5000))
+        kind = int(rng.integers(0, 3))
+        if kind == 0:
+            out.append(rng.integers(0, 256, k, dtype=np.uint8).tobytes())
+        elif kind == 1:
+            out.append(bytes([int(rng.integers(0, 256))]) * k)
+        else:
+            base = rng.integers(0, 5, int(rng.integers(1, 30)), dtype=np.uint8).tobytes()
+            out.append((base * (k // len(base) + 1))[:k])
+    return b"".join(out)
